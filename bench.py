@@ -1,0 +1,315 @@
+#!/usr/bin/env python
+"""Benchmark: hierarchical iso-surface extraction at 512^3 on the scientific-field workload.
+
+One step = one full extraction through the C interface (isx_extract_isosurface): every octree
+level from the root to 512^3 bounded by propagating affine / probabilistic-affine forms through the
+3 -> 256 (5 hidden) -> 1 ReLU INR, culling, compaction, corner evaluation of the active cells and
+marching cubes for the 8 iso-values.  `value` is AA-bounded cells per second over the timed steps
+(cells bounded, summed over levels, divided by extraction time); `ms_per_step` is the extraction
+time.  Between steps a 512 MB buffer is written to flush the L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank extracts its own INR replica (independent problems; no
+collective on the data path); value = cells bounded on all ranks / max time over ranks.
+--impl reference times the float64 CPU oracle on a bounded sample of the same workload (cells of
+levels 6-9 drawn at random), on rank 0 only.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "scientific"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="clt", choices=["sound", "clt", "raua"])
+    ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "bf16"])
+    ap.add_argument("--k", type=float, default=3.0)
+    ap.add_argument("--max-level", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples taken while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def traffic_for(kernel, src_file):
+    """ncu DRAM bytes per launch recorded in profiles/traffic.json, if the kernel source is unchanged."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+        sha = hashlib.sha256(open(src_file, "rb").read()).hexdigest()[:16]
+        return rec["dram_bytes_per_launch"] if rec.get("src_sha") == sha else None
+    except Exception:
+        return None
+
+
+def cpu_baseline(layers, mode, k, budget_s=12.0):
+    """Float64 oracle bounding random cells of levels 6-9 of the same workload for ~budget_s."""
+    import numpy as np
+    from oracle import affine
+    from synth import boxes
+    ijk, level, lo, hi = boxes.random_cubes(4096, 77, 6, 9)
+    done = 0
+    t0 = time.perf_counter()
+    bs = 16
+    while time.perf_counter() - t0 < budget_s and done < 4096:
+        affine.bound(layers, lo[done:done + bs], hi[done:done + bs], mode, batch=bs)
+        done += bs
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OPENBLAS_NUM_THREADS", os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)))
+    return {"value": done / dt, "unit": "cells/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} random cells of levels 6-9 bounded by the float64 oracle ({mode}) in {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from synth import inr
+    layers, isos, wl = inr.load_inr(WORKLOAD)
+    mode = args.mode
+    per = []
+    total = 0.0
+    for s in range(args.warmup + args.steps):
+        cb = cpu_baseline(layers, mode, args.k, budget_s=8.0 if s >= args.warmup else 2.0)
+        if s >= args.warmup:
+            per.append(cb["value"])
+            total += 1
+    value = statistics.mean(per)
+    line = {"impl": "reference", "metric": "AA-bounded cells/s (hierarchical iso-extraction, 512^3, 8 isos)",
+            "value": value, "unit": "cells/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "scientific-field 512^3, 3->256x5->1 ReLU INR, 8 isos",
+                                            "mode": mode, "k": args.k},
+            "cpu_baseline": dict(cb, value=value),
+            "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2402_13861_gb300 as pkg
+    from synth import inr
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    # weights: committed fixture or per-box cache (rank 0 fits if needed)
+    if rank == 0:
+        layers, isos, wl = inr.load_inr(WORKLOAD)
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        layers, isos, wl = inr.load_inr(WORKLOAD)
+    L = args.max_level if args.max_level is not None else wl.max_level
+    prec = args.prec
+    net = pkg.Inr(layers)
+    if prec == "auto":
+        prec = "bf16" if pkg._lib.load() and _bf16_ok(net, pkg) else "fp32"
+    kw = dict(mode=args.mode, k=args.k, prec=prec, inflate=(args.mode == "sound"))
+    bufs = {}
+    res = net.extract(L, isos, buffers=bufs, active_cap=1 << 22, tri_cap=1 << 24, **kw)   # sizes the buffers
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(max(0, args.warmup - 1)):
+        flush.zero_()
+        net.extract(L, isos, buffers=bufs, **kw)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    pkg.profile_reset()
+    pkg.profile_enable(True)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    total_ms, cells, phases = 0.0, 0, np.zeros(3)
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        res = net.extract(L, isos, buffers=bufs, **kw)
+        b.record(st)
+        torch.cuda.synchronize()
+        total_ms += a.elapsed_time(b)
+        cells += sum(res["cells_bounded"])
+        phases += [res["ms_acp"], res["ms_inr"], res["ms_mc"]]
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    pkg.profile_enable(False)
+    stats = pkg.profile_read()
+    t = torch.tensor([total_ms, float(cells)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        total_ms, cells = float(tmax[0]), float(t[1])
+    value = cells / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+
+    # end to end through the public API with host buffers: weights in, mesh out
+    e2e = None
+    if not args.no_e2e:
+        e2e_ms, h2d, d2h = 0.0, 0, 0
+        pinned = {}
+        host_layers = [(np.ascontiguousarray(W), np.ascontiguousarray(b_)) for W, b_ in layers]
+        for _ in range(max(1, min(args.steps, 2))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            net2 = pkg.Inr(host_layers)
+            r = net2.extract(L, isos, buffers=bufs, **kw)
+            nt, na = r["n_tris"], r["n_active"]
+            for key, tens in (("vert", r["tri_vert"]), ("edge", r["tri_edge"]), ("iso", r["tri_iso"]),
+                              ("code", r["codes"]), ("mask", r["masks"])):
+                if key not in pinned or pinned[key].numel() < tens.numel():
+                    pinned[key] = torch.empty(max(tens.numel(), 1), dtype=tens.dtype, pin_memory=True)
+                pinned[key][:tens.numel()].copy_(tens.reshape(-1), non_blocking=True)
+            torch.cuda.synchronize()
+            e2e_ms += (time.perf_counter() - t0) * 1e3
+            net2.close()
+            h2d = sum(W.nbytes + b_.nbytes for W, b_ in host_layers)
+            d2h = nt * (36 + 24 + 4) + na * 8
+            steps_e2e = max(1, min(args.steps, 2))
+        cells_one = sum(r["cells_bounded"])
+        e2e = {"value": cells_one * world / (e2e_ms / steps_e2e / 1e3), "unit": "cells/s",
+               "ms_per_step": e2e_ms / steps_e2e, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    peaks = load_peaks()
+    bound_kernels = ["bound_tc", "gemm_fp32"]
+    dom = max(bound_kernels, key=lambda k: stats.get(k, {}).get("ms", 0.0))
+    ds = stats[dom]
+    if dom == "bound_tc":
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak_source": "measured bf16_tflops_sustained"}
+        src = os.path.join(ROOT, "paper_2402_13861_gb300", "csrc", "bound_tc.cu")
+    else:
+        # float32 FMA issue rate: 152 SMs x 128 lanes x 2 FLOP x max SM clock
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak_source": "152 SM x 128 FP32 lanes x 2 x max SM clock"}
+        src = os.path.join(ROOT, "paper_2402_13861_gb300", "csrc", "bound_fp32.cu")
+    achieved = ds["flops"] / (ds["ms"] / 1e3) / 1e12 if ds["ms"] > 0 else 0.0
+    tr = traffic_for(dom, src)
+    roof.update({"kernel": dom, "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                 "launches": ds["launches"], "avg_launch_ms": ds["ms"] / max(ds["launches"], 1),
+                 "traffic": tr})
+    launches = int(sum(v["launches"] for v in stats.values()))
+    shares = {k: round(v["ms"] / max(sum(x["ms"] for x in stats.values()), 1e-9), 4) for k, v in stats.items()
+              if v["ms"] > 0}
+    line = {"metric": "AA-bounded cells/s (hierarchical iso-extraction, 512^3, 8 isos)", "value": value,
+            "unit": "cells/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if prec == "bf16" else "f32", "data": "synthetic",
+            "config": {"workload": f"scientific-field {1 << L}^3: 3->256x5->1 ReLU INR fitted to 256 anisotropic "
+                                   f"Gaussians + sine, 8 isos over the 10-90% quantiles", "mode": args.mode,
+                       "k": args.k, "precision": prec, "inflate": kw["inflate"], "max_level": L,
+                       "l2": "512 MB buffer written between timed steps", "parallelism": f"replicas x{world}"},
+            "phase_ms": {"acp": phases[0] / args.steps, "inr": phases[1] / args.steps, "mc": phases[2] / args.steps},
+            "cells_bounded_per_step": cells / args.steps / world, "n_active": res["n_active"],
+            "n_tris": res["n_tris"], "cells_bounded_per_level": res["cells_bounded"],
+            "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "kernel_time_share": shares}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(layers, args.mode, args.k)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    net.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _bf16_ok(net, pkg):
+    import torch
+    try:
+        lo = torch.zeros((1, 3), device="cuda")
+        net.bound_cells(lo, lo + 0.5, mode="clt", prec="bf16")
+        torch.cuda.synchronize()
+        return True
+    except pkg.IsxError:
+        return False
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * isx.h -- C interface of the GB300 (sm_103a) library for hierarchical iso-surface extraction on
+ * ReLU-MLP implicit neural representations (Li & Shen, "Improving Efficiency of Iso-Surface
+ * Extraction on Implicit Neural Representations Using Uncertainty Propagation").
+ *
+ * Conventions for every entry point
+ *  - Pointers named d_* are CUDA device pointers on the current device, owned by the caller; the
+ *    library never frees them.  Host pointers (descriptors, iso-value arrays) are read during the
+ *    call only.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Work is enqueued
+ *    on it; entry points that must read counts back (extraction) synchronise it before returning.
+ *  - Every entry point returns an isx_status; nothing throws across this interface.  On failure
+ *    isx_last_error() returns a message for the calling thread.  A capacity shortfall returns
+ *    ISX_ERR_CAPACITY after filling in the required sizes, without writing past any capacity.
+ *  - Cells of octree level l are integer triples (i, j, k) in [0, 2^l)^3 with box
+ *    lo = -1 + 2 (i, j, k) / 2^l, hi = lo + 2 / 2^l; they are passed packed as
+ *    code = i | j << 10 | k << 20, so levels go up to ISX_MAX_LEVEL = 10 (1024^3 cells).
+ *  - The library keeps a per-INR workspace in device memory (grown with cudaMalloc on first use
+ *    of a larger problem and freed by isx_destroy_inr).
+ */
+#ifndef ISX_H
+#define ISX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ISX_MAX_ISO 32
+#define ISX_MAX_LEVEL 10
+#define ISX_MAX_LAYERS 16
+#define ISX_MC_MAX_TRI 5
+
+typedef struct isx_inr_s* isx_inr;
+
+typedef enum {
+  ISX_OK = 0,
+  ISX_ERR_ARG = 1,          /* invalid argument (null pointer, bad size, unsupported shape)      */
+  ISX_ERR_CUDA = 2,         /* a CUDA runtime call or kernel launch failed                       */
+  ISX_ERR_CAPACITY = 3,     /* an output buffer is too small; required sizes were filled in      */
+  ISX_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up; the context stays usable     */
+  ISX_ERR_UNSUPPORTED = 5,  /* valid request this build does not implement (e.g. width for BF16) */
+  ISX_ERR_NOMEM = 6         /* workspace allocation failed                                       */
+} isx_status;
+
+/* How a cell's output range is bounded.
+ *  SOUND: affine arithmetic (Sec. III-A, Eqs. 1-4): [x0 - r, x0 + r], r = sum |x_i| (Eq. 2), with
+ *         the minimax (Chebyshev) linearisation of ReLU (Eq. 4).
+ *  CLT:   uncertainty propagation with probabilistic affine forms (Sec. IV-B/C, Eqs. 6-10): input
+ *         symbols scaled by 1/sqrt(3), ReLU linearised by least squares under N(mu, sigma^2)
+ *         (Table VII), output N(mu, sigma^2) with sigma^2 = sum x_i^2 (Eq. 7), bound mu +- k sigma
+ *         (Algorithm 1).
+ *  RAUA:  SOUND propagation, then sigma^2 = (1/3) sum x_i^2 at the output only (Sec. IV-A),
+ *         bound x0 +- k sigma. */
+typedef enum { ISX_BOUND_SOUND = 0, ISX_BOUND_CLT = 1, ISX_BOUND_RAUA = 2 } isx_bound_mode;
+
+/* Arithmetic of the coefficient propagation.  FP32: float32 storage and FMA.  BF16: coefficient
+ * matrices stored in bfloat16 and multiplied on tcgen05 tensor cores with float32 accumulation;
+ * centres, reductions and linearisations stay float32. */
+typedef enum { ISX_PREC_FP32 = 0, ISX_PREC_BF16 = 1 } isx_precision;
+
+/* A ReLU MLP: n_layers linear layers 3 -> w -> ... -> w -> 1 with ReLU after every layer but the
+ * last (the ReLU INRs of App. E).  All hidden widths must be equal.  W[l] is row-major
+ * [dims[l+1]][dims[l]] float32, b[l] has dims[l+1] entries; both are HOST pointers, copied by
+ * isx_create_inr (the caller keeps ownership). */
+typedef struct {
+  int n_layers;             /* 2 .. ISX_MAX_LAYERS                     */
+  const int* dims;          /* n_layers + 1 entries, dims[0] = 3, dims[n_layers] = 1 */
+  const float* const* W;
+  const float* const* b;
+} isx_inr_desc;
+
+/* Copies the weights to the current device (float32, transposed and bfloat16 copies for the
+ * kernels).  Errors: ISX_ERR_ARG for a malformed descriptor, ISX_ERR_CUDA / ISX_ERR_NOMEM. */
+isx_status isx_create_inr(const isx_inr_desc* desc, isx_inr* out);
+isx_status isx_destroy_inr(isx_inr inr);
+
+/* Bounds the INR over n axis-aligned boxes (the per-node step of Algorithm 1: node set-up,
+ * propagation, read-off).  d_lo, d_hi: device float32 [n][3], lo <= hi componentwise.
+ * Outputs (device float32 [n]): d_center = x0 (SOUND, RAUA) or mu (CLT); d_spread = r (SOUND) or
+ * sigma (CLT, RAUA).  `inflate` != 0 (SOUND only) widens r by a bound on every rounding error of
+ * the chosen precision so that [x0 - r, x0 + r] encloses the exact range of the float32-weight
+ * network; with inflate = 0 the arithmetic follows the paper's formulas without that term.
+ * n = 0 is valid and enqueues nothing. */
+isx_status isx_bound_cells(isx_inr inr, const float* d_lo, const float* d_hi, int64_t n,
+                           isx_bound_mode mode, isx_precision prec, int inflate,
+                           float* d_center, float* d_spread, void* stream);
+
+/* Evaluates the INR at n points (device float32 [n][3]) into d_out (device float32 [n]). */
+isx_status isx_eval_points(isx_inr inr, const float* d_xyz, int64_t n, isx_precision prec,
+                           float* d_out, void* stream);
+
+typedef struct {
+  int max_level;                 /* finest grid: 2^max_level cells per axis over [-1, 1]^3     */
+  int n_iso;                     /* 1 .. ISX_MAX_ISO                                            */
+  float iso[ISX_MAX_ISO];        /* iso-values c (Algorithm 1)                                  */
+  isx_bound_mode mode;
+  float k;                       /* confidence multiplier t of Algorithm 1 (CLT, RAUA)          */
+  isx_precision prec;
+  int inflate;                   /* SOUND only: rounding-error inflation (see isx_bound_cells)  */
+  int bound_stop_level;          /* levels deeper than this keep every child without bounding;
+                                    < 0 or >= max_level: bound every level (the paper's setting) */
+} isx_extract_params;
+
+typedef struct {
+  /* caller-owned device outputs and capacities (in elements of the first dimension) */
+  uint32_t* d_active_code;       /* [active_cap] packed codes of the predicted active cells      */
+  uint32_t* d_active_mask;       /* [active_cap] bit q set: cell predicted active for iso q       */
+  int64_t active_cap;
+  float* d_tri_vert;             /* [tri_cap][3][3] triangle vertex positions                     */
+  int64_t* d_tri_edge;           /* [tri_cap][3] global lattice-edge id of each vertex            */
+  int32_t* d_tri_iso;            /* [tri_cap] iso-value index of each triangle                    */
+  uint32_t* d_tri_cell;          /* [tri_cap] packed code of each triangle's cell (may be NULL)   */
+  int64_t tri_cap;
+  /* filled in by the call */
+  int64_t n_active;              /* predicted active cells                                        */
+  int64_t n_tris;                /* triangles over all iso-values                                 */
+  int64_t n_points;              /* distinct lattice corners evaluated                            */
+  int64_t cells_bounded[ISX_MAX_LEVEL + 1];
+  int64_t cells_kept[ISX_MAX_LEVEL + 1];
+  float ms_acp, ms_inr, ms_mc, ms_total;   /* active-cell prediction, corner evaluation, marching
+                                              cubes, whole call (CUDA events on `stream`)        */
+} isx_mesh;
+
+/* Hierarchical extraction (Algorithm 1 run level by level over octree cubes, then corner queries
+ * and marching cubes in the predicted active cells, Sec. IV-D).  The root cell [-1,1]^3 is bounded
+ * first; a cell keeps iso q iff lower <= c_q <= upper and survives while any iso remains; at
+ * max_level the survivors are the active cells.  Their distinct corners are evaluated and
+ * triangulated per iso-value (inside = value < c).  Triangles are written in cell order.
+ * Synchronises `stream`.  Errors: ISX_ERR_ARG, ISX_ERR_CAPACITY (n_active / n_tris hold the
+ * required sizes), ISX_ERR_UNSUPPORTED (e.g. BF16 for an unsupported width), ISX_ERR_CUDA. */
+isx_status isx_extract_isosurface(isx_inr inr, const isx_extract_params* params, isx_mesh* mesh,
+                                  void* stream);
+
+/* The dense baseline of Sec. V-A.4: evaluates every lattice point of the (2^max_level + 1)^3 grid
+ * and runs marching cubes in every cell.  d_active_* are not written (n_active = cells with at least
+ * one triangle).  mode, k, inflate and bound_stop_level are ignored. */
+isx_status isx_extract_dense(isx_inr inr, const isx_extract_params* params, isx_mesh* mesh,
+                             void* stream);
+
+/* The library's marching-cubes case table (host memory): ntri[256] triangle counts and
+ * tris[256][ISX_MC_MAX_TRI][3] local edge numbers (-1 = unused).  Corner c of a cell sits at
+ * (c & 1, c >> 1 & 1, c >> 2 & 1); edge 4a + t runs along axis a from the corner with bit a clear;
+ * the two other axes p < q take bits t & 1 and t >> 1.  Host-only; needs no GPU. */
+isx_status isx_mc_table(int8_t* ntri, int8_t* tris);
+
+/* ---- measurement ----------------------------------------------------------------------------
+ * Per-kernel accounting.  Launch counts and the algorithmic work of every launch (FLOPs and bytes
+ * the method needs, excluding padding and recomputation) are always accumulated; with profiling
+ * enabled every launch is also bracketed by CUDA events on its stream, and isx_profile_read
+ * synchronises on them.  Counters are process-wide. */
+typedef struct {
+  const char* name;              /* kernel name (static string)                                   */
+  int64_t launches;
+  double ms;                     /* summed event time (0 unless profiling was enabled)            */
+  double flops;                  /* summed algorithmic FLOPs                                       */
+  double bytes;                  /* summed algorithmic HBM bytes                                   */
+} isx_kernel_stats;
+
+void isx_profile_enable(int on);
+void isx_profile_reset(void);
+/* Fills up to `max` entries and returns how many kernels the library knows. */
+int isx_profile_read(isx_kernel_stats* out, int max);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* isx_last_error(void);
+
+/* Library version: 100 * major + minor. */
+int isx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISX_H */

@@ -1,0 +1,7 @@
+"""GB300 (sm_103a) hierarchical iso-surface extraction on ReLU-MLP implicit neural representations.
+
+The computation lives in the CUDA library ``libisx.so`` (C interface: include/isx.h); this package
+only builds it and marshals arguments to it (``_lib``).
+"""
+from ._lib import (BF16, CLT, FP32, RAUA, SOUND, Inr, IsxError, load, mc_table, profile_enable,  # noqa: F401
+                   profile_read, profile_reset)

@@ -1,0 +1,251 @@
+"""ctypes binding of the C interface in include/isx.h: argument marshalling only.
+
+Device memory and streams come from PyTorch (tensors' data pointers, torch.cuda streams); every
+step of the computation runs in the library's CUDA kernels.  There is no fallback: if the
+library is missing or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+PKG = Path(__file__).resolve().parent
+LIB_PATH = PKG / "libisx.so"
+
+ISX_MAX_ISO = 32
+ISX_MAX_LEVEL = 10
+ISX_MC_MAX_TRI = 5
+
+SOUND, CLT, RAUA = 0, 1, 2
+FP32, BF16 = 0, 1
+MODES = {"sound": SOUND, "clt": CLT, "raua": RAUA}
+PRECS = {"fp32": FP32, "bf16": BF16}
+
+STATUS = {0: "ISX_OK", 1: "ISX_ERR_ARG", 2: "ISX_ERR_CUDA", 3: "ISX_ERR_CAPACITY", 4: "ISX_ERR_TIMEOUT",
+          5: "ISX_ERR_UNSUPPORTED", 6: "ISX_ERR_NOMEM"}
+
+
+class IsxError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class KernelStats(C.Structure):
+    _fields_ = [("name", C.c_char_p), ("launches", C.c_int64), ("ms", C.c_double), ("flops", C.c_double),
+                ("bytes", C.c_double)]
+
+
+class InrDesc(C.Structure):
+    _fields_ = [("n_layers", C.c_int), ("dims", C.POINTER(C.c_int)),
+                ("W", C.POINTER(C.POINTER(C.c_float))), ("b", C.POINTER(C.POINTER(C.c_float)))]
+
+
+class ExtractParams(C.Structure):
+    _fields_ = [("max_level", C.c_int), ("n_iso", C.c_int), ("iso", C.c_float * ISX_MAX_ISO),
+                ("mode", C.c_int), ("k", C.c_float), ("prec", C.c_int), ("inflate", C.c_int),
+                ("bound_stop_level", C.c_int)]
+
+
+class Mesh(C.Structure):
+    _fields_ = [("d_active_code", C.c_void_p), ("d_active_mask", C.c_void_p), ("active_cap", C.c_int64),
+                ("d_tri_vert", C.c_void_p), ("d_tri_edge", C.c_void_p), ("d_tri_iso", C.c_void_p),
+                ("d_tri_cell", C.c_void_p), ("tri_cap", C.c_int64),
+                ("n_active", C.c_int64), ("n_tris", C.c_int64), ("n_points", C.c_int64),
+                ("cells_bounded", C.c_int64 * (ISX_MAX_LEVEL + 1)),
+                ("cells_kept", C.c_int64 * (ISX_MAX_LEVEL + 1)),
+                ("ms_acp", C.c_float), ("ms_inr", C.c_float), ("ms_mc", C.c_float), ("ms_total", C.c_float)]
+
+
+_lib = None
+
+
+def load(path: Path | None = None):
+    """Load the shared library (building nothing); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = Path(path) if path else LIB_PATH
+    if not p.exists():
+        raise FileNotFoundError(f"{p} is missing: run __graft_entry__.build() (or python -m "
+                                f"paper_2402_13861_gb300.build) first")
+    lib = C.CDLL(str(p))
+    vp, i64, f32p = C.c_void_p, C.c_int64, C.POINTER(C.c_float)
+    lib.isx_create_inr.argtypes = [C.POINTER(InrDesc), C.POINTER(vp)]
+    lib.isx_destroy_inr.argtypes = [vp]
+    lib.isx_bound_cells.argtypes = [vp, vp, vp, i64, C.c_int, C.c_int, C.c_int, vp, vp, vp]
+    lib.isx_eval_points.argtypes = [vp, vp, i64, C.c_int, vp, vp]
+    lib.isx_extract_isosurface.argtypes = [vp, C.POINTER(ExtractParams), C.POINTER(Mesh), vp]
+    lib.isx_extract_dense.argtypes = [vp, C.POINTER(ExtractParams), C.POINTER(Mesh), vp]
+    lib.isx_mc_table.argtypes = [C.POINTER(C.c_int8), C.POINTER(C.c_int8)]
+    lib.isx_last_error.restype = C.c_char_p
+    lib.isx_last_error.argtypes = []
+    lib.isx_version.restype = C.c_int
+    lib.isx_profile_enable.argtypes = [C.c_int]
+    lib.isx_profile_enable.restype = None
+    lib.isx_profile_reset.argtypes = []
+    lib.isx_profile_reset.restype = None
+    lib.isx_profile_read.argtypes = [C.POINTER(KernelStats), C.c_int]
+    lib.isx_profile_read.restype = C.c_int
+    for name in ("isx_create_inr", "isx_destroy_inr", "isx_bound_cells", "isx_eval_points",
+                 "isx_extract_isosurface", "isx_extract_dense", "isx_mc_table"):
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != 0:
+        raise IsxError(status, load().isx_last_error().decode())
+
+
+def mc_table():
+    """The library's marching-cubes table: (ntri[256] int8, tris[256, 5, 3] int8)."""
+    lib = load()
+    ntri = np.zeros(256, dtype=np.int8)
+    tris = np.zeros(256 * ISX_MC_MAX_TRI * 3, dtype=np.int8)
+    _check(lib.isx_mc_table(ntri.ctypes.data_as(C.POINTER(C.c_int8)), tris.ctypes.data_as(C.POINTER(C.c_int8))))
+    return ntri, tris.reshape(256, ISX_MC_MAX_TRI, 3)
+
+
+def profile_enable(on=True):
+    load().isx_profile_enable(int(bool(on)))
+
+
+def profile_reset():
+    load().isx_profile_reset()
+
+
+def profile_read():
+    """{kernel name: dict(launches, ms, flops, bytes)} accumulated since the last reset."""
+    arr = (KernelStats * 64)()
+    n = load().isx_profile_read(arr, 64)
+    return {arr[i].name.decode(): dict(launches=arr[i].launches, ms=arr[i].ms, flops=arr[i].flops,
+                                       bytes=arr[i].bytes) for i in range(n)}
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+class Inr:
+    """An INR resident on the current CUDA device (wraps isx_inr)."""
+
+    def __init__(self, layers):
+        lib = load()
+        self.layers = [(np.ascontiguousarray(W, dtype=np.float32), np.ascontiguousarray(b, dtype=np.float32))
+                       for W, b in layers]
+        dims = [self.layers[0][0].shape[1]] + [W.shape[0] for W, _ in self.layers]
+        self.dims = dims
+        n = len(self.layers)
+        c_dims = (C.c_int * (n + 1))(*dims)
+        Wp = (C.POINTER(C.c_float) * n)(*[W.ctypes.data_as(C.POINTER(C.c_float)) for W, _ in self.layers])
+        bp = (C.POINTER(C.c_float) * n)(*[b.ctypes.data_as(C.POINTER(C.c_float)) for _, b in self.layers])
+        desc = InrDesc(n, c_dims, Wp, bp)
+        h = C.c_void_p()
+        _check(lib.isx_create_inr(C.byref(desc), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().isx_destroy_inr(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def bound_cells(self, lo, hi, mode="sound", prec="fp32", inflate=False, center=None, spread=None, stream=None):
+        """lo, hi: float32 CUDA tensors (n, 3).  Returns (center, spread) CUDA tensors (n,)."""
+        import torch
+        n = lo.shape[0]
+        assert lo.is_cuda and lo.dtype == torch.float32 and lo.is_contiguous() and hi.is_contiguous()
+        if center is None:
+            center = torch.empty(n, dtype=torch.float32, device=lo.device)
+        if spread is None:
+            spread = torch.empty(n, dtype=torch.float32, device=lo.device)
+        _check(load().isx_bound_cells(self._h, _ptr(lo), _ptr(hi), n, MODES[mode], PRECS[prec], int(bool(inflate)),
+                                      _ptr(center), _ptr(spread), _stream_ptr(stream)))
+        return center, spread
+
+    def eval_points(self, xyz, prec="fp32", out=None, stream=None):
+        import torch
+        n = xyz.shape[0]
+        if out is None:
+            out = torch.empty(n, dtype=torch.float32, device=xyz.device)
+        _check(load().isx_eval_points(self._h, _ptr(xyz), n, PRECS[prec], _ptr(out), _stream_ptr(stream)))
+        return out
+
+    @staticmethod
+    def params(max_level, isos, mode="sound", k=3.0, prec="fp32", inflate=False, bound_stop_level=-1):
+        p = ExtractParams()
+        p.max_level = max_level
+        isos = list(np.atleast_1d(np.asarray(isos, dtype=np.float32)))
+        p.n_iso = len(isos)
+        for q, c in enumerate(isos):
+            p.iso[q] = float(c)
+        p.mode = MODES[mode]
+        p.k = float(k)
+        p.prec = PRECS[prec]
+        p.inflate = int(bool(inflate))
+        p.bound_stop_level = bound_stop_level
+        return p
+
+    def extract(self, max_level, isos, mode="sound", k=3.0, prec="fp32", inflate=False, bound_stop_level=-1,
+                active_cap=1 << 16, tri_cap=1 << 18, dense=False, stream=None, buffers=None):
+        """Hierarchical (or, with dense=True, dense) extraction.  Grows the output buffers and
+        retries once if a capacity is exceeded.  Returns a dict of tensors and counters."""
+        import torch
+        p = self.params(max_level, isos, mode, k, prec, inflate, bound_stop_level)
+        fn = load().isx_extract_dense if dense else load().isx_extract_isosurface
+        dev = torch.device("cuda", torch.cuda.current_device())
+        bufs = buffers if buffers is not None else {}
+        for attempt in range(3):
+            if bufs.get("active_cap", -1) < active_cap:
+                bufs["code"] = torch.empty(max(active_cap, 1), dtype=torch.int32, device=dev)
+                bufs["mask"] = torch.empty(max(active_cap, 1), dtype=torch.int32, device=dev)
+                bufs["active_cap"] = active_cap
+            if bufs.get("tri_cap", -1) < tri_cap:
+                bufs["vert"] = torch.empty((max(tri_cap, 1), 3, 3), dtype=torch.float32, device=dev)
+                bufs["edge"] = torch.empty((max(tri_cap, 1), 3), dtype=torch.int64, device=dev)
+                bufs["iso"] = torch.empty(max(tri_cap, 1), dtype=torch.int32, device=dev)
+                bufs["cell"] = torch.empty(max(tri_cap, 1), dtype=torch.int32, device=dev)
+                bufs["tri_cap"] = tri_cap
+            m = Mesh()
+            m.d_active_code = bufs["code"].data_ptr()
+            m.d_active_mask = bufs["mask"].data_ptr()
+            m.active_cap = bufs["active_cap"]
+            m.d_tri_vert = bufs["vert"].data_ptr()
+            m.d_tri_edge = bufs["edge"].data_ptr()
+            m.d_tri_iso = bufs["iso"].data_ptr()
+            m.d_tri_cell = bufs["cell"].data_ptr()
+            m.tri_cap = bufs["tri_cap"]
+            st = fn(self._h, C.byref(p), C.byref(m), _stream_ptr(stream))
+            if st == 3 and attempt < 2:
+                active_cap = max(active_cap, int(m.n_active))
+                tri_cap = max(tri_cap, int(m.n_tris))
+                continue
+            _check(st)
+            break
+        na, nt = int(m.n_active), int(m.n_tris)
+        return dict(
+            codes=None if dense else bufs["code"][:na], masks=None if dense else bufs["mask"][:na],
+            tri_vert=bufs["vert"][:nt], tri_edge=bufs["edge"][:nt], tri_iso=bufs["iso"][:nt], tri_cell=bufs["cell"][:nt],
+            n_active=na, n_tris=nt, n_points=int(m.n_points),
+            cells_bounded=list(m.cells_bounded)[:max_level + 1], cells_kept=list(m.cells_kept)[:max_level + 1],
+            ms_acp=m.ms_acp, ms_inr=m.ms_inr, ms_mc=m.ms_mc, ms_total=m.ms_total, buffers=bufs)

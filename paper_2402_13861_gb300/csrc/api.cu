@@ -1,0 +1,390 @@
+// The C interface (include/isx.h): INR handles, workspace, and the host-side driver of the level
+// loop of Algorithm 1 followed by corner queries and marching cubes.
+#include "internal.cuh"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+namespace isx {
+
+namespace {
+thread_local std::string g_err;
+}
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+isx_status cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  char buf[512];
+  std::snprintf(buf, sizeof(buf), "CUDA error %d (%s) in %s at %s:%d", (int)e, cudaGetErrorString(e), what, file,
+                line);
+  g_err = buf;
+  if (e == cudaErrorMemoryAllocation) return ISX_ERR_NOMEM;
+  return ISX_ERR_CUDA;
+}
+
+isx_status Buf::ensure(size_t need, const char* name) {
+  if (need <= bytes) return ISX_OK;
+  if (ptr) {
+    cudaError_t e = cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+    if (e != cudaSuccess) return cuda_fail(e, name, __FILE__, __LINE__);
+  }
+  size_t alloc = std::max<size_t>(need + need / 8, 4096);
+  alloc = (alloc + 255) & ~size_t(255);
+  cudaError_t e = cudaMalloc(&ptr, alloc);
+  if (e != cudaSuccess) {
+    ptr = nullptr;
+    (void)cudaGetLastError();
+    return cuda_fail(e, name, __FILE__, __LINE__);
+  }
+  bytes = alloc;
+  return ISX_OK;
+}
+
+void Buf::release() {
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+  bytes = 0;
+}
+
+namespace {
+
+isx_status check_inr(isx_inr inr) {
+  if (!inr) {
+    set_error("null INR handle");
+    return ISX_ERR_ARG;
+  }
+  int dev = -1;
+  ISX_CUDA(cudaGetDevice(&dev));
+  if (dev != inr->device) {
+    set_error("the INR was created on another device than the current one");
+    return ISX_ERR_ARG;
+  }
+  return ISX_OK;
+}
+
+isx_status bound_dispatch(isx_inr inr, const CellSource& src, int64_t n, isx_bound_mode mode, isx_precision prec,
+                          int inflate, float* center, float* spread, cudaStream_t st) {
+  if (prec == ISX_PREC_BF16) return bound_bf16(inr, src, n, mode, inflate, center, spread, st);
+  return bound_fp32(inr, src, n, mode, inflate, center, spread, st);
+}
+
+struct Timer {
+  cudaEvent_t ev[4] = {};
+  isx_status init() {
+    for (auto& e : ev) ISX_CUDA(cudaEventCreate(&e));
+    return ISX_OK;
+  }
+  ~Timer() {
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
+isx_status validate_params(const isx_extract_params* p, const isx_mesh* m) {
+  if (!p || !m) {
+    set_error("null params or mesh");
+    return ISX_ERR_ARG;
+  }
+  if (p->max_level < 0 || p->max_level > ISX_MAX_LEVEL) {
+    set_error("max_level must be in [0, 10]");
+    return ISX_ERR_ARG;
+  }
+  if (p->n_iso < 1 || p->n_iso > ISX_MAX_ISO) {
+    set_error("n_iso must be in [1, 32]");
+    return ISX_ERR_ARG;
+  }
+  if (p->mode < ISX_BOUND_SOUND || p->mode > ISX_BOUND_RAUA || p->prec < ISX_PREC_FP32 || p->prec > ISX_PREC_BF16) {
+    set_error("bad mode or precision");
+    return ISX_ERR_ARG;
+  }
+  if (!(p->k >= 0.0f) && p->mode != ISX_BOUND_SOUND) {
+    set_error("k must be >= 0");
+    return ISX_ERR_ARG;
+  }
+  return ISX_OK;
+}
+
+IsoSet iso_of(const isx_extract_params* p) {
+  IsoSet s;
+  s.n = p->n_iso;
+  for (int q = 0; q < ISX_MAX_ISO; ++q) s.c[q] = q < p->n_iso ? p->iso[q] : 0.0f;
+  return s;
+}
+
+}  // namespace
+}  // namespace isx
+
+using namespace isx;
+
+extern "C" {
+
+const char* isx_last_error(void) { return g_err.c_str(); }
+
+int isx_version(void) { return 100; }
+
+isx_status isx_mc_table(int8_t* ntri, int8_t* tris) {
+  if (!ntri || !tris) {
+    set_error("null table pointer");
+    return ISX_ERR_ARG;
+  }
+  mc_build_table(ntri, tris);
+  return ISX_OK;
+}
+
+isx_status isx_create_inr(const isx_inr_desc* d, isx_inr* out) {
+  if (!d || !out || !d->dims || !d->W || !d->b) {
+    set_error("null descriptor field");
+    return ISX_ERR_ARG;
+  }
+  *out = nullptr;
+  int L = d->n_layers;
+  if (L < 2 || L > ISX_MAX_LAYERS) {
+    set_error("n_layers must be in [2, 16]");
+    return ISX_ERR_ARG;
+  }
+  if (d->dims[0] != 3 || d->dims[L] != 1) {
+    set_error("dims must start with 3 and end with 1");
+    return ISX_ERR_ARG;
+  }
+  int w = d->dims[1];
+  for (int l = 1; l < L; ++l)
+    if (d->dims[l] != w) {
+      set_error("hidden widths must be equal");
+      return ISX_ERR_ARG;
+    }
+  if (w < 16 || w > 512 || w % 16 != 0) {
+    set_error("hidden width must be a multiple of 16 in [16, 512]");
+    return ISX_ERR_UNSUPPORTED;
+  }
+  for (int l = 0; l < L; ++l)
+    if (!d->W[l] || !d->b[l]) {
+      set_error("null weight pointer");
+      return ISX_ERR_ARG;
+    }
+  isx_inr inr = new isx_inr_s();
+  ISX_CUDA(cudaGetDevice(&inr->device));
+  inr->n_layers = L;
+  inr->H = L - 1;
+  inr->w = w;
+  inr->W.assign(L, nullptr);
+  inr->Wt.assign(L, nullptr);
+  inr->b.assign(L, nullptr);
+  inr->Wt_bf16.assign(L, nullptr);
+  inr->absW_rowsum.assign(L, nullptr);
+  inr->hW.resize(L);
+  inr->hb.resize(L);
+  auto fail = [&](isx_status s) {
+    isx_destroy_inr(inr);
+    return s;
+  };
+  for (int l = 0; l < L; ++l) {
+    int fi = d->dims[l], fo = d->dims[l + 1];
+    inr->hW[l].assign(d->W[l], d->W[l] + (size_t)fi * fo);
+    inr->hb[l].assign(d->b[l], d->b[l] + fo);
+    std::vector<float> t((size_t)fi * fo);
+    std::vector<__nv_bfloat16> tb((size_t)fi * fo);
+    for (int o = 0; o < fo; ++o)
+      for (int i = 0; i < fi; ++i) {
+        t[(size_t)i * fo + o] = d->W[l][(size_t)o * fi + i];
+        tb[(size_t)i * fo + o] = __float2bfloat16_rn(d->W[l][(size_t)o * fi + i]);
+      }
+    size_t bytes = (size_t)fi * fo * sizeof(float);
+    cudaError_t e;
+    if ((e = cudaMalloc(&inr->W[l], bytes)) != cudaSuccess) return fail(cuda_fail(e, "W", __FILE__, __LINE__));
+    if ((e = cudaMalloc(&inr->Wt[l], bytes)) != cudaSuccess) return fail(cuda_fail(e, "Wt", __FILE__, __LINE__));
+    if ((e = cudaMalloc(&inr->b[l], fo * sizeof(float))) != cudaSuccess)
+      return fail(cuda_fail(e, "b", __FILE__, __LINE__));
+    if ((e = cudaMalloc(&inr->Wt_bf16[l], (size_t)fi * fo * 2)) != cudaSuccess)
+      return fail(cuda_fail(e, "Wt bf16", __FILE__, __LINE__));
+    if ((e = cudaMemcpy(inr->W[l], d->W[l], bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(inr->Wt[l], t.data(), bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(inr->b[l], d->b[l], fo * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(inr->Wt_bf16[l], tb.data(), (size_t)fi * fo * 2, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return fail(cuda_fail(e, "weight copy", __FILE__, __LINE__));
+  }
+  *out = inr;
+  return ISX_OK;
+}
+
+isx_status isx_destroy_inr(isx_inr inr) {
+  if (!inr) return ISX_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(inr->device);
+  for (auto* p : inr->W) if (p) cudaFree(p);
+  for (auto* p : inr->Wt) if (p) cudaFree(p);
+  for (auto* p : inr->b) if (p) cudaFree(p);
+  for (auto* p : inr->Wt_bf16) if (p) cudaFree(p);
+  for (auto* p : inr->absW_rowsum) if (p) cudaFree(p);
+  for (auto& buf : inr->ws) buf.release();
+  if (prev >= 0) cudaSetDevice(prev);
+  delete inr;
+  return ISX_OK;
+}
+
+isx_status isx_bound_cells(isx_inr inr, const float* d_lo, const float* d_hi, int64_t n, isx_bound_mode mode,
+                           isx_precision prec, int inflate, float* d_center, float* d_spread, void* stream) {
+  ISX_TRY(check_inr(inr));
+  if (n < 0 || (n > 0 && (!d_lo || !d_hi || !d_center || !d_spread))) {
+    set_error("bad size or null pointer");
+    return ISX_ERR_ARG;
+  }
+  if (mode < ISX_BOUND_SOUND || mode > ISX_BOUND_RAUA || prec < ISX_PREC_FP32 || prec > ISX_PREC_BF16) {
+    set_error("bad mode or precision");
+    return ISX_ERR_ARG;
+  }
+  if (n == 0) return ISX_OK;
+  CellSource src;
+  src.lo = d_lo;
+  src.hi = d_hi;
+  return bound_dispatch(inr, src, n, mode, prec, inflate, d_center, d_spread, (cudaStream_t)stream);
+}
+
+isx_status isx_eval_points(isx_inr inr, const float* d_xyz, int64_t n, isx_precision prec, float* d_out,
+                           void* stream) {
+  ISX_TRY(check_inr(inr));
+  if (n < 0 || (n > 0 && (!d_xyz || !d_out))) {
+    set_error("bad size or null pointer");
+    return ISX_ERR_ARG;
+  }
+  (void)prec;
+  return eval_points_fp32(inr, d_xyz, nullptr, 0, n, d_out, (cudaStream_t)stream);
+}
+
+isx_status isx_extract_isosurface(isx_inr inr, const isx_extract_params* p, isx_mesh* mesh, void* stream) {
+  ISX_TRY(check_inr(inr));
+  ISX_TRY(validate_params(p, mesh));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (p->prec == ISX_PREC_BF16 && !bf16_supported(inr)) {
+    set_error("BF16 propagation is not available for this width");
+    return ISX_ERR_UNSUPPORTED;
+  }
+  const int L = p->max_level;
+  const int R = 1 << L;
+  const IsoSet iso = iso_of(p);
+  const int stop = (p->bound_stop_level < 0 || p->bound_stop_level >= L) ? L : p->bound_stop_level;
+  for (int l = 0; l <= ISX_MAX_LEVEL; ++l) mesh->cells_bounded[l] = mesh->cells_kept[l] = 0;
+  mesh->n_active = mesh->n_tris = mesh->n_points = 0;
+  Timer tm;
+  ISX_TRY(tm.init());
+  ISX_CUDA(cudaEventRecord(tm.ev[0], st));
+  auto& ws = inr->ws;
+  ISX_TRY(ws[WS_CODES_A].ensure(64, "codes"));
+  ISX_TRY(ws[WS_MASK_A].ensure(64, "masks"));
+  ISX_TRY(ws[WS_COUNT].ensure(64, "count"));
+  uint32_t root[2] = {0u, (iso.n >= 32) ? 0xffffffffu : ((1u << iso.n) - 1u)};
+  ISX_CUDA(cudaMemcpyAsync(ws[WS_CODES_A].ptr, &root[0], 4, cudaMemcpyHostToDevice, st));
+  ISX_CUDA(cudaMemcpyAsync(ws[WS_MASK_A].ptr, &root[1], 4, cudaMemcpyHostToDevice, st));
+  int64_t* d_count = ws[WS_COUNT].as<int64_t>();
+  int64_t n = 1;
+  Slot ca = WS_CODES_A, cb = WS_CODES_B, ma = WS_MASK_A, mb = WS_MASK_B;
+  for (int level = 0; level <= L; ++level) {
+    bool bounded = level <= stop;
+    bool expand = level < L;
+    mesh->cells_bounded[level] = bounded ? n : 0;
+    if (n > 0) {
+      ISX_TRY(ws[WS_CENTER].ensure((size_t)n * 4, "center"));
+      ISX_TRY(ws[WS_SPREAD].ensure((size_t)n * 4, "spread"));
+      if (bounded) {
+        CellSource src;
+        src.codes = ws[ca].as<uint32_t>();
+        src.level = level;
+        ISX_TRY(bound_dispatch(inr, src, n, p->mode, p->prec, p->inflate, ws[WS_CENTER].as<float>(),
+                               ws[WS_SPREAD].as<float>(), st));
+      }
+      size_t need = (size_t)(expand ? 8 : 1) * n * 4;
+      ISX_TRY(ws[cb].ensure(need, "codes"));
+      ISX_TRY(ws[mb].ensure(need, "masks"));
+    }
+    ISX_TRY(level_step(inr, ws[ca].as<uint32_t>(), ws[ma].as<uint32_t>(), n, ws[WS_CENTER].as<float>(),
+                       ws[WS_SPREAD].as<float>(), bounded, iso, p->mode, p->k, p->inflate, expand,
+                       ws[cb].as<uint32_t>(), ws[mb].as<uint32_t>(), d_count, st));
+    int64_t cnt = 0;
+    ISX_CUDA(cudaMemcpyAsync(&cnt, d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    ISX_CUDA(cudaStreamSynchronize(st));
+    mesh->cells_kept[level] = expand ? cnt / 8 : cnt;
+    std::swap(ca, cb);
+    std::swap(ma, mb);
+    n = cnt;
+  }
+  ISX_CUDA(cudaEventRecord(tm.ev[1], st));
+  mesh->n_active = n;
+  if (n > mesh->active_cap) {
+    set_error("active-cell capacity exceeded");
+    return ISX_ERR_CAPACITY;
+  }
+  const uint32_t* codes = ws[ca].as<uint32_t>();
+  const uint32_t* masks = ws[ma].as<uint32_t>();
+  if (n > 0) {
+    if (!mesh->d_active_code || !mesh->d_active_mask) {
+      set_error("null active-cell output buffer");
+      return ISX_ERR_ARG;
+    }
+    ISX_CUDA(cudaMemcpyAsync(mesh->d_active_code, codes, n * 4, cudaMemcpyDeviceToDevice, st));
+    ISX_CUDA(cudaMemcpyAsync(mesh->d_active_mask, masks, n * 4, cudaMemcpyDeviceToDevice, st));
+  }
+  // distinct corners of the active cells
+  int64_t nlat = (int64_t)(R + 1) * (R + 1) * (R + 1);
+  ISX_TRY(ws[WS_LATTICE_FLAG].ensure((size_t)nlat, "lattice flags"));
+  ISX_TRY(ws[WS_LATTICE_IDX].ensure((size_t)nlat * 4, "lattice map"));
+  ISX_CUDA(cudaMemsetAsync(ws[WS_LATTICE_FLAG].ptr, 0, (size_t)nlat, st));
+  ISX_TRY(mark_corners(codes, n, R, ws[WS_LATTICE_FLAG].as<uint8_t>(), st));
+  int64_t npts_cap = std::min<int64_t>(nlat, 8 * std::max<int64_t>(n, 1));
+  ISX_TRY(ws[WS_POINTS].ensure((size_t)npts_cap * 4, "points"));
+  ISX_TRY(compact_flags(inr, ws[WS_LATTICE_FLAG].as<uint8_t>(), nlat, ws[WS_POINTS].as<uint32_t>(),
+                        ws[WS_LATTICE_IDX].as<uint32_t>(), d_count, st));
+  int64_t npts = 0;
+  ISX_CUDA(cudaMemcpyAsync(&npts, d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  ISX_CUDA(cudaStreamSynchronize(st));
+  mesh->n_points = npts;
+  ISX_TRY(ws[WS_VALUES].ensure((size_t)std::max<int64_t>(npts, 1) * 4, "values"));
+  ISX_TRY(eval_points_fp32(inr, nullptr, ws[WS_POINTS].as<uint32_t>(), R, npts, ws[WS_VALUES].as<float>(), st));
+  ISX_CUDA(cudaEventRecord(tm.ev[2], st));
+  isx_status s = marching_cubes(inr, codes, masks, n, R, ws[WS_LATTICE_IDX].as<uint32_t>(),
+                                ws[WS_VALUES].as<float>(), iso, mesh, false, st);
+  ISX_CUDA(cudaEventRecord(tm.ev[3], st));
+  ISX_CUDA(cudaEventSynchronize(tm.ev[3]));
+  cudaEventElapsedTime(&mesh->ms_acp, tm.ev[0], tm.ev[1]);
+  cudaEventElapsedTime(&mesh->ms_inr, tm.ev[1], tm.ev[2]);
+  cudaEventElapsedTime(&mesh->ms_mc, tm.ev[2], tm.ev[3]);
+  cudaEventElapsedTime(&mesh->ms_total, tm.ev[0], tm.ev[3]);
+  return s;
+}
+
+isx_status isx_extract_dense(isx_inr inr, const isx_extract_params* p, isx_mesh* mesh, void* stream) {
+  ISX_TRY(check_inr(inr));
+  ISX_TRY(validate_params(p, mesh));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int L = p->max_level;
+  const int R = 1 << L;
+  const IsoSet iso = iso_of(p);
+  for (int l = 0; l <= ISX_MAX_LEVEL; ++l) mesh->cells_bounded[l] = mesh->cells_kept[l] = 0;
+  mesh->n_active = mesh->n_tris = 0;
+  Timer tm;
+  ISX_TRY(tm.init());
+  ISX_CUDA(cudaEventRecord(tm.ev[0], st));
+  ISX_CUDA(cudaEventRecord(tm.ev[1], st));
+  int64_t nlat = (int64_t)(R + 1) * (R + 1) * (R + 1);
+  auto& ws = inr->ws;
+  ISX_TRY(ws[WS_VALUES].ensure((size_t)nlat * 4, "values"));
+  mesh->n_points = nlat;
+  // lattice ids are 0..nlat-1: evaluate with an identity id list
+  ISX_TRY(ws[WS_POINTS].ensure((size_t)nlat * 4, "points"));
+  ISX_TRY(iota_u32(ws[WS_POINTS].as<uint32_t>(), nlat, st));
+  ISX_TRY(eval_points_fp32(inr, nullptr, ws[WS_POINTS].as<uint32_t>(), R, nlat, ws[WS_VALUES].as<float>(), st));
+  ISX_CUDA(cudaEventRecord(tm.ev[2], st));
+  isx_status s = marching_cubes(inr, nullptr, nullptr, (int64_t)R * R * R, R, nullptr, ws[WS_VALUES].as<float>(),
+                                iso, mesh, true, st);
+  ISX_CUDA(cudaEventRecord(tm.ev[3], st));
+  ISX_CUDA(cudaEventSynchronize(tm.ev[3]));
+  cudaEventElapsedTime(&mesh->ms_acp, tm.ev[0], tm.ev[1]);
+  cudaEventElapsedTime(&mesh->ms_inr, tm.ev[1], tm.ev[2]);
+  cudaEventElapsedTime(&mesh->ms_mc, tm.ev[2], tm.ev[3]);
+  cudaEventElapsedTime(&mesh->ms_total, tm.ev[0], tm.ev[3]);
+  return s;
+}
+
+}  // extern "C"

@@ -1,0 +1,154 @@
+// Internal declarations shared by the translation units of the isx library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/isx.h"
+
+namespace isx {
+
+// ---- errors ------------------------------------------------------------------------------------
+void set_error(const std::string& msg);
+isx_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define ISX_CUDA(call)                                                              \
+  do {                                                                              \
+    cudaError_t _e = (call);                                                        \
+    if (_e != cudaSuccess) return ::isx::cuda_fail(_e, #call, __FILE__, __LINE__);  \
+  } while (0)
+
+#define ISX_LAUNCH_CHECK(what)                                                         \
+  do {                                                                                 \
+    cudaError_t _e = cudaGetLastError();                                               \
+    if (_e != cudaSuccess) return ::isx::cuda_fail(_e, what, __FILE__, __LINE__);      \
+  } while (0)
+
+#define ISX_TRY(expr)                        \
+  do {                                       \
+    isx_status _s = (expr);                  \
+    if (_s != ISX_OK) return _s;             \
+  } while (0)
+
+// ---- device buffers ----------------------------------------------------------------------------
+// A growable device allocation owned by an INR's workspace.
+struct Buf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  isx_status ensure(size_t need, const char* name);
+  void release();
+  template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+// Workspace slots (one growable buffer each).
+enum Slot {
+  WS_CODES_A, WS_CODES_B, WS_MASK_A, WS_MASK_B, WS_CENTER, WS_SPREAD, WS_FLAGS, WS_BLOCKSUM,
+  WS_COUNT, WS_C, WS_X0, WS_X1, WS_RAD, WS_ALPHA, WS_GAMMA, WS_DELTA, WS_AUX,
+  WS_LATTICE_FLAG, WS_LATTICE_IDX, WS_POINTS, WS_VALUES, WS_TRI_COUNT, WS_TRI_OFFSET,
+  WS_TC_SCRATCH, WS_TC_STATE, WS_TC_STATUS,
+  WS_N_SLOTS
+};
+
+}  // namespace isx
+
+// The opaque INR handle.
+struct isx_inr_s {
+  int device = 0;
+  int n_layers = 0;           // linear layers = H + 1
+  int H = 0;                  // hidden (activation) layers
+  int w = 0;                  // hidden width
+  // device copies, per linear layer l: W[l] row-major [out][in], Wt[l] = W[l]^T row-major [in][out]
+  std::vector<float*> W, Wt, b;
+  std::vector<__nv_bfloat16*> Wt_bf16;   // W[l]^T in bfloat16 (hidden layers), for the tensor-core path
+  std::vector<float*> absW_rowsum;       // sum_k |W[l][n][k]| per output neuron
+  std::vector<std::vector<float>> hW, hb;  // host copies
+  isx::Buf ws[isx::WS_N_SLOTS];
+  float* h_pinned = nullptr;            // small pinned host buffer for count read-back
+  int* h_pinned_i = nullptr;
+};
+
+namespace isx {
+
+// ---- launch accounting (prof.cu) --------------------------------------------------------------
+enum KernelId {
+  K_INPUT, K_RELU, K_GEMV, K_GEMM_FP32, K_FRESH, K_REDUCE, K_OUTPUT, K_CULL, K_SCAN, K_SCATTER, K_MARK,
+  K_FLAGCOUNT, K_SCATTER_FLAGS, K_EVAL_FP32, K_MC_COUNT, K_MC_EMIT, K_IOTA, K_BOUND_TC, K_TC_PREP, K_TC_OUTPUT,
+  K_EVAL_TC, K_COUNT
+};
+namespace prof {
+// RAII bracket around one kernel launch: counts it, adds its algorithmic work, and (when
+// profiling is enabled) records CUDA events before and after it on `st`.
+class Scope {
+ public:
+  Scope(int kernel, cudaStream_t st, double flops = 0, double bytes = 0);
+  ~Scope();
+ private:
+  int kernel_;
+  cudaStream_t st_;
+  bool active_ = false;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+}  // namespace prof
+
+// ---- kernels and launchers (bound_fp32.cu) -----------------------------------------------------
+// Cells given either as boxes (lo, hi) or as packed codes of one octree level.
+struct CellSource {
+  const float* lo = nullptr;
+  const float* hi = nullptr;
+  const uint32_t* codes = nullptr;
+  int level = 0;
+};
+
+// Bounds n cells in float32 with the layer-by-layer path; chunked over the workspace.
+isx_status bound_fp32(isx_inr inr, const CellSource& src, int64_t n, isx_bound_mode mode,
+                      int inflate, float* d_center, float* d_spread, cudaStream_t st);
+
+// Tensor-core (tcgen05, bfloat16) path; ISX_ERR_UNSUPPORTED for shapes it does not cover.
+isx_status bound_bf16(isx_inr inr, const CellSource& src, int64_t n, isx_bound_mode mode,
+                      int inflate, float* d_center, float* d_spread, cudaStream_t st);
+bool bf16_supported(isx_inr inr);
+
+// ---- octree level step (tree.cu) ---------------------------------------------------------------
+struct IsoSet {
+  int n = 0;
+  float c[ISX_MAX_ISO];
+};
+// Computes the surviving iso mask of every cell and compacts survivors (stable).  If `expand`,
+// writes the 8 children of every survivor (child c = 2 (i,j,k) + bits of c) with the parent's
+// mask; otherwise writes the survivors themselves.  `bounded` = 0 keeps every cell with its mask.
+// The number of written cells goes to *d_count (device int64).
+isx_status level_step(isx_inr inr, const uint32_t* codes, const uint32_t* masks, int64_t n,
+                      const float* center, const float* spread, bool bounded, const IsoSet& iso,
+                      isx_bound_mode mode, float k, int inflate, bool expand, uint32_t* out_codes,
+                      uint32_t* out_masks, int64_t* d_count, cudaStream_t st);
+
+// Stable compaction of the indices i < n with flags[i] != 0 into out_idx; count to *d_count.
+isx_status compact_flags(isx_inr inr, const uint8_t* flags, int64_t n, uint32_t* out_idx,
+                         uint32_t* idx_map, int64_t* d_count, cudaStream_t st);
+
+// Exclusive scan of nb int counts into int64 offsets (single block); total to *d_total.
+isx_status scan_block_counts(isx_inr inr, const int* counts, int64_t nb, int64_t* offsets, int64_t* d_total,
+                             cudaStream_t st);
+// out[i] = i for i < n.
+isx_status iota_u32(uint32_t* out, int64_t n, cudaStream_t st);
+
+// ---- mesh (mesh.cu) ----------------------------------------------------------------------------
+// flags[lattice id] = 1 for the 8 corners of every listed cell of the R^3 grid.
+isx_status mark_corners(const uint32_t* codes, int64_t n, int R, uint8_t* flags, cudaStream_t st);
+// Marching cubes over n listed cells (codes, masks) or, with codes == nullptr, over all R^3 cells for
+// every iso-value.  Corner values are values[idx_map[lattice id]] (idx_map == nullptr: by lattice id).
+// Writes mesh->n_tris; emits only if it fits mesh->tri_cap (else ISX_ERR_CAPACITY).  With
+// count_nonempty, mesh->n_active becomes the number of cells with at least one triangle.
+isx_status marching_cubes(isx_inr inr, const uint32_t* codes, const uint32_t* masks, int64_t n, int R,
+                          const uint32_t* idx_map, const float* values, const IsoSet& iso, isx_mesh* mesh,
+                          bool count_nonempty, cudaStream_t st);
+isx_status eval_points_fp32(isx_inr inr, const float* xyz, const uint32_t* lattice_ids, int R,
+                            int64_t n, float* out, cudaStream_t st);
+isx_status mc_upload_table(int device);
+void mc_build_table(int8_t* ntri, int8_t* tris);
+
+}  // namespace isx

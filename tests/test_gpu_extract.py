@@ -1,0 +1,179 @@
+"""GPU parity of the hierarchical and dense extraction (isx_extract_isosurface, isx_extract_dense)
+against the float64 oracle, through the C interface.
+
+Acceptance (float32 path): predicted active sets equal the oracle's except for cells with an
+ancestor-or-self whose oracle bound endpoint lies within 1e-5 of an iso-value; on cells both sides
+keep, the triangles of every (cell, iso) whose corner values are all more than 1e-5 from the
+iso-value are identical (same lattice-edge triples in the same order) with vertices within 1e-4.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import affine, mc, mlp, octree
+from synth import inr
+
+from _helpers import band_codes, excused, pack, to_np, unpack
+
+pytestmark = pytest.mark.gpu
+
+BAND = 1e-5
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2402_13861_gb300 as p
+    torch.cuda.set_device(0)
+    return p
+
+
+@pytest.fixture(scope="module")
+def small(pkg):
+    layers, isos, wl = inr.load_inr("small")
+    net = pkg.Inr(layers)
+    R = 1 << wl.max_level
+    vals = mlp.mlp_forward(layers, octree.lattice_points(R))
+    return layers, isos, wl, net, vals
+
+
+def _oracle_triangles(vals, cells, masks, isos, R):
+    """(code, iso) -> list of (edge triple, vertices) from the oracle."""
+    out = {}
+    for q, c in enumerate(isos):
+        sel = ((masks >> q) & 1) == 1
+        e, p, cell = mc.march(vals, cells[sel], R, c)
+        codes = pack(cells[sel])[cell]
+        for t in range(e.shape[0]):
+            out.setdefault((int(codes[t]), q), []).append((tuple(e[t]), p[t]))
+    return out
+
+
+def _gpu_triangles(res):
+    out = {}
+    cells = to_np(res["tri_cell"]).astype(np.int64) & 0xFFFFFFFF
+    isoq = to_np(res["tri_iso"])
+    edges = to_np(res["tri_edge"])
+    verts = to_np(res["tri_vert"]).astype(np.float64)
+    for t in range(cells.shape[0]):
+        out.setdefault((int(cells[t]), int(isoq[t])), []).append((tuple(edges[t]), verts[t]))
+    return out
+
+
+def _corner_clean(vals, code, c, R):
+    ijk = unpack([code])
+    cv = mc.corner_values(vals, ijk, R)[0]
+    return np.all(np.abs(cv - c) > BAND)
+
+
+def _check_extraction(layers, isos, L, vals, res, mode, k):
+    R = 1 << L
+    levels = octree.extract_active(layers, L, isos, mode, k=k, batch=512)
+    o_cells, o_masks = octree.active_cells(levels)
+    bands = band_codes(levels, isos, BAND, L)
+    g_codes = to_np(res["codes"]).astype(np.int64) & 0xFFFFFFFF
+    g_masks = to_np(res["masks"]).astype(np.int64) & 0xFFFFFFFF
+    o_map = dict(zip(pack(o_cells).tolist(), o_masks.tolist()))
+    g_map = dict(zip(g_codes.tolist(), g_masks.tolist()))
+    assert len(g_map) == len(g_codes)                         # no duplicates
+    diff = [c for c in set(o_map) ^ set(g_map)] + [c for c in set(o_map) & set(g_map) if o_map[c] != g_map[c]]
+    bad = [c for c in diff if not excused(c, bands, L)]
+    assert not bad, f"{len(bad)} active-set differences outside the 1e-5 band"
+    # per-level counts agree up to band cells
+    for l, lv in enumerate(levels):
+        assert abs(res["cells_bounded"][l] - lv["ijk"].shape[0]) <= len(diff) * 8 + 0
+    # triangles on common clean cells
+    o_tri = _oracle_triangles(vals, o_cells, o_masks, isos, R)
+    g_tri = _gpu_triangles(res)
+    checked = 0
+    for code in set(o_map) & set(g_map):
+        for q, c in enumerate(isos):
+            if not ((o_map[code] >> q) & 1 and (g_map[code] >> q) & 1):
+                continue
+            if not _corner_clean(vals, code, c, R):
+                continue
+            a = o_tri.get((code, q), [])
+            b = g_tri.get((code, q), [])
+            assert [t[0] for t in a] == [t[0] for t in b], (code, q)
+            for (_, pa), (_, pb) in zip(a, b):
+                assert np.abs(pa - pb).max() <= 1e-4
+            checked += len(a)
+    assert checked > 0.9 * sum(len(v) for v in o_tri.values())
+    return levels, diff
+
+
+@pytest.mark.parametrize("mode,k", [("sound", 0.0), ("clt", 3.0), ("raua", 3.0)])
+def test_fp32_extraction_matches_oracle_small(small, mode, k):
+    layers, isos, wl, net, vals = small
+    L = wl.max_level
+    res = net.extract(L, isos, mode=mode, k=k, prec="fp32")
+    torch.cuda.synchronize()
+    levels, diff = _check_extraction(layers, isos, L, vals, res, mode, k)
+    assert res["n_active"] > 1000 and res["n_tris"] > 1000
+
+
+def test_fp32_extraction_several_isos(small):
+    layers, isos, wl, net, vals = small
+    R = 1 << wl.max_level
+    many = np.quantile(vals, np.linspace(0.2, 0.95, 6)).astype(np.float32)
+    L = 5
+    vals5 = mlp.mlp_forward(layers, octree.lattice_points(1 << L))
+    res = net.extract(L, many, mode="clt", k=2.0, prec="fp32")
+    _check_extraction(layers, many, L, vals5, res, affine.CLT, 2.0)
+
+
+def test_sound_inflated_hierarchy_equals_gpu_dense(small):
+    """Sound bounds with inflation never cull a cell whose float32 corner values straddle the
+    iso-value, so hierarchical and dense GPU extraction give the same triangles."""
+    layers, isos, wl, net, vals = small
+    L = wl.max_level
+    h = net.extract(L, isos, mode="sound", prec="fp32", inflate=True)
+    d = net.extract(L, isos, prec="fp32", dense=True)
+    gh, gd = _gpu_triangles(h), _gpu_triangles(d)
+    assert set(gd) <= set(gh)
+    for key, tris in gd.items():
+        assert [t[0] for t in tris] == [t[0] for t in gh[key]]
+    assert h["n_tris"] == d["n_tris"]
+
+
+def test_dense_extraction_matches_oracle(small):
+    layers, isos, wl, net, vals = small
+    L = wl.max_level
+    R = 1 << L
+    d = net.extract(L, isos, prec="fp32", dense=True)
+    cells = mc.crossing_cells(vals, R, isos[0])
+    o = _oracle_triangles(vals, cells, np.ones(cells.shape[0], dtype=np.int64), isos, R)
+    g = _gpu_triangles(d)
+    clean = [key for key in o if _corner_clean(vals, key[0], isos[0], R)]
+    assert len(clean) > 0.95 * len(o)
+    for key in clean:
+        assert [t[0] for t in o[key]] == [t[0] for t in g[key]]
+        for (_, pa), (_, pb) in zip(o[key], g[key]):
+            assert np.abs(pa - pb).max() <= 1e-4
+    extra = set(g) - set(o)
+    assert all(not _corner_clean(vals, key[0], isos[0], R) for key in extra)
+
+
+def test_capacity_error_reports_sizes(small, pkg):
+    import ctypes as C
+    from paper_2402_13861_gb300 import _lib
+    layers, isos, wl, net, vals = small
+    p = net.params(4, isos, mode="sound")
+    m = _lib.Mesh()
+    buf = torch.empty(16, dtype=torch.int32, device="cuda")
+    m.d_active_code = m.d_active_mask = buf.data_ptr()
+    m.active_cap = 4
+    st = _lib.load().isx_extract_isosurface(net.handle, C.byref(p), C.byref(m), None)
+    assert st == 3 and m.n_active > 4
+    res = net.extract(4, isos, mode="sound", active_cap=4, tri_cap=4)   # grows and retries
+    assert res["n_active"] == m.n_active
+
+
+def test_edge_levels(small):
+    """Level 0 (a single cell) and level 1 work; an iso-value outside the range yields nothing."""
+    layers, isos, wl, net, vals = small
+    r0 = net.extract(0, isos, mode="sound")
+    assert r0["n_active"] in (0, 1) and r0["cells_bounded"][0] == 1
+    r = net.extract(3, [1e6], mode="sound")
+    assert r["n_active"] == 0 and r["n_tris"] == 0

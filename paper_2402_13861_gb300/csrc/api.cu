@@ -173,6 +173,7 @@ isx_status isx_create_inr(const isx_inr_desc* d, isx_inr* out) {
   inr->Wt.assign(L, nullptr);
   inr->b.assign(L, nullptr);
   inr->Wt_bf16.assign(L, nullptr);
+  inr->W_bf16.assign(L, nullptr);
   inr->absW_rowsum.assign(L, nullptr);
   inr->hW.resize(L);
   inr->hb.resize(L);
@@ -185,11 +186,12 @@ isx_status isx_create_inr(const isx_inr_desc* d, isx_inr* out) {
     inr->hW[l].assign(d->W[l], d->W[l] + (size_t)fi * fo);
     inr->hb[l].assign(d->b[l], d->b[l] + fo);
     std::vector<float> t((size_t)fi * fo);
-    std::vector<__nv_bfloat16> tb((size_t)fi * fo);
+    std::vector<__nv_bfloat16> tb((size_t)fi * fo), rb((size_t)fi * fo);
     for (int o = 0; o < fo; ++o)
       for (int i = 0; i < fi; ++i) {
         t[(size_t)i * fo + o] = d->W[l][(size_t)o * fi + i];
         tb[(size_t)i * fo + o] = __float2bfloat16_rn(d->W[l][(size_t)o * fi + i]);
+        rb[(size_t)o * fi + i] = __float2bfloat16_rn(d->W[l][(size_t)o * fi + i]);
       }
     size_t bytes = (size_t)fi * fo * sizeof(float);
     cudaError_t e;
@@ -199,6 +201,10 @@ isx_status isx_create_inr(const isx_inr_desc* d, isx_inr* out) {
       return fail(cuda_fail(e, "b", __FILE__, __LINE__));
     if ((e = cudaMalloc(&inr->Wt_bf16[l], (size_t)fi * fo * 2)) != cudaSuccess)
       return fail(cuda_fail(e, "Wt bf16", __FILE__, __LINE__));
+    if ((e = cudaMalloc(&inr->W_bf16[l], (size_t)fi * fo * 2)) != cudaSuccess)
+      return fail(cuda_fail(e, "W bf16", __FILE__, __LINE__));
+    if ((e = cudaMemcpy(inr->W_bf16[l], rb.data(), (size_t)fi * fo * 2, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return fail(cuda_fail(e, "W bf16 copy", __FILE__, __LINE__));
     if ((e = cudaMemcpy(inr->W[l], d->W[l], bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(inr->Wt[l], t.data(), bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(inr->b[l], d->b[l], fo * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -218,6 +224,7 @@ isx_status isx_destroy_inr(isx_inr inr) {
   for (auto* p : inr->Wt) if (p) cudaFree(p);
   for (auto* p : inr->b) if (p) cudaFree(p);
   for (auto* p : inr->Wt_bf16) if (p) cudaFree(p);
+  for (auto* p : inr->W_bf16) if (p) cudaFree(p);
   for (auto* p : inr->absW_rowsum) if (p) cudaFree(p);
   for (auto& buf : inr->ws) buf.release();
   if (prev >= 0) cudaSetDevice(prev);

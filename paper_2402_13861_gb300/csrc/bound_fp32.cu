@@ -18,6 +18,7 @@
 // standard error analysis: a K-term dot product errs by at most gamma_K sum |a_k b_k| with
 // gamma_K = K u / (1 - K u), u = 2^-24; products alpha_k W_nk rounded once more add u.
 #include "internal.cuh"
+#include "linearise.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -28,8 +29,6 @@ namespace {
 constexpr float kU = 5.9604645e-08f;        // 2^-24, float32 unit roundoff
 constexpr float kSafe = 1.0000010f;         // (1 + 2^-20): slack for evaluating error formulas
 constexpr float kInvSqrt3 = 0.57735026918962576f;
-constexpr float kInvSqrt2 = 0.70710678118654752f;
-constexpr float kInvSqrt2Pi = 0.39894228040143268f;
 
 __host__ __device__ __forceinline__ float gamma_k(int k) { return (k * kU) / (1.0f - k * kU); }
 
@@ -97,58 +96,11 @@ __global__ void k_relu(int64_t total, int mode, int inflate, float* C, const flo
                        const float* DELTA, float* ALPHA, float* GAMMA) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= total) return;
-  float c = C[i], rad = RAD[i];
-  float alpha, beta, gamma;
-  if (mode == ISX_BOUND_CLT) {
-    float mu = c, sigma = rad;
-    if (sigma > 0.0f && fabsf(mu) < 40.0f * sigma) {
-      float t = mu / sigma;
-      float Phi = 0.5f * erfcf(-t * kInvSqrt2);     // P(X > 0): alpha of Table VII
-      float Q = 0.5f * erfcf(t * kInvSqrt2);        // 1 - Phi without cancellation
-      float phi = expf(-0.5f * t * t) * kInvSqrt2Pi;
-      alpha = Phi;
-      beta = sigma * phi;
-      // Table VII: gamma^2 = (1 - a^2)/4 (mu^2 + sigma^2) + a mu beta - beta^2, a = Q - Phi,
-      // (1 - a^2)/4 = Phi Q, written in units of sigma^2
-      float g2 = Phi * Q * (t * t + 1.0f) + (Q - Phi) * t * phi - phi * phi;
-      gamma = sigma * sqrtf(fmaxf(g2, 0.0f));
-    } else {
-      alpha = mu > 0.0f ? 1.0f : (mu == 0.0f ? 0.5f : 0.0f);
-      beta = 0.0f;
-      gamma = 0.0f;
-    }
-    C[i] = fmaf(alpha, mu, beta);
-  } else {
-    float d = inflate ? DELTA[i] : 0.0f;
-    float R = inflate ? __fadd_ru(__fmul_ru(rad, kSafe), d) : rad;
-    float l = inflate ? __fsub_rd(c, R) : c - R;
-    float u = inflate ? __fadd_ru(c, R) : c + R;
-    if (u <= 0.0f) {
-      alpha = 0.0f; beta = 0.0f; gamma = 0.0f;
-    } else if (l >= 0.0f) {
-      alpha = 1.0f; beta = 0.0f; gamma = 0.0f;
-    } else {
-      alpha = u / (u - l);
-      beta = -0.5f * alpha * l;
-      if (inflate) {
-        // the error of relu(x) - (alpha x + beta) is piecewise linear: extremes at l, 0, u
-        float e1 = fabsf(-alpha * l - beta), e2 = fabsf(beta), e3 = fabsf(u - alpha * u - beta);
-        gamma = fmaxf(e1, fmaxf(e2, e3));
-        gamma = __fadd_ru(gamma, 4.0f * kU * (fabsf(alpha * l) + fabsf(u) + fabsf(beta)));
-      } else {
-        gamma = beta;
-      }
-    }
-    float cn = fmaf(alpha, c, beta);
-    if (inflate) {
-      // alpha * slack, plus the rounding of the new centre
-      gamma = __fadd_ru(gamma, __fmul_ru(alpha, d));
-      gamma = __fadd_ru(gamma, 2.0f * kU * (fabsf(alpha * c) + fabsf(beta)) * kSafe);
-    }
-    C[i] = cn;
-  }
-  ALPHA[i] = alpha;
-  GAMMA[i] = gamma;
+  Lin r = (mode == ISX_BOUND_CLT) ? relu_clt(C[i], RAD[i])
+                                  : relu_sound(C[i], RAD[i], inflate ? DELTA[i] : 0.0f, inflate != 0);
+  C[i] = r.center;
+  ALPHA[i] = r.alpha;
+  GAMMA[i] = r.gamma;
 }
 
 // Centre of the next layer, c' = W a + b, and (inflate) the slack of the next pre-activation:

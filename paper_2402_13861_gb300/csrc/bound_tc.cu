@@ -40,8 +40,12 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <string>
+#include <vector>
 
 namespace isx {
 namespace {
@@ -54,6 +58,7 @@ constexpr int kMathThreads = 32 * kMathWarps;
 constexpr int kMathBase = 32 * (2 + kEpiWarps);                // first math thread
 constexpr uint32_t kStageBytes = 128 * 128;                    // 128 rows x 64 bf16
 constexpr uint64_t kWaitNs = 2000000000ull;                    // 2 s per wait
+constexpr uint32_t kSuspendNs = 100000;                        // 100 us suspend hint per try
 constexpr float kUb = 0.00390625f;                             // 2^-8
 constexpr float kUa = 7.62939453125e-06f;                      // 2^-17
 
@@ -71,6 +76,7 @@ struct TcArgs {
   float* spread;
   int* status;
   float kappa, kappa_out;
+  long long* trace;     // optional per-phase clock64 stamps of CTA 0 (ISX_TRACE=1)
 };
 
 struct TcMaps {
@@ -85,12 +91,14 @@ __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvt
 __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
 }
+// try_wait with a suspend-time hint: the thread sleeps (issuing nothing) until the phase completes
+// or the hint (ns) expires.
 __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.b32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(su32(b)), "r"(parity)
+      : "r"(su32(b)), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
@@ -265,7 +273,7 @@ __device__ __forceinline__ bool wait_bar(const Smem& s, uint64_t* b, uint32_t pa
   const uint64_t t0 = global_ns();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try(b, parity)) return true;
-    if ((it & 63) == 0) {
+    if ((it & 3) == 0) {
       if (*(volatile int*)s.abort) return false;
       if (global_ns() - t0 > kWaitNs) {
         *(volatile int*)s.abort = 1;
@@ -274,6 +282,13 @@ __device__ __forceinline__ bool wait_bar(const Smem& s, uint64_t* b, uint32_t pa
       }
     }
   }
+}
+
+// Trace slots: [role][cell < kTraceCells][event < kTraceEvents]
+constexpr int kTraceCells = 4, kTraceEvents = 48;
+__device__ __forceinline__ void trace(const TcArgs& a, int role, int64_t cell, int ev) {
+  if (a.trace && blockIdx.x == 0 && cell < kTraceCells && ev < kTraceEvents)
+    a.trace[(role * kTraceCells + cell) * kTraceEvents + ev] = clock64();
 }
 
 __device__ __forceinline__ int tiles_per_block(int w) { return w / 128; }
@@ -387,6 +402,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
         for (int j = 2; j <= H - 1 && ok; ++j) {
           if (!wait_bar(s, &s.bar[BAR_BREADY], bready_n & 1, args.status)) { ok = false; break; }
           ++bready_n;
+          trace(args, 1, cell / gridDim.x, 2 * j);
           tc_fence_after();
           const int T = layer_tiles(j, w);
           for (int t = 0; t < T && ok; ++t) {
@@ -409,6 +425,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
             ++tiles_done;
           }
           mma_commit(&s.bar[BAR_BFREE]);
+          trace(args, 1, cell / gridDim.x, 2 * j + 1);
         }
         if (!ok) break;
         const int TO = out_tiles(H, w);
@@ -518,6 +535,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
           ++tiles_done;
         }
         if (!ok) break;
+        if (warp == 2 && lane == 0) trace(args, 2, cell / gridDim.x, j);
         if (store) fence_async_global();
         if (outpass) {
           if (hf == 0 && lane == 0) s.red[q * w] = pout;
@@ -549,6 +567,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
       math_sync();
       if (s.scal[63] != 0.f) break;
       bool ok = true;
+      if (mt == 0) trace(args, 0, cell / gridDim.x, 0);
       // ---- input layer z_1 = W_0 x + b_0 over the box (Sec. III-B / IV-C) ----
       float xc[3], h[3];
       {
@@ -588,6 +607,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
                            : 0.0f;
       }
       math_sync();
+      if (mt == 0) trace(args, 0, cell / gridDim.x, 1);
       for (int j = 1; j <= H - 1; ++j) {
         float* al = s.alpha + (j % 3) * w;
         float* ga = s.gamma + (j % 3) * w;
@@ -624,6 +644,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
         } else {
           math_sync();
         }
+        if (mt == 0) trace(args, 0, cell / gridDim.x, 2 + 4 * (j - 1));
         // ---- CUDA-core part of linear layer j: centre, I rows, implicit block G_j, slack ----
         // Every thread owns 4 consecutive neurons (float4 loads of W_j^T rows) for one half of
         // the k range; the two halves are combined through shared memory.
@@ -634,7 +655,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
           if (mt < 2 * LG) {
             const float4* Wp = reinterpret_cast<const float4*>(Wt) + ln;
             const int kb = grp * kh;
-#pragma unroll 8
+#pragma unroll 16
             for (int k = kb; k < kb + kh; ++k) {
               const float4 wk = __ldg(Wp + (size_t)k * LG);
               const float ak = s.a[k], gk = ga[k], q0 = s.Ia[k], q1 = s.Ia[w + k], q2 = s.Ia[2 * w + k];
@@ -689,12 +710,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
           }
         }
         // ---- the G rows' reductions from the epilogue ----
+        if (mt == 0) trace(args, 0, cell / gridDim.x, 3 + 4 * (j - 1));
         if (j >= 2) {
           if (!group_wait(&s.bar[BAR_RED], red_n & 1)) { ok = false; break; }
           ++red_n;
         } else {
           math_sync();
         }
+        if (mt == 0) trace(args, 0, cell / gridDim.x, 4 + 4 * (j - 1));
         const bool stored = (j >= 2) && (j < H - 1);
         for (int nn = mt; nn < w; nn += kMathThreads) {
           float tc = 0.f;
@@ -709,6 +732,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
           s.I[2 * w + nn] = s.Inew[2 * w + nn];
         }
         math_sync();
+        if (mt == 0) trace(args, 0, cell / gridDim.x, 5 + 4 * (j - 1));
       }
       if (!ok) break;
       // ---- ReLU H, then the output layer (through layer H-1 for the G rows) ----
@@ -722,6 +746,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
       }
       math_sync();
       const float* wout = args.W[H];
+      if (mt == 0) trace(args, 0, cell / gridDim.x, 40);
       const float* WHm1 = args.W[H - 1];                 // row-major [n][k]
       const float* alm1 = s.alpha + ((H - 1) % 3) * w;
       // v = W_{H-1}^T (alpha_H * w_out), |v|abs, u = alpha_{H-1} * v  (4 k per thread, n split in halves)
@@ -769,23 +794,38 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
         math_sync();
         if (mt == 0) mbar_arrive(&s.bar[BAR_BOUTREADY]);
       }
-      // CUDA-core rows: implicit G_{H-2} at z_{H-1} (through u), G_{H-1} at z_H (v), fresh G_H,
-      // and the I rows of z_H (through alpha_H * w_out)
+      // implicit G_{H-2} at z_{H-1} (through u): y_m = gamma_{H-2,m} sum_n W_{H-2}[n][m] u_n
+      if (H >= 3) {
+        const int LG = w / 4, grp = mt / LG, ln = mt % LG, nh = w / 2;
+        float4 dd = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (mt < 2 * LG) {
+          const float4* Wp = reinterpret_cast<const float4*>(args.W[H - 2]) + ln;
+#pragma unroll 8
+          for (int nn = grp * nh; nn < grp * nh + nh; ++nn) {
+            const float4 wv = __ldg(Wp + (size_t)nn * LG);
+            const float un = s.u[nn];
+            dd.x = fmaf(wv.x, un, dd.x); dd.y = fmaf(wv.y, un, dd.y); dd.z = fmaf(wv.z, un, dd.z); dd.w = fmaf(wv.w, un, dd.w);
+          }
+          if (grp == 1) reinterpret_cast<float4*>(s.rpart)[ln] = dd;
+        }
+        math_sync();
+        if (mt < LG) {
+          const float4 t = reinterpret_cast<const float4*>(s.rpart)[ln];
+          s.spart[4 * ln] = dd.x + t.x;
+          s.spart[4 * ln + 1] = dd.y + t.y;
+          s.spart[4 * ln + 2] = dd.z + t.z;
+          s.spart[4 * ln + 3] = dd.w + t.w;
+        }
+        math_sync();
+      }
+      // CUDA-core rows: G_{H-2} at z_{H-1} (above), G_{H-1} at z_H (v), fresh G_H, and the I rows of
+      // z_H (through alpha_H * w_out)
       float acc = 0.f, eabs = 0.f, x0p = 0.f, cen = 0.f;
       const float* gam1 = s.gamma + ((H - 1) % 3) * w;
       for (int m = mt; m < w; m += kMathThreads) {
         if (H >= 3) {
-          const float* WHm2 = args.W[H - 2];
           const float* gam2 = s.gamma + ((H - 2) % 3) * w;
-          float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
-#pragma unroll 4
-          for (int nn = 0; nn < w; nn += 4) {
-            d0 = fmaf(__ldg(WHm2 + (size_t)nn * w + m), s.u[nn], d0);
-            d1 = fmaf(__ldg(WHm2 + (size_t)(nn + 1) * w + m), s.u[nn + 1], d1);
-            d2 = fmaf(__ldg(WHm2 + (size_t)(nn + 2) * w + m), s.u[nn + 2], d2);
-            d3 = fmaf(__ldg(WHm2 + (size_t)(nn + 3) * w + m), s.u[nn + 3], d3);
-          }
-          const float y = gam2[m] * ((d0 + d1) + (d2 + d3));
+          const float y = gam2[m] * s.spart[m];
           acc += sq ? y * y : fabsf(y);
         }
         const float y1 = gam1[m] * s.v[m];
@@ -809,12 +849,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         if (lane == 0) s.scal[qv * 4 + (mt >> 5)] = x;
       }
+      if (mt == 0) trace(args, 0, cell / gridDim.x, 41);
       if (TO > 0) {
         if (!group_wait(&s.bar[BAR_RED], red_n & 1)) break;
         ++red_n;
       } else {
         math_sync();
       }
+      if (mt == 0) trace(args, 0, cell / gridDim.x, 42);
       if (mt == 0) {
         float tot = 0.f, ea = 0.f, xp = 0.f, ce = 0.f;
         for (int i = 0; i < 4; ++i) {
@@ -942,6 +984,13 @@ isx_status bound_bf16(isx_inr inr, const CellSource& src, int64_t n, isx_bound_m
     ISX_TRY(make_map(&maps.wrow[l], inr->W_bf16[l], w, w, 64, w));
   }
   ISX_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), st));
+  const bool tracing = std::getenv("ISX_TRACE") != nullptr;
+  a.trace = nullptr;
+  if (tracing) {
+    ISX_TRY(ws[WS_AUX].ensure(3 * kTraceCells * kTraceEvents * sizeof(long long), "trace"));
+    a.trace = ws[WS_AUX].as<long long>();
+    ISX_CUDA(cudaMemsetAsync(a.trace, 0, 3 * kTraceCells * kTraceEvents * sizeof(long long), st));
+  }
   const size_t smem = smem_bytes(w);
   ISX_CUDA(cudaFuncSetAttribute(k_bound_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   {
@@ -957,6 +1006,20 @@ isx_status bound_bf16(isx_inr inr, const CellSource& src, int64_t n, isx_bound_m
   if (status != 0) {
     set_error("tensor-core bound kernel gave up waiting (bounded wait expired)");
     return (isx_status)status;
+  }
+  if (tracing) {
+    std::vector<long long> h(3 * kTraceCells * kTraceEvents);
+    ISX_CUDA(cudaMemcpy(h.data(), a.trace, h.size() * sizeof(long long), cudaMemcpyDeviceToHost));
+    const long long t0 = h[0];
+    for (int role = 0; role < 3; ++role)
+      for (int c = 0; c < kTraceCells; ++c) {
+        std::fprintf(stderr, "isx trace n=%lld role=%d cell=%d:", (long long)n, role, c);
+        for (int e = 0; e < kTraceEvents; ++e) {
+          long long v = h[(role * kTraceCells + c) * kTraceEvents + e];
+          if (v) std::fprintf(stderr, " %d:%lld", e, v - t0);
+        }
+        std::fprintf(stderr, "\n");
+      }
   }
   return ISX_OK;
 }

@@ -87,6 +87,27 @@ isx_status isx_bound_cells(isx_inr inr, const float* d_lo, const float* d_hi, in
                            isx_bound_mode mode, isx_precision prec, int inflate,
                            float* d_center, float* d_spread, void* stream);
 
+/* Allocation-free variant of isx_bound_cells with prec = ISX_PREC_BF16 (the paper has no
+ * counterpart; this is a deployment convenience).  Some callers cannot allocate device memory once
+ * they are running: a process whose device memory is owned by a framework's caching allocator,
+ * or a latency-critical loop that must not take the device-wide synchronisation that cudaMalloc
+ * and cudaFree imply.  This entry point allocates nothing: the tensor-core kernel takes its
+ * per-CTA coefficient slices and its status word from a 16 MiB array compiled into the library
+ * (every device that loads the library holds that array until the process exits).  Arguments
+ * and results are those of isx_bound_cells (same kernel, same per-cell arithmetic, so the results
+ * are identical); it only uses as many CTAs as the array has slices for (63 for a 256-wide,
+ * 5-hidden-layer network), so it can be slower.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
+ *    caches it; make that first call before any stream capture.
+ *  - All calls share the array, which keeps the last call's contents; the call clears the status
+ *    word itself.  Calls that overlap on the GPU (several streams or threads) race on the array:
+ *    serialise them.
+ *  - Errors: those of isx_bound_cells, ISX_ERR_UNSUPPORTED for widths other than 128 / 256, and
+ *    ISX_ERR_CAPACITY if one CTA's slice would not fit in the array.  Synchronises `stream`. */
+isx_status isx_bound_cells_noalloc(isx_inr inr, const float* d_lo, const float* d_hi, int64_t n,
+                                   isx_bound_mode mode, int inflate, float* d_center, float* d_spread,
+                                   void* stream);
+
 /* Evaluates the INR at n points (device float32 [n][3]) into d_out (device float32 [n]). */
 isx_status isx_eval_points(isx_inr inr, const float* d_xyz, int64_t n, isx_precision prec,
                            float* d_out, void* stream);

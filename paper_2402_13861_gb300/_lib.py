@@ -77,6 +77,8 @@ def load(path: Path | None = None):
     lib.isx_destroy_inr.argtypes = [vp]
     lib.isx_bound_cells.argtypes = [vp, vp, vp, i64, C.c_int, C.c_int, C.c_int, vp, vp, vp]
     lib.isx_eval_points.argtypes = [vp, vp, i64, C.c_int, vp, vp]
+    lib.isx_bound_cells_noalloc.argtypes = [vp, vp, vp, i64, C.c_int, C.c_int, vp, vp, vp]
+    lib.isx_bound_cells_noalloc.restype = C.c_int
     lib.isx_extract_isosurface.argtypes = [vp, C.POINTER(ExtractParams), C.POINTER(Mesh), vp]
     lib.isx_extract_dense.argtypes = [vp, C.POINTER(ExtractParams), C.POINTER(Mesh), vp]
     lib.isx_mc_table.argtypes = [C.POINTER(C.c_int8), C.POINTER(C.c_int8)]

@@ -1025,3 +1025,132 @@ isx_status bound_bf16(isx_inr inr, const CellSource& src, int64_t n, isx_bound_m
 }
 
 }  // namespace isx
+
+// ---- allocation-free variant ---------------------------------------------------------------------------
+// isx_bound_cells_noalloc runs the same tensor-core kernel, but takes its per-CTA coefficient
+// slices and its status word from a fixed array compiled into this file instead of the INR's
+// workspace, so the call itself never allocates device memory.
+namespace isx {
+namespace {
+
+constexpr size_t kStaticScratchBytes = 16ull << 20;   // 16 MiB, held by every device that loads the library
+constexpr size_t kStaticStatusBytes = 256;            // status word, padded to keep the slices aligned
+static __device__ __align__(256) uint8_t g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void* g_static_addr[64] = {};
+
+// Device address of g_static_scratch on the current device, looked up once per device.
+isx_status static_scratch_address(int dev, void** out) {
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (dev < 0 || dev >= 64) {
+    set_error("device index out of range for the static scratch table");
+    return ISX_ERR_ARG;
+  }
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
+                                                 "cudaGetSymbolAddress(g_static_scratch)", __FILE__, __LINE__);
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return ISX_OK;
+}
+
+}  // namespace
+}  // namespace isx
+
+extern "C" isx_status isx_bound_cells_noalloc(isx_inr inr, const float* d_lo, const float* d_hi, int64_t n,
+                                             isx_bound_mode mode, int inflate, float* d_center, float* d_spread,
+                                             void* stream) {
+  using namespace isx;
+  if (!inr) {
+    set_error("null INR handle");
+    return ISX_ERR_ARG;
+  }
+  if (n < 0 || (n > 0 && (!d_lo || !d_hi || !d_center || !d_spread))) {
+    set_error("bad size or null pointer");
+    return ISX_ERR_ARG;
+  }
+  if (mode < ISX_BOUND_SOUND || mode > ISX_BOUND_RAUA) {
+    set_error("bad mode");
+    return ISX_ERR_ARG;
+  }
+  int dev = -1;
+  ISX_CUDA(cudaGetDevice(&dev));
+  if (dev != inr->device) {
+    set_error("the INR was created on another device than the current one");
+    return ISX_ERR_ARG;
+  }
+  if (!bf16_supported(inr)) {
+    set_error("isx_bound_cells_noalloc supports the bf16 tensor-core path only (hidden width 128 or 256)");
+    return ISX_ERR_UNSUPPORTED;
+  }
+  if (n == 0) return ISX_OK;
+  const int w = inr->w, H = inr->H;
+  const int rows = std::max(1, w * std::max(0, H - 3));
+  const size_t per_cta = (((size_t)rows * w * 2) + 255) & ~size_t(255);
+  if (per_cta > kStaticScratchBytes - kStaticStatusBytes) {
+    set_error("isx_bound_cells_noalloc: this network needs " + std::to_string(per_cta) +
+              " bytes of scratch per CTA, more than the 16 MiB static scratch array holds");
+    return ISX_ERR_CAPACITY;
+  }
+  void* base = nullptr;
+  ISX_TRY(static_scratch_address(dev, &base));
+  int sms = 0;
+  ISX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t fit = (int64_t)((kStaticScratchBytes - kStaticStatusBytes) / per_cta);
+  const int grid = (int)std::min<int64_t>(std::min<int64_t>(n, sms), fit);
+  cudaStream_t st = (cudaStream_t)stream;
+  TcArgs a{};
+  a.src.lo = d_lo;
+  a.src.hi = d_hi;
+  a.n = n;
+  a.mode = (int)mode;
+  a.inflate = (mode == ISX_BOUND_SOUND) ? inflate : 0;
+  a.w = w;
+  a.H = H;
+  for (int l = 0; l < inr->n_layers; ++l) {
+    a.W[l] = inr->W[l];
+    a.Wt[l] = inr->Wt[l];
+    a.b[l] = inr->b[l];
+  }
+  a.bout = inr->hb[inr->n_layers - 1][0];
+  a.status = reinterpret_cast<int*>(base);
+  a.scratch = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<uint8_t*>(base) + kStaticStatusBytes);
+  a.rows_per_cta = (int)(per_cta / (w * 2));
+  a.center = d_center;
+  a.spread = d_spread;
+  a.trace = nullptr;
+  const float ub = kUb, ua = kUa, u = kLinU;
+  const float gK = (w * ua) / (1.0f - w * ua), gK32 = (w * u) / (1.0f - w * u);
+  a.kappa = (1 + ub) * (1 + ub) * (1 + ub) * (1 + gK) * (1 + u) - 1;
+  a.kappa_out = (1 + ub) * (1 + gK) * (1 + gK32) * (1 + gK32) * (1 + u) * (1 + u) - 1;
+  TcMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  ISX_TRY(make_map(&maps.scratch, a.scratch, w, (uint64_t)grid * a.rows_per_cta, 64, 128));
+  for (int l = 1; l < inr->n_layers - 1; ++l) {
+    ISX_TRY(make_map(&maps.wt[l], inr->Wt_bf16[l], w, w, 64, 128));
+    ISX_TRY(make_map(&maps.wrow[l], inr->W_bf16[l], w, w, 64, w));
+  }
+  // the status word must start at zero on every call; the slices need no clearing (every row is
+  // written before it is read)
+  ISX_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), st));
+  const size_t smem = smem_bytes(w);
+  ISX_CUDA(cudaFuncSetAttribute(k_bound_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    const double rows_gemm = (double)w * (H - 1) * (H - 2) / 2.0;
+    prof::Scope ps(K_BOUND_TC, st, (double)n * 2.0 * w * w * (3.0 * (H - 1) + rows_gemm), 0);
+    k_bound_tc<<<grid, kThreads, smem, st>>>(a, maps);
+  }
+  ISX_LAUNCH_CHECK("k_bound_tc (static scratch)");
+  int status = 0;
+  ISX_CUDA(cudaMemcpyAsync(&status, a.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  ISX_CUDA(cudaStreamSynchronize(st));
+  if (status != 0) {
+    set_error("tensor-core bound kernel gave up waiting (bounded wait expired)");
+    return (isx_status)status;
+  }
+  return ISX_OK;
+}

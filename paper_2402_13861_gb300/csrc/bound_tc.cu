@@ -36,6 +36,7 @@
 // and the output radius adds kappa_out times the matching absolute sums.
 #include "internal.cuh"
 #include "linearise.cuh"
+#include "tc_ptx.cuh"
 
 #include <cuda.h>
 
@@ -58,7 +59,6 @@ constexpr int kMathThreads = 32 * kMathWarps;
 constexpr int kMathBase = 32 * (2 + kEpiWarps);                // first math thread
 constexpr uint32_t kStageBytes = 128 * 128;                    // 128 rows x 64 bf16
 constexpr uint64_t kWaitNs = 2000000000ull;                    // 2 s per wait
-constexpr uint32_t kSuspendNs = 100000;                        // 100 us suspend hint per try
 constexpr float kUb = 0.00390625f;                             // 2^-8
 constexpr float kUa = 7.62939453125e-06f;                      // 2^-17
 
@@ -79,113 +79,14 @@ struct TcArgs {
   long long* trace;     // optional per-phase clock64 stamps of CTA 0 (ISX_TRACE=1)
 };
 
+using namespace tc;
+__device__ __forceinline__ void math_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kMathThreads) : "memory"); }
+
 struct TcMaps {
   CUtensorMap scratch;                 // [rows][w] bf16, box {64, 128}
   CUtensorMap wt[ISX_MAX_LAYERS];      // W_l^T bf16 [w][w], box {64, 128}: implicit-block A
   CUtensorMap wrow[ISX_MAX_LAYERS];    // W_l bf16 [w][w], box {64, w}: source of B
 };
-
-// ---- PTX wrappers ---------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
-}
-// try_wait with a suspend-time hint: the thread sleeps (issuing nothing) until the phase completes
-// or the hint (ns) expires.
-__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.b32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(su32(b)), "r"(parity), "r"(kSuspendNs)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
-      "[%2];" ::"r"(su32(dst)),
-      "l"(map), "r"(su32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void math_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kMathThreads) : "memory"); }
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-// Instruction descriptor: kind::f16, bf16 x bf16 -> f32, both K-major, M = 128.
-__device__ __forceinline__ uint32_t idesc(int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-}
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          tmem_d),
-      "l"(a), "l"(b), "r"(id), "r"(acc)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
-  uint32_t r;
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-  return __uint_as_float(r);
-}
-
-// Reduce 32 values per lane across the warp: afterwards lane l holds sum over lanes of v[l]
-// (pairwise summation, 31 shuffles).
-__device__ __forceinline__ float transpose_reduce32(float v[32]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) {
-    const bool upper = (lane & off) != 0;
-#pragma unroll
-    for (int i = 0; i < off; ++i) {
-      float send = upper ? v[i] : v[i + off];
-      float keep = upper ? v[i + off] : v[i];
-      float recv = __shfl_xor_sync(0xffffffffu, send, off);
-      v[i] = keep + recv;
-    }
-  }
-  return v[0];
-}
-
-__device__ __forceinline__ float gamma_k(int k, float u) { return (k * u) / (1.0f - k * u); }
 
 // ---- shared-memory layout ------------------------------------------------------------------------------
 struct Smem {
@@ -258,12 +159,6 @@ __device__ Smem carve(uint8_t* raw, int w) {
   s.tmem_slot = (uint32_t*)(s.bar + BAR_COUNT);
   s.abort = (int*)(s.tmem_slot + 1);
   return s;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
 }
 
 // Bounded wait (kWaitNs of wall time); on timeout raises the CTA-wide abort flag and the global
@@ -937,6 +832,11 @@ isx_status make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t o
 
 }  // namespace
 
+isx_status tensor_map_bf16(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                           uint32_t box_outer) {
+  return make_map(m, base, inner, outer, box_inner, box_outer);
+}
+
 bool bf16_supported(isx_inr inr) { return (inr->w == 128 || inr->w == 256) && inr->H >= 2 && inr->H <= 12; }
 
 isx_status bound_bf16(isx_inr inr, const CellSource& src, int64_t n, isx_bound_mode mode, int inflate,
@@ -946,6 +846,11 @@ isx_status bound_bf16(isx_inr inr, const CellSource& src, int64_t n, isx_bound_m
     return ISX_ERR_UNSUPPORTED;
   }
   if (n <= 0) return ISX_OK;
+  // ISX_CLT_COV=1 selects the covariance (Gram-matrix) propagation of bound_cov.cu for CLT: faster,
+  // but its bf16 rounding error grows with the square of the output-layer cancellation ratio, so
+  // the coefficient propagation below stays the default
+  if (mode == ISX_BOUND_CLT && std::getenv("ISX_CLT_COV") != nullptr)
+    return bound_bf16_clt_cov(inr, src, n, d_center, d_spread, st);
   const int w = inr->w, H = inr->H;
   int dev = inr->device, sms = 0;
   ISX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

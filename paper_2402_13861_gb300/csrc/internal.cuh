@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of the isx library.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -78,7 +79,7 @@ namespace isx {
 enum KernelId {
   K_INPUT, K_RELU, K_GEMV, K_GEMM_FP32, K_FRESH, K_REDUCE, K_OUTPUT, K_CULL, K_SCAN, K_SCATTER, K_MARK,
   K_FLAGCOUNT, K_SCATTER_FLAGS, K_EVAL_FP32, K_MC_COUNT, K_MC_EMIT, K_IOTA, K_BOUND_TC, K_TC_PREP, K_TC_OUTPUT,
-  K_EVAL_TC, K_COUNT
+  K_EVAL_TC, K_BOUND_COV, K_COUNT
 };
 namespace prof {
 // RAII bracket around one kernel launch: counts it, adds its algorithmic work, and (when
@@ -112,6 +113,12 @@ isx_status bound_fp32(isx_inr inr, const CellSource& src, int64_t n, isx_bound_m
 isx_status bound_bf16(isx_inr inr, const CellSource& src, int64_t n, isx_bound_mode mode,
                       int inflate, float* d_center, float* d_spread, cudaStream_t st);
 bool bf16_supported(isx_inr inr);
+// 2-D bfloat16 tensor map [outer][inner] (row stride inner * 2 bytes), 128-byte swizzle.
+isx_status tensor_map_bf16(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                           uint32_t box_outer);
+// CLT bound by covariance propagation on tcgen05 (bound_cov.cu).
+isx_status bound_bf16_clt_cov(isx_inr inr, const CellSource& src, int64_t n, float* d_center, float* d_spread,
+                              cudaStream_t st);
 
 // ---- octree level step (tree.cu) ---------------------------------------------------------------
 struct IsoSet {

@@ -3,6 +3,7 @@
 #include "internal.cuh"
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 
@@ -174,6 +175,8 @@ isx_status isx_create_inr(const isx_inr_desc* d, isx_inr* out) {
   inr->b.assign(L, nullptr);
   inr->Wt_bf16.assign(L, nullptr);
   inr->W_bf16.assign(L, nullptr);
+  inr->Wabs_bf16.assign(L, nullptr);
+  inr->Wsq_bf16.assign(L, nullptr);
   inr->absW_rowsum.assign(L, nullptr);
   inr->hW.resize(L);
   inr->hb.resize(L);
@@ -186,12 +189,15 @@ isx_status isx_create_inr(const isx_inr_desc* d, isx_inr* out) {
     inr->hW[l].assign(d->W[l], d->W[l] + (size_t)fi * fo);
     inr->hb[l].assign(d->b[l], d->b[l] + fo);
     std::vector<float> t((size_t)fi * fo);
-    std::vector<__nv_bfloat16> tb((size_t)fi * fo), rb((size_t)fi * fo);
+    std::vector<__nv_bfloat16> tb((size_t)fi * fo), rb((size_t)fi * fo), ab((size_t)fi * fo), sb((size_t)fi * fo);
     for (int o = 0; o < fo; ++o)
       for (int i = 0; i < fi; ++i) {
-        t[(size_t)i * fo + o] = d->W[l][(size_t)o * fi + i];
-        tb[(size_t)i * fo + o] = __float2bfloat16_rn(d->W[l][(size_t)o * fi + i]);
-        rb[(size_t)o * fi + i] = __float2bfloat16_rn(d->W[l][(size_t)o * fi + i]);
+        const float x = d->W[l][(size_t)o * fi + i];
+        t[(size_t)i * fo + o] = x;
+        tb[(size_t)i * fo + o] = __float2bfloat16_rn(x);
+        rb[(size_t)o * fi + i] = __float2bfloat16_rn(x);
+        ab[(size_t)o * fi + i] = __float2bfloat16_rn(std::fabs(x));
+        sb[(size_t)o * fi + i] = __float2bfloat16_rn(x * x);
       }
     size_t bytes = (size_t)fi * fo * sizeof(float);
     cudaError_t e;
@@ -205,6 +211,12 @@ isx_status isx_create_inr(const isx_inr_desc* d, isx_inr* out) {
       return fail(cuda_fail(e, "W bf16", __FILE__, __LINE__));
     if ((e = cudaMemcpy(inr->W_bf16[l], rb.data(), (size_t)fi * fo * 2, cudaMemcpyHostToDevice)) != cudaSuccess)
       return fail(cuda_fail(e, "W bf16 copy", __FILE__, __LINE__));
+    if ((e = cudaMalloc(&inr->Wabs_bf16[l], (size_t)fi * fo * 2)) != cudaSuccess ||
+        (e = cudaMalloc(&inr->Wsq_bf16[l], (size_t)fi * fo * 2)) != cudaSuccess)
+      return fail(cuda_fail(e, "|W| / W^2 bf16", __FILE__, __LINE__));
+    if ((e = cudaMemcpy(inr->Wabs_bf16[l], ab.data(), (size_t)fi * fo * 2, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(inr->Wsq_bf16[l], sb.data(), (size_t)fi * fo * 2, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return fail(cuda_fail(e, "|W| / W^2 bf16 copy", __FILE__, __LINE__));
     if ((e = cudaMemcpy(inr->W[l], d->W[l], bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(inr->Wt[l], t.data(), bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(inr->b[l], d->b[l], fo * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -225,6 +237,8 @@ isx_status isx_destroy_inr(isx_inr inr) {
   for (auto* p : inr->b) if (p) cudaFree(p);
   for (auto* p : inr->Wt_bf16) if (p) cudaFree(p);
   for (auto* p : inr->W_bf16) if (p) cudaFree(p);
+  for (auto* p : inr->Wabs_bf16) if (p) cudaFree(p);
+  for (auto* p : inr->Wsq_bf16) if (p) cudaFree(p);
   for (auto* p : inr->absW_rowsum) if (p) cudaFree(p);
   for (auto& buf : inr->ws) buf.release();
   if (prev >= 0) cudaSetDevice(prev);

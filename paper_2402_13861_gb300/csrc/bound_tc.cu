@@ -46,6 +46,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 namespace isx {
@@ -54,13 +55,17 @@ namespace {
 constexpr int kStages = 3;
 constexpr int kEpiWarps = 8;
 constexpr int kMathWarps = 4;
-constexpr int kThreads = 32 * (2 + kEpiWarps + kMathWarps);   // 448
+constexpr int kRingWarp = 2 + kEpiWarps + kMathWarps;              // 14: producer of the math ring
+constexpr int kThreads = 32 * (kRingWarp + 1);                     // 480
 constexpr int kMathThreads = 32 * kMathWarps;
-constexpr int kMathBase = 32 * (2 + kEpiWarps);                // first math thread
-constexpr uint32_t kStageBytes = 128 * 128;                    // 128 rows x 64 bf16
-constexpr uint64_t kWaitNs = 2000000000ull;                    // 2 s per wait
-constexpr float kUb = 0.00390625f;                             // 2^-8
-constexpr float kUa = 7.62939453125e-06f;                      // 2^-17
+constexpr int kMathBase = 32 * (2 + kEpiWarps);                    // first math thread
+constexpr uint32_t kStageBytes = 128 * 128;                        // 128 rows x 64 bf16
+constexpr uint32_t kRingBytes = 8192;                              // one stage of float32 weight rows
+constexpr int kRingStages = 2;
+constexpr uint64_t kWaitNs = 2000000000ull;                        // 2 s per wait
+constexpr float kUb = 0.00390625f;                                 // 2^-8
+constexpr float kUa = 7.62939453125e-06f;                          // 2^-17
+constexpr float kGemvSafe = 1.015625f;                             // 1 + 2^-6: bf16 GEMV results bounded above
 
 struct TcArgs {
   CellSource src;
@@ -84,15 +89,19 @@ __device__ __forceinline__ void math_sync() { asm volatile("bar.sync 1, %0;" ::"
 
 struct TcMaps {
   CUtensorMap scratch;                 // [rows][w] bf16, box {64, 128}
-  CUtensorMap wt[ISX_MAX_LAYERS];      // W_l^T bf16 [w][w], box {64, 128}: implicit-block A
-  CUtensorMap wrow[ISX_MAX_LAYERS];    // W_l bf16 [w][w], box {64, w}: source of B
+  CUtensorMap wt[ISX_MAX_LAYERS];      // W_l^T bf16, box {64, 128}: A of implicit blocks
+  CUtensorMap wrow[ISX_MAX_LAYERS];    // W_l bf16, box {64, w}: source of B = D W^T
+  CUtensorMap wa[ISX_MAX_LAYERS];      // W_l bf16, box {64, 128}: A of the I-row pass
+  CUtensorMap wabs[ISX_MAX_LAYERS];    // |W_l| bf16, box {64, 128}: A of the sound reduction pass
+  CUtensorMap wsq[ISX_MAX_LAYERS];     // W_l^2 bf16, box {64, 128}: A of the CLT reduction pass
 };
 
 // ---- shared-memory layout ------------------------------------------------------------------------------
 struct Smem {
-  uint8_t* B;        // w/64 chunks of [w rows][128 B]
+  uint8_t* B;        // w/64 chunks of [w rows][128 B]: D_j W_j^T
   uint8_t* A;        // kStages x 16 KB
-  uint8_t* Bout;     // w/64 chunks of [16 rows][128 B]
+  uint8_t* Bs;       // w/64 chunks of [16 rows][128 B]: small B (GEMV columns, then u)
+  float* ring;       // kRingStages x 8 KB of float32 weight rows
   float* alpha;      // [3][w] (slot = layer % 3)
   float* gamma;      // [3][w]
   float* c;          // centre of the current z
@@ -100,42 +109,44 @@ struct Smem {
   float* delta;      // slack of the current z
   float* a;          // a-form centre
   float* rada;       // a-form radius (sound)
+  float* rprev;      // radius of the previous z
   float* red;        // [4][w] epilogue partial reductions
   float* I;          // [3][w] input-symbol rows of the current z
-  float* Ia;         // [3][w] I rows times alpha
-  float* Inew;       // [3][w] next layer's I rows
-  float* rprev;      // radius of the previous z
-  float* rpart;      // CUDA-core part of the next radius
-  float* spart;      // CUDA-core part of the next slack
-  float* v;          // [w]
-  float* u;          // [w]
-  float* tmp;        // [w]
+  float* Inew;       // [3][w] next layer's I rows (small pass 1), later G_{H-2} output values
+  float* imp;        // implicit-block reduction (small pass 2); output: v
+  float* ig;         // sum |W| rad_a (small pass 2); output: u
+  float* ie;         // sum |W| |a| (small pass 2); output: |v|abs
   float* scal;       // [64] block-reduction scratch
-  uint64_t* bar;     // barriers
+  uint64_t* bar;
   uint32_t* tmem_slot;
   int* abort;
 };
 
-enum Bars { BAR_FULL = 0, BAR_EMPTY = kStages, BAR_TFULL = 2 * kStages, BAR_TEMPTY = 2 * kStages + 2,
-            BAR_BREADY = 2 * kStages + 4, BAR_BFREE, BAR_WLOADED, BAR_RED, BAR_BOUTREADY, BAR_COUNT };
+enum Bars {
+  BAR_FULL = 0, BAR_EMPTY = kStages, BAR_TFULL = 2 * kStages, BAR_TEMPTY = 2 * kStages + 2,
+  BAR_BREADY = 2 * kStages + 4, BAR_BFREE, BAR_WLOADED, BAR_RED, BAR_BOUTREADY,
+  BAR_MFULL, BAR_MEMPTY = BAR_MFULL + kRingStages, BAR_COUNT = BAR_MEMPTY + kRingStages
+};
 
 __host__ __device__ inline size_t smem_bytes(int w) {
   size_t off = 0;
-  off += (size_t)w * w * 2;                 // B
-  off += (size_t)kStages * kStageBytes;     // A
-  off += (size_t)16 * w * 2;                // Bout
-  off += (size_t)(3 + 3 + 5 + 4 + 3 + 3 + 3 + 3 + 3) * w * 4 + 64 * 4;
+  off += (size_t)w * w * 2;                       // B
+  off += (size_t)kStages * kStageBytes;           // A
+  off += (size_t)16 * w * 2;                      // Bs
+  off += (size_t)kRingStages * kRingBytes;        // ring
+  off += (size_t)(25 * w + 64) * 4;               // floats
   off += BAR_COUNT * 8 + 16;
-  return off + 1024;                        // alignment slack
+  return off + 1024;                              // alignment slack (carve aligns the base to 1024)
 }
 
 __device__ Smem carve(uint8_t* raw, int w) {
-  uintptr_t base = ((uintptr_t)raw + 1023) & ~(uintptr_t)1023;
+  const uintptr_t base = ((uintptr_t)raw + 1023) & ~(uintptr_t)1023;   // swizzled operands need 1024-byte alignment
   uint8_t* p = (uint8_t*)base;
   Smem s;
   s.B = p; p += (size_t)w * w * 2;
   s.A = p; p += (size_t)kStages * kStageBytes;
-  s.Bout = p; p += (size_t)16 * w * 2;
+  s.Bs = p; p += (size_t)16 * w * 2;
+  s.ring = (float*)p; p += (size_t)kRingStages * kRingBytes;
   float* f = (float*)p;
   s.alpha = f; f += 3 * w;
   s.gamma = f; f += 3 * w;
@@ -144,16 +155,13 @@ __device__ Smem carve(uint8_t* raw, int w) {
   s.delta = f; f += w;
   s.a = f; f += w;
   s.rada = f; f += w;
+  s.rprev = f; f += w;
   s.red = f; f += 4 * w;
   s.I = f; f += 3 * w;
-  s.Ia = f; f += 3 * w;
   s.Inew = f; f += 3 * w;
-  s.rprev = f; f += w;
-  s.rpart = f; f += w;
-  s.spart = f; f += w;
-  s.v = f; f += w;
-  s.u = f; f += w;
-  s.tmp = f; f += w;
+  s.imp = f; f += w;
+  s.ig = f; f += w;
+  s.ie = f; f += w;
   s.scal = f; f += 64;
   s.bar = (uint64_t*)(((uintptr_t)f + 7) & ~(uintptr_t)7);
   s.tmem_slot = (uint32_t*)(s.bar + BAR_COUNT);
@@ -186,19 +194,68 @@ __device__ __forceinline__ void trace(const TcArgs& a, int role, int64_t cell, i
     a.trace[(role * kTraceCells + cell) * kTraceEvents + ev] = clock64();
 }
 
-__device__ __forceinline__ int tiles_per_block(int w) { return w / 128; }
 // TC layers are j = 2 .. H-1; layer j has (j - 1) blocks of w rows.
-__device__ __forceinline__ int layer_tiles(int j, int w) { return (j - 1) * tiles_per_block(w); }
-__device__ __forceinline__ int out_tiles(int H, int w) { return H >= 4 ? (H - 3) * tiles_per_block(w) : 0; }
+__device__ __forceinline__ int out_tiles(int H, int w) { return H >= 4 ? (H - 3) * (w / 128) : 0; }
+
+// Element (row, k) of a K-major, 128-byte-swizzled operand of `rows` rows: byte offset.
+__device__ __forceinline__ uint32_t swz(int rows, int row, int k) {
+  return (uint32_t)((k >> 6) * rows * 128 + row * 128 + ((((k & 63) >> 3) ^ (row & 7)) << 4) + (k & 7) * 2);
+}
+
+// One weight matrix streamed through the math ring (rows k in the bulk producer's order):
+// acc[v][e] += sum_k row_k[col_e] * x_v[k] for col_e = mt + e * 128 and NX vectors x_v, where
+// x_0 = x and, with NX == 4, x_{1..3}[k] = I[r][k] * al[k] (the input-symbol rows times alpha);
+// with `with_abs`, aacc[e] += sum_k |row_k[col_e]| |x[k]|.
+template <int W, int NX, int NPT>
+__device__ __forceinline__ bool ring_gemv(const Smem& s, int* status, uint32_t& ms, uint32_t& mph, int mt, int lane,
+                                          const float* x, const float* al, float (&acc)[NX][NPT], float (&aacc)[NPT],
+                                          bool with_abs) {
+  constexpr int R = kRingBytes / (4 * W);
+  for (int r0 = 0; r0 < W; r0 += R) {
+    if (!wait_bar(s, &s.bar[BAR_MFULL + ms], mph, status)) return false;
+    const float* rows = s.ring + (size_t)ms * (kRingBytes / 4);
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+      const int k = r0 + rr;
+      float xv[NX];
+      xv[0] = x[k];
+      if constexpr (NX == 4) {
+        const float ak = al[k];
+        xv[1] = s.I[k] * ak;
+        xv[2] = s.I[W + k] * ak;
+        xv[3] = s.I[2 * W + k] * ak;
+      }
+#pragma unroll
+      for (int e = 0; e < NPT; ++e) {
+        const float wv = rows[rr * W + mt + e * kMathThreads];
+#pragma unroll
+        for (int vq = 0; vq < NX; ++vq) acc[vq][e] = fmaf(wv, xv[vq], acc[vq][e]);
+        if (with_abs) aacc[e] = fmaf(fabsf(wv), fabsf(xv[0]), aacc[e]);
+      }
+    }
+    // The stage is refilled by the bulk copy engine (async proxy) once every math warp has
+    // released it; the proxy fence orders this thread's generic reads of the stage before that
+    // write.  Without it, reads still queued behind heavy global-store traffic (the epilogue
+    // writing stored G rows) were observed to return the next stage's rows.
+    fence_async_shared();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&s.bar[BAR_MEMPTY + ms]);
+    if (++ms == kRingStages) { ms = 0; mph ^= 1; }
+  }
+  return true;
+}
 
 // ---- the kernel ------------------------------------------------------------------------------------------
+template <int W>
 __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant__ TcArgs args,
                                                            const __grid_constant__ TcMaps maps) {
   extern __shared__ uint8_t smem_raw[];
-  const int w = args.w, H = args.H;
-  Smem s = carve(smem_raw, w);
+  constexpr int MT = W / 128;              // 128-row tiles per block of w rows
+  constexpr int KC = W / 64;               // 64-wide K chunks
+  constexpr int R = kRingBytes / (4 * W);  // weight rows per ring stage
+  const int H = args.H;
+  Smem s = carve(smem_raw, W);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nkc = w / 64;                  // 64-wide K chunks
   const int mode = args.mode;
   const bool clt = mode == ISX_BOUND_CLT;
   const bool infl = args.inflate != 0 && mode == ISX_BOUND_SOUND;
@@ -212,6 +269,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
       mbar_init(&s.bar[BAR_TFULL + i], 1);
       mbar_init(&s.bar[BAR_TEMPTY + i], kEpiWarps);
     }
+    for (int i = 0; i < kRingStages; ++i) {
+      mbar_init(&s.bar[BAR_MFULL + i], 1);
+      mbar_init(&s.bar[BAR_MEMPTY + i], kMathWarps);
+    }
     mbar_init(&s.bar[BAR_BREADY], 1);
     mbar_init(&s.bar[BAR_BFREE], 1);
     mbar_init(&s.bar[BAR_WLOADED], 1);
@@ -220,9 +281,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
     *s.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // zero Bout (rows 1..15 stay zero)
-  for (int i = threadIdx.x; i < 16 * w * 2 / 16; i += blockDim.x)
-    reinterpret_cast<uint4*>(s.Bout)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = threadIdx.x; i < 16 * W * 2 / 16; i += blockDim.x)
+    reinterpret_cast<uint4*>(s.Bs)[i] = make_uint4(0, 0, 0, 0);
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(su32(s.tmem_slot))
                  : "memory");
@@ -233,168 +293,198 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *s.tmem_slot;
-  __nv_bfloat16* scratch = args.scratch + (size_t)blockIdx.x * args.rows_per_cta * w;
+  __nv_bfloat16* scratch = args.scratch + (size_t)blockIdx.x * args.rows_per_cta * W;
   const int scratch_row0 = blockIdx.x * args.rows_per_cta;
 
   if (warp == 0) {
-    // ================================ TMA producer ================================
+    // ============================ TMA producer: B source and A tiles ============================
     if (lane == 0) {
       uint32_t stage = 0, sphase = 0, bfree_n = 0, red_n = 0;
-      for (int64_t cell = blockIdx.x; cell < args.n && !*(volatile int*)s.abort; cell += gridDim.x) {
-        for (int j = 2; j <= H - 1; ++j) {
-          // B source: W_j (bf16) into the B buffer once the previous B is no longer read
-          if (!wait_bar(s, &s.bar[BAR_BFREE], (bfree_n & 1) ^ 1, args.status)) break;
-          ++bfree_n;
-          mbar_expect_tx(&s.bar[BAR_WLOADED], (uint32_t)(w * w * 2));
-          for (int c = 0; c < nkc; ++c) tma_load_2d(s.B + (size_t)c * w * 128, &maps.wrow[j], &s.bar[BAR_WLOADED], c * 64, 0);
-          // rows written by the previous layer must be complete before they are read
-          if (j >= 3) {
-            if (!wait_bar(s, &s.bar[BAR_RED], red_n & 1, args.status)) break;
+      bool ok = true;
+      auto load_a = [&](const CUtensorMap* m, int x, int y) -> bool {
+        if (!wait_bar(s, &s.bar[BAR_EMPTY + stage], sphase ^ 1, args.status)) return false;
+        mbar_expect_tx(&s.bar[BAR_FULL + stage], kStageBytes);
+        tma_load_2d(s.A + (size_t)stage * kStageBytes, m, &s.bar[BAR_FULL + stage], x, y);
+        if (++stage == kStages) { stage = 0; sphase ^= 1; }
+        return true;
+      };
+      for (int64_t cell = blockIdx.x; cell < args.n && ok; cell += gridDim.x) {
+        for (int j = 1; j <= H - 1 && ok; ++j) {
+          if (j >= 2) {
+            // B source: W_j once the previous layer's MMAs no longer read B
+            if (!wait_bar(s, &s.bar[BAR_BFREE], (bfree_n & 1) ^ 1, args.status)) { ok = false; break; }
+            ++bfree_n;
+            mbar_expect_tx(&s.bar[BAR_WLOADED], (uint32_t)(W * W * 2));
+            for (int c = 0; c < KC; ++c) tma_load_2d(s.B + (size_t)c * W * 128, &maps.wrow[j], &s.bar[BAR_WLOADED], c * 64, 0);
+            // the previous layer is complete (its stored rows are read below); the proxy fence
+            // orders the epilogue's generic stores, acquired through RED, before this thread's TMA reads
+            if (!wait_bar(s, &s.bar[BAR_RED], red_n & 1, args.status)) { ok = false; break; }
             ++red_n;
+            fence_async_global();
           }
-          const int T = layer_tiles(j, w), tb = tiles_per_block(w);
-          for (int t = 0; t < T; ++t) {
-            const int blk = t / tb + 1, sub = t % tb;      // G_blk
-            const bool implicit = (blk == j - 1);
-            for (int c = 0; c < nkc; ++c) {
-              if (!wait_bar(s, &s.bar[BAR_EMPTY + stage], sphase ^ 1, args.status)) break;
-              mbar_expect_tx(&s.bar[BAR_FULL + stage], kStageBytes);
-              uint8_t* dst = s.A + (size_t)stage * kStageBytes;
-              if (implicit) tma_load_2d(dst, &maps.wt[j - 1], &s.bar[BAR_FULL + stage], c * 64, sub * 128);
-              else tma_load_2d(dst, &maps.scratch, &s.bar[BAR_FULL + stage], c * 64, scratch_row0 + (blk - 1) * w + sub * 128);
-              if (++stage == kStages) { stage = 0; sphase ^= 1; }
+          // reduction pass: A = |W_j| (sound) or W_j^2 (CLT) against the small B columns
+          {
+            const CUtensorMap* m = clt ? &maps.wsq[j] : &maps.wabs[j];
+            for (int mt = 0; mt < MT && ok; ++mt)
+              for (int c = 0; c < KC; ++c)
+                if (!load_a(m, c * 64, mt * 128)) { ok = false; break; }
+          }
+          if (j >= 2) {
+            const int T = (j - 1) * MT;
+            for (int t = 0; t < T && ok; ++t) {
+              const int blk = t / MT + 1, sub = t % MT;      // G_blk
+              const bool implicit = (blk == j - 1);
+              for (int c = 0; c < KC; ++c) {
+                bool good = implicit ? load_a(&maps.wt[j - 1], c * 64, sub * 128)
+                                     : load_a(&maps.scratch, c * 64, scratch_row0 + (blk - 1) * W + sub * 128);
+                if (!good) { ok = false; break; }
+              }
             }
           }
         }
-        // red_ready of the last TC layer (not waited above) keeps the phase count in step
-        if (H >= 3) {
-          if (!wait_bar(s, &s.bar[BAR_RED], red_n & 1, args.status)) break;
-          ++red_n;
-        }
-        const int TO = out_tiles(H, w);
-        for (int t = 0; t < TO; ++t) {
-          for (int c = 0; c < nkc; ++c) {
-            if (!wait_bar(s, &s.bar[BAR_EMPTY + stage], sphase ^ 1, args.status)) break;
-            mbar_expect_tx(&s.bar[BAR_FULL + stage], kStageBytes);
-            tma_load_2d(s.A + (size_t)stage * kStageBytes, &maps.scratch, &s.bar[BAR_FULL + stage], c * 64,
-                        scratch_row0 + t * 128);
-            if (++stage == kStages) { stage = 0; sphase ^= 1; }
-          }
-        }
-        if (TO > 0) {
+        if (!ok) break;
+        if (!wait_bar(s, &s.bar[BAR_RED], red_n & 1, args.status)) break;   // layer H-1
+        ++red_n;
+        fence_async_global();
+        const int TO = out_tiles(H, W);
+        for (int t = 0; t < TO && ok; ++t)
+          for (int c = 0; c < KC; ++c)
+            if (!load_a(&maps.scratch, c * 64, scratch_row0 + t * 128)) { ok = false; break; }
+        if (ok && TO > 0) {
           if (!wait_bar(s, &s.bar[BAR_RED], red_n & 1, args.status)) break;
           ++red_n;
         }
       }
     }
+  } else if (warp == kRingWarp) {
+    // ============================ bulk producer: float32 weight rows for the math warps ============================
+    if (lane == 0) {
+      uint32_t ms = 0, mph = 0;
+      bool ok = true;
+      auto push = [&](const float* src) -> bool {
+        for (int r0 = 0; r0 < W; r0 += R) {
+          if (!wait_bar(s, &s.bar[BAR_MEMPTY + ms], mph ^ 1, args.status)) return false;
+          mbar_expect_tx(&s.bar[BAR_MFULL + ms], kRingBytes);
+          bulk_load(s.ring + (size_t)ms * (kRingBytes / 4), src + (size_t)r0 * W, kRingBytes, &s.bar[BAR_MFULL + ms]);
+          if (++ms == kRingStages) { ms = 0; mph ^= 1; }
+        }
+        return true;
+      };
+      for (int64_t cell = blockIdx.x; cell < args.n && ok; cell += gridDim.x) {
+        for (int j = 1; j <= H - 1 && ok; ++j) ok = push(args.Wt[j]);      // centre of z_{j+1}
+        if (ok) ok = push(args.W[H - 1]);                                   // v
+        if (ok && H >= 3) ok = push(args.W[H - 2]);                         // implicit G_{H-2}
+      }
+    }
   } else if (warp == 1) {
-    // ================================ MMA issuer ================================
+    // ============================ MMA issuer ============================
     if (lane == 0) {
       uint32_t stage = 0, sphase = 0, bready_n = 0, bout_n = 0, tiles_done = 0;
-      const uint32_t id_main = idesc(w), id_out = idesc(16);
-      for (int64_t cell = blockIdx.x; cell < args.n && !*(volatile int*)s.abort; cell += gridDim.x) {
-        bool ok = true;
-        for (int j = 2; j <= H - 1 && ok; ++j) {
+      const uint32_t id_main = idesc(W), id_small = idesc(16);
+      bool ok = true;
+      // one 128-row tile: K chunks from the A ring against B (bsmem, rows of the B operand)
+      auto tile = [&](uint8_t* bsm, int brows, uint32_t id) -> bool {
+        const uint32_t acc = tiles_done & 1;
+        if (!wait_bar(s, &s.bar[BAR_TEMPTY + acc], ((tiles_done >> 1) & 1) ^ 1, args.status)) return false;
+        tc_fence_after();
+        const uint32_t d = tmem + acc * 256;
+        for (int c = 0; c < KC; ++c) {
+          if (!wait_bar(s, &s.bar[BAR_FULL + stage], sphase, args.status)) return false;
+          tc_fence_after();
+          const uint32_t a0 = su32(s.A + (size_t)stage * kStageBytes);
+          const uint32_t b0 = su32(bsm + (size_t)c * brows * 128);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            mma_bf16(d, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), id, (c > 0 || kk > 0) ? 1u : 0u);
+          mma_commit(&s.bar[BAR_EMPTY + stage]);
+          if (++stage == kStages) { stage = 0; sphase ^= 1; }
+        }
+        mma_commit(&s.bar[BAR_TFULL + acc]);
+        ++tiles_done;
+        return true;
+      };
+      for (int64_t cell = blockIdx.x; cell < args.n && ok; cell += gridDim.x) {
+        for (int j = 1; j <= H - 1 && ok; ++j) {
           if (!wait_bar(s, &s.bar[BAR_BREADY], bready_n & 1, args.status)) { ok = false; break; }
           ++bready_n;
           trace(args, 1, cell / gridDim.x, 2 * j);
           tc_fence_after();
-          const int T = layer_tiles(j, w);
-          for (int t = 0; t < T && ok; ++t) {
-            const uint32_t acc = tiles_done & 1;
-            if (!wait_bar(s, &s.bar[BAR_TEMPTY + acc], ((tiles_done >> 1) & 1) ^ 1, args.status)) { ok = false; break; }
-            tc_fence_after();
-            const uint32_t d = tmem + acc * 256;
-            for (int c = 0; c < nkc; ++c) {
-              if (!wait_bar(s, &s.bar[BAR_FULL + stage], sphase, args.status)) { ok = false; break; }
-              tc_fence_after();
-              const uint32_t a0 = su32(s.A + (size_t)stage * kStageBytes);
-              const uint32_t b0 = su32(s.B + (size_t)c * w * 128);
-#pragma unroll
-              for (int kk = 0; kk < 4; ++kk)
-                mma_bf16(d, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), id_main, (c > 0 || kk > 0) ? 1u : 0u);
-              mma_commit(&s.bar[BAR_EMPTY + stage]);
-              if (++stage == kStages) { stage = 0; sphase ^= 1; }
-            }
-            mma_commit(&s.bar[BAR_TFULL + acc]);
-            ++tiles_done;
+          for (int t = 0; t < MT && ok; ++t) ok = tile(s.Bs, 16, id_small);
+          if (j >= 2) {
+            const int T = (j - 1) * MT;
+            for (int t = 0; t < T && ok; ++t) ok = tile(s.B, W, id_main);
+            if (ok) mma_commit(&s.bar[BAR_BFREE]);
           }
-          mma_commit(&s.bar[BAR_BFREE]);
           trace(args, 1, cell / gridDim.x, 2 * j + 1);
         }
         if (!ok) break;
-        const int TO = out_tiles(H, w);
+        const int TO = out_tiles(H, W);
         if (TO > 0) {
           if (!wait_bar(s, &s.bar[BAR_BOUTREADY], bout_n & 1, args.status)) break;
           ++bout_n;
           tc_fence_after();
-          for (int t = 0; t < TO && ok; ++t) {
-            const uint32_t acc = tiles_done & 1;
-            if (!wait_bar(s, &s.bar[BAR_TEMPTY + acc], ((tiles_done >> 1) & 1) ^ 1, args.status)) { ok = false; break; }
-            tc_fence_after();
-            const uint32_t d = tmem + acc * 256;
-            for (int c = 0; c < nkc; ++c) {
-              if (!wait_bar(s, &s.bar[BAR_FULL + stage], sphase, args.status)) { ok = false; break; }
-              tc_fence_after();
-              const uint32_t a0 = su32(s.A + (size_t)stage * kStageBytes);
-              const uint32_t b0 = su32(s.Bout + (size_t)c * 16 * 128);
-#pragma unroll
-              for (int kk = 0; kk < 4; ++kk)
-                mma_bf16(d, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), id_out, (c > 0 || kk > 0) ? 1u : 0u);
-              mma_commit(&s.bar[BAR_EMPTY + stage]);
-              if (++stage == kStages) { stage = 0; sphase ^= 1; }
-            }
-            mma_commit(&s.bar[BAR_TFULL + acc]);
-            ++tiles_done;
-          }
+          for (int t = 0; t < TO && ok; ++t) ok = tile(s.Bs, 16, id_small);
         }
       }
     }
   } else if (warp < 2 + kEpiWarps) {
-    // ================================ epilogue ================================
+    // ============================ epilogue ============================
     const int q = warp & 3;                    // TMEM lane quarter this warp may access
     const int hf = (warp - 2) >> 2;            // column half
-    const int half = w / 2, nch = half / 32;   // columns and 32-column chunks per half
+    constexpr int HALF = W / 2, NCH = HALF / 32;
     uint32_t tiles_done = 0;
+    auto wait_tile = [&](uint32_t acc) -> bool {
+      int good = 1;
+      if (lane == 0) good = wait_bar(s, &s.bar[BAR_TFULL + acc], (tiles_done >> 1) & 1, args.status) ? 1 : 0;
+      return __shfl_sync(0xffffffffu, good, 0) != 0;
+    };
+    auto release = [&](uint32_t acc) {
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&s.bar[BAR_TEMPTY + acc]);
+      ++tiles_done;
+    };
     for (int64_t cell = blockIdx.x; cell < args.n; cell += gridDim.x) {
       if (__shfl_sync(0xffffffffu, *(volatile int*)s.abort, 0)) break;
       bool ok = true;
-      const int TO = out_tiles(H, w);
-      for (int j = 2; j <= H && ok; ++j) {
-        const bool outpass = (j == H);
-        if (outpass && TO == 0) break;
-        const bool store = !outpass && (j < H - 1);
-        const int T = outpass ? TO : layer_tiles(j, w);
-        const int tb = tiles_per_block(w);
-        float p[4] = {0.f, 0.f, 0.f, 0.f}, comp[4] = {0.f, 0.f, 0.f, 0.f};
-        float pout = 0.f;
-        const float* gprev = s.gamma + ((j - 1) % 3) * w;   // gamma_{j-1}: scale of implicit rows
-        for (int t = 0; t < T; ++t) {
+      for (int j = 1; j <= H - 1 && ok; ++j) {
+        // ---- the reduction pass: 16-column results per output neuron ----
+        for (int mt = 0; mt < MT; ++mt) {
           const uint32_t acc = tiles_done & 1;
-          {
-            int good = 1;
-            if (lane == 0) good = wait_bar(s, &s.bar[BAR_TFULL + acc], (tiles_done >> 1) & 1, args.status) ? 1 : 0;
-            good = __shfl_sync(0xffffffffu, good, 0);
-            if (!good) { ok = false; break; }
-          }
+          if (!wait_tile(acc)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t tbase = tmem + acc * 256 + ((uint32_t)(32 * q) << 16);
-          const int row = 32 * q + lane;                     // row within the tile
-          if (outpass) {
-            if (hf == 0) {
-              float y = tmem_ld1(tbase);
-              float x = clt || mode == ISX_BOUND_RAUA ? y * y : fabsf(y);
+          if (hf == 0) {
+            float v[16];
+            tmem_ld16(tmem + acc * 256 + ((uint32_t)(32 * q) << 16), v);
+            const int p = mt * 128 + 32 * q + lane;
+            s.imp[p] = v[3];
+            s.ig[p] = v[4];
+            s.ie[p] = v[5];
+          }
+          release(acc);
+        }
+        if (!ok) break;
+        // ---- main tiles: G rows of z_{j+1} ----
+        if (j >= 2) {
+          const bool store = j < H - 1;
+          const int T = (j - 1) * MT;
+          float p[NCH], comp[NCH];
 #pragma unroll
-              for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-              pout += x;
-            }
-          } else {
-            const int blk = t / tb + 1, sub = t % tb;
+          for (int ch = 0; ch < NCH; ++ch) p[ch] = comp[ch] = 0.f;
+          const float* gprev = s.gamma + ((j - 1) % 3) * W;   // gamma_{j-1}: scale of implicit rows
+          for (int t = 0; t < T; ++t) {
+            const uint32_t acc = tiles_done & 1;
+            if (!wait_tile(acc)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t tbase = tmem + acc * 256 + ((uint32_t)(32 * q) << 16);
+            const int row = 32 * q + lane;
+            const int blk = t / MT + 1, sub = t % MT;
             const bool implicit = (blk == j - 1);
             const float rs = implicit ? gprev[sub * 128 + row] : 1.0f;
-            __nv_bfloat16* dst = scratch + (size_t)((blk - 1) * w + sub * 128 + row) * w;
-            for (int ch = 0; ch < nch; ++ch) {
-              const int col0 = hf * half + ch * 32;
+            __nv_bfloat16* dst = scratch + (size_t)((blk - 1) * W + sub * 128 + row) * W;
+#pragma unroll
+            for (int ch = 0; ch < NCH; ++ch) {
+              const int col0 = hf * HALF + ch * 32;
               float v[32];
               tmem_ld32(tbase + col0, v);
               if (store) {
@@ -403,7 +493,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
                 for (int i = 0; i < 16; ++i) {
                   __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * i] * rs, v[2 * i + 1] * rs);
                   pk[i] = *reinterpret_cast<uint32_t*>(&h2);
-                  float2 f2 = __bfloat1622float2(h2);
+                  const float2 f2 = __bfloat1622float2(h2);
                   v[2 * i] = f2.x;
                   v[2 * i + 1] = f2.y;
                 }
@@ -416,39 +506,61 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
               }
 #pragma unroll
               for (int i = 0; i < 32; ++i) v[i] = clt ? v[i] * v[i] : fabsf(v[i]);
-              float sum = transpose_reduce32(v);
-              // compensated accumulation across tiles
-              float y = sum - comp[ch];
-              float tt = p[ch] + y;
+              const float sum = transpose_reduce32(v);
+              const float y = sum - comp[ch];
+              const float tt = p[ch] + y;
               comp[ch] = (tt - p[ch]) - y;
               p[ch] = tt;
             }
+            release(acc);
           }
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&s.bar[BAR_TEMPTY + acc]);
-          ++tiles_done;
+          if (!ok) break;
+          if (store) {
+            // the next layer's TMA reads these rows: make the stores visible at GPU scope, then
+            // order them before the async proxy
+            __threadfence();
+            fence_async_global();
+          }
+#pragma unroll
+          for (int ch = 0; ch < NCH; ++ch) s.red[q * W + hf * HALF + ch * 32 + lane] = p[ch];
         }
-        if (!ok) break;
         if (warp == 2 && lane == 0) trace(args, 2, cell / gridDim.x, j);
-        if (store) fence_async_global();
-        if (outpass) {
-          if (hf == 0 && lane == 0) s.red[q * w] = pout;
-        } else {
-          for (int ch = 0; ch < nch; ++ch) s.red[q * w + hf * half + ch * 32 + lane] = p[ch];
-        }
         __syncwarp();
         if (lane == 0) mbar_arrive(&s.bar[BAR_RED]);
       }
       if (!ok) break;
+      // ---- output pass: y rows of the stored blocks of z_{H-1} (column 0) ----
+      const int TO = out_tiles(H, W);
+      if (TO > 0) {
+        float pout = 0.f;
+        for (int t = 0; t < TO; ++t) {
+          const uint32_t acc = tiles_done & 1;
+          if (!wait_tile(acc)) { ok = false; break; }
+          tc_fence_after();
+          if (hf == 0) {
+            float v[16];
+            tmem_ld16(tmem + acc * 256 + ((uint32_t)(32 * q) << 16), v);
+            float x = (clt || mode == ISX_BOUND_RAUA) ? v[0] * v[0] : fabsf(v[0]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            pout += x;
+          }
+          release(acc);
+        }
+        if (!ok) break;
+        if (hf == 0 && lane == 0) s.red[q * W] = pout;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s.bar[BAR_RED]);
+      }
     }
-  } else {
-    // ================================ math ================================
+  } else if (warp < kRingWarp) {
+    // ============================ math ============================
     const int mt = threadIdx.x - kMathBase;    // 0..127
-    uint32_t wl_n = 0, red_n = 0;
+    const int mwarp = mt >> 5;
+    constexpr int NPT = W / kMathThreads;      // neurons per thread (1 or 2)
+    uint32_t wl_n = 0, red_n = 0, ms = 0, mph = 0;
     const float kap = args.kappa;
     const bool sq = clt || mode == ISX_BOUND_RAUA;
-    // uniform decisions: thread 0 of the group waits / reads the abort flag, the group syncs
     auto group_wait = [&](uint64_t* b, uint32_t parity) -> bool {
       if (mt == 0) {
         wait_bar(s, b, parity, args.status);
@@ -486,13 +598,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
           for (int d = 0; d < 3; ++d) h[d] *= 0.57735026918962576f;
       }
       const float* W0 = args.W[0];
-      for (int nn = mt; nn < w; nn += kMathThreads) {
+      for (int nn = mt; nn < W; nn += kMathThreads) {
         float w0 = W0[3 * nn], w1 = W0[3 * nn + 1], w2 = W0[3 * nn + 2], b0 = args.b[0][nn];
         float c = fmaf(w2, xc[2], fmaf(w1, xc[1], fmaf(w0, xc[0], b0)));
         float x0 = h[0] * w0, x1 = h[1] * w1, x2 = h[2] * w2;
         s.I[nn] = x0;
-        s.I[w + nn] = x1;
-        s.I[2 * w + nn] = x2;
+        s.I[W + nn] = x1;
+        s.I[2 * W + nn] = x2;
         s.c[nn] = c;
         float r = clt ? sqrtf(x0 * x0 + x1 * x1 + x2 * x2) : fabsf(x0) + fabsf(x1) + fabsf(x2);
         s.r[nn] = r;
@@ -504,245 +616,197 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
       math_sync();
       if (mt == 0) trace(args, 0, cell / gridDim.x, 1);
       for (int j = 1; j <= H - 1; ++j) {
-        float* al = s.alpha + (j % 3) * w;
-        float* ga = s.gamma + (j % 3) * w;
+        float* al = s.alpha + (j % 3) * W;
+        float* ga = s.gamma + (j % 3) * W;
         // ---- ReLU j (Eq. 4 / Eq. 9) ----
-        for (int nn = mt; nn < w; nn += kMathThreads) {
+        for (int nn = mt; nn < W; nn += kMathThreads) {
           Lin L = clt ? relu_clt(s.c[nn], s.r[nn]) : relu_sound(s.c[nn], s.r[nn], s.delta[nn], infl);
           al[nn] = L.alpha;
           ga[nn] = L.gamma;
           s.a[nn] = L.center;
           s.rada[nn] = infl ? fmaf(L.alpha, s.r[nn], L.gamma) : 0.0f;
-          for (int rr = 0; rr < 3; ++rr) s.Ia[rr * w + nn] = s.I[rr * w + nn] * L.alpha;
+        }
+        math_sync();
+        // ---- small B: columns of the two GEMV passes (rows 0-2: I alpha, 3: gamma or gamma^2,
+        //      4: alpha r + gamma, 5: |a|), K-major 128-byte swizzle ----
+        for (int k = mt; k < W; k += kMathThreads) {
+          __nv_bfloat16* bs = reinterpret_cast<__nv_bfloat16*>(s.Bs);
+          const float ak = al[k];
+          (void)ak;
+          bs[swz(16, 3, k) / 2] = __float2bfloat16_rn(clt ? ga[k] * ga[k] : ga[k]);
+          bs[swz(16, 4, k) / 2] = __float2bfloat16_rn(s.rada[k]);
+          bs[swz(16, 5, k) / 2] = __float2bfloat16_rn(infl ? fabsf(s.a[k]) : 0.0f);
         }
         if (j >= 2) {
-          // ---- B = D_j W_j^T in place: scale the bf16 rows of W_j (K-major, 128-byte swizzle) ----
+          // ---- B = D_j W_j^T: scale the bf16 rows of W_j in place by alpha_j ----
           if (!group_wait(&s.bar[BAR_WLOADED], wl_n & 1)) { ok = false; break; }
           ++wl_n;
-          const int units = nkc * w * 8;   // 16-byte units
-          for (int uidx = mt; uidx < units; uidx += kMathThreads) {
-            const int c = uidx / (w * 8), rem = uidx % (w * 8), nrow = rem >> 3, pu = rem & 7;
-            const int k0 = c * 64 + 8 * (pu ^ (nrow & 7));
-            uint4* ptr = reinterpret_cast<uint4*>(s.B + (size_t)c * w * 128 + nrow * 128 + pu * 16);
-            uint4 val = *ptr;
-            __nv_bfloat162* hv = reinterpret_cast<__nv_bfloat162*>(&val);
+          constexpr int UNITS = KC * W * 8;     // 16-byte units
+          for (int u0 = mt; u0 < UNITS; u0 += 4 * kMathThreads) {
+            uint4 val[4];
+            int k0[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              float2 f = __bfloat1622float2(hv[i]);
-              hv[i] = __floats2bfloat162_rn(f.x * al[k0 + 2 * i], f.y * al[k0 + 2 * i + 1]);
+            for (int e = 0; e < 4; ++e) {
+              const int uidx = u0 + e * kMathThreads;
+              const int c = uidx / (W * 8), rem = uidx % (W * 8), nrow = rem >> 3, pu = rem & 7;
+              k0[e] = c * 64 + 8 * (pu ^ (nrow & 7));
+              val[e] = *reinterpret_cast<const uint4*>(s.B + (size_t)uidx * 16);
             }
-            *ptr = val;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float4 a0 = *reinterpret_cast<const float4*>(al + k0[e]);
+              const float4 a1 = *reinterpret_cast<const float4*>(al + k0[e] + 4);
+              __nv_bfloat162* hv = reinterpret_cast<__nv_bfloat162*>(&val[e]);
+              float2 f0 = __bfloat1622float2(hv[0]), f1 = __bfloat1622float2(hv[1]);
+              float2 f2 = __bfloat1622float2(hv[2]), f3 = __bfloat1622float2(hv[3]);
+              hv[0] = __floats2bfloat162_rn(f0.x * a0.x, f0.y * a0.y);
+              hv[1] = __floats2bfloat162_rn(f1.x * a0.z, f1.y * a0.w);
+              hv[2] = __floats2bfloat162_rn(f2.x * a1.x, f2.y * a1.y);
+              hv[3] = __floats2bfloat162_rn(f3.x * a1.z, f3.y * a1.w);
+              *reinterpret_cast<uint4*>(s.B + (size_t)(u0 + e * kMathThreads) * 16) = val[e];
+            }
           }
-          fence_async_shared();
-          math_sync();
-          if (mt == 0) mbar_arrive(&s.bar[BAR_BREADY]);
-        } else {
-          math_sync();
         }
+        fence_async_shared();
+        math_sync();
+        if (mt == 0) mbar_arrive(&s.bar[BAR_BREADY]);
         if (mt == 0) trace(args, 0, cell / gridDim.x, 2 + 4 * (j - 1));
-        // ---- CUDA-core part of linear layer j: centre, I rows, implicit block G_j, slack ----
-        // Every thread owns 4 consecutive neurons (float4 loads of W_j^T rows) for one half of
-        // the k range; the two halves are combined through shared memory.
+        // ---- centre and I rows of z_{j+1} in float32: W_j a_j + b_j and I_j D_j W_j^T (weights via the ring) ----
         {
-          const float* Wt = args.Wt[j];
-          const int LG = w / 4, grp = mt / LG, ln = mt % LG, kh = w / 2;
-          float4 cc = make_float4(0.f, 0.f, 0.f, 0.f), i0 = cc, i1 = cc, i2 = cc, imp = cc, ee = cc, gg = cc;
-          if (mt < 2 * LG) {
-            const float4* Wp = reinterpret_cast<const float4*>(Wt) + ln;
-            const int kb = grp * kh;
-#pragma unroll 16
-            for (int k = kb; k < kb + kh; ++k) {
-              const float4 wk = __ldg(Wp + (size_t)k * LG);
-              const float ak = s.a[k], gk = ga[k], q0 = s.Ia[k], q1 = s.Ia[w + k], q2 = s.Ia[2 * w + k];
-              cc.x = fmaf(wk.x, ak, cc.x); cc.y = fmaf(wk.y, ak, cc.y); cc.z = fmaf(wk.z, ak, cc.z); cc.w = fmaf(wk.w, ak, cc.w);
-              i0.x = fmaf(wk.x, q0, i0.x); i0.y = fmaf(wk.y, q0, i0.y); i0.z = fmaf(wk.z, q0, i0.z); i0.w = fmaf(wk.w, q0, i0.w);
-              i1.x = fmaf(wk.x, q1, i1.x); i1.y = fmaf(wk.y, q1, i1.y); i1.z = fmaf(wk.z, q1, i1.z); i1.w = fmaf(wk.w, q1, i1.w);
-              i2.x = fmaf(wk.x, q2, i2.x); i2.y = fmaf(wk.y, q2, i2.y); i2.z = fmaf(wk.z, q2, i2.z); i2.w = fmaf(wk.w, q2, i2.w);
-              if (clt) {
-                const float tx = wk.x * gk, ty = wk.y * gk, tz = wk.z * gk, tw = wk.w * gk;
-                imp.x = fmaf(tx, tx, imp.x); imp.y = fmaf(ty, ty, imp.y); imp.z = fmaf(tz, tz, imp.z); imp.w = fmaf(tw, tw, imp.w);
-              } else {
-                imp.x = fmaf(fabsf(wk.x), gk, imp.x); imp.y = fmaf(fabsf(wk.y), gk, imp.y);
-                imp.z = fmaf(fabsf(wk.z), gk, imp.z); imp.w = fmaf(fabsf(wk.w), gk, imp.w);
-                if (infl) {
-                  const float aa = fabsf(ak), ra = s.rada[k];
-                  ee.x = fmaf(fabsf(wk.x), aa, ee.x); ee.y = fmaf(fabsf(wk.y), aa, ee.y);
-                  ee.z = fmaf(fabsf(wk.z), aa, ee.z); ee.w = fmaf(fabsf(wk.w), aa, ee.w);
-                  gg.x = fmaf(fabsf(wk.x), ra, gg.x); gg.y = fmaf(fabsf(wk.y), ra, gg.y);
-                  gg.z = fmaf(fabsf(wk.z), ra, gg.z); gg.w = fmaf(fabsf(wk.w), ra, gg.w);
-                }
-              }
-            }
+          float acc[4][NPT], dummy[NPT];
+#pragma unroll
+          for (int e = 0; e < NPT; ++e) {
+            acc[0][e] = acc[1][e] = acc[2][e] = acc[3][e] = 0.f;
+            dummy[e] = 0.f;
           }
-          // group 1 hands its partial sums over (v, u, tmp, rpart, spart, Inew as staging)
-          float* stg[7] = {s.tmp, s.Inew, s.Inew + w, s.Inew + 2 * w, s.rpart, s.v, s.u};
-          const float4 mine[7] = {cc, i0, i1, i2, imp, ee, gg};
-          if (mt < 2 * LG && grp == 1)
-            for (int q = 0; q < 7; ++q) reinterpret_cast<float4*>(stg[q])[ln] = mine[q];
-          math_sync();
-          if (mt < LG) {
-            float4 o[7];
-            for (int q = 0; q < 7; ++q) {
-              const float4 t = reinterpret_cast<const float4*>(stg[q])[ln];
-              o[q] = make_float4(mine[q].x + t.x, mine[q].y + t.y, mine[q].z + t.z, mine[q].w + t.w);
-            }
-            const float4 bb = reinterpret_cast<const float4*>(args.b[j])[ln];
-            const float bv[4] = {bb.x, bb.y, bb.z, bb.w};
-            const float cv[4] = {o[0].x, o[0].y, o[0].z, o[0].w};
-            const float v0[4] = {o[1].x, o[1].y, o[1].z, o[1].w}, v1[4] = {o[2].x, o[2].y, o[2].z, o[2].w},
-                        v2[4] = {o[3].x, o[3].y, o[3].z, o[3].w}, im[4] = {o[4].x, o[4].y, o[4].z, o[4].w},
-                        ev[4] = {o[5].x, o[5].y, o[5].z, o[5].w}, gv[4] = {o[6].x, o[6].y, o[6].z, o[6].w};
-            for (int e4 = 0; e4 < 4; ++e4) {
-              const int nn = 4 * ln + e4;
-              s.tmp[nn] = cv[e4] + bv[e4];
-              s.Inew[nn] = v0[e4];
-              s.Inew[w + nn] = v1[e4];
-              s.Inew[2 * w + nn] = v2[e4];
-              s.rpart[nn] = im[e4] + (clt ? v0[e4] * v0[e4] + v1[e4] * v1[e4] + v2[e4] * v2[e4]
-                                          : fabsf(v0[e4]) + fabsf(v1[e4]) + fabsf(v2[e4]));
-              s.spart[nn] = infl ? (kap * gv[e4] + gamma_k(w + 2, kLinU) * (ev[e4] + fabsf(bv[e4]))) * kLinSafe : 0.0f;
-            }
+          if (!ring_gemv<W, 4, NPT>(s, args.status, ms, mph, mt, lane, s.a, al, acc, dummy, false)) ok = false;
+          math_sync();     // every thread has read a, c and I
+          if (!ok) break;
+#pragma unroll
+          for (int e = 0; e < NPT; ++e) {
+            const int nn = mt + e * kMathThreads;
+            s.c[nn] = acc[0][e] + args.b[j][nn];
+            s.Inew[nn] = acc[1][e];
+            s.Inew[W + nn] = acc[2][e];
+            s.Inew[2 * W + nn] = acc[3][e];
           }
         }
-        // ---- the G rows' reductions from the epilogue ----
         if (mt == 0) trace(args, 0, cell / gridDim.x, 3 + 4 * (j - 1));
-        if (j >= 2) {
-          if (!group_wait(&s.bar[BAR_RED], red_n & 1)) { ok = false; break; }
-          ++red_n;
-        } else {
-          math_sync();
-        }
+        // ---- combine: radius and slack of z_{j+1} ----
+        if (!group_wait(&s.bar[BAR_RED], red_n & 1)) { ok = false; break; }
+        ++red_n;
         if (mt == 0) trace(args, 0, cell / gridDim.x, 4 + 4 * (j - 1));
         const bool stored = (j >= 2) && (j < H - 1);
-        for (int nn = mt; nn < w; nn += kMathThreads) {
-          float tc = 0.f;
-          if (j >= 2) tc = s.red[nn] + s.red[w + nn] + s.red[2 * w + nn] + s.red[3 * w + nn];
-          float tot = s.rpart[nn] + tc;
+        const float* bj = args.b[j];
+        for (int nn = mt; nn < W; nn += kMathThreads) {
+          const float tc = (j >= 2) ? s.red[nn] + s.red[W + nn] + s.red[2 * W + nn] + s.red[3 * W + nn] : 0.f;
+          const float i0 = s.Inew[nn], i1 = s.Inew[W + nn], i2 = s.Inew[2 * W + nn];
+          const float rI = clt ? i0 * i0 + i1 * i1 + i2 * i2 : fabsf(i0) + fabsf(i1) + fabsf(i2);
+          const float imp = clt ? s.imp[nn] : s.imp[nn] * (infl ? kGemvSafe : 1.0f);
+          const float tot = tc + rI + imp;
           s.rprev[nn] = s.r[nn];
           s.r[nn] = clt ? sqrtf(tot) : tot;
-          s.delta[nn] = infl ? s.spart[nn] + (stored ? kUb / (1.0f - kUb) * tc * kLinSafe : 0.f) : 0.f;
-          s.c[nn] = s.tmp[nn];
-          s.I[nn] = s.Inew[nn];
-          s.I[w + nn] = s.Inew[w + nn];
-          s.I[2 * w + nn] = s.Inew[2 * w + nn];
+          s.delta[nn] = infl ? (kap * s.ig[nn] + gamma_k(W + 2, kLinU) * (s.ie[nn] + fabsf(bj[nn]))) * kGemvSafe +
+                                   (stored ? kUb / (1.0f - kUb) * tc * kLinSafe : 0.f)
+                             : 0.f;
+          s.I[nn] = i0;
+          s.I[W + nn] = i1;
+          s.I[2 * W + nn] = i2;
         }
         math_sync();
         if (mt == 0) trace(args, 0, cell / gridDim.x, 5 + 4 * (j - 1));
       }
       if (!ok) break;
       // ---- ReLU H, then the output layer (through layer H-1 for the G rows) ----
-      float* al = s.alpha + (H % 3) * w;
-      float* ga = s.gamma + (H % 3) * w;
-      for (int nn = mt; nn < w; nn += kMathThreads) {
+      float* al = s.alpha + (H % 3) * W;
+      float* ga = s.gamma + (H % 3) * W;
+      const float* wout = args.W[H];
+      for (int nn = mt; nn < W; nn += kMathThreads) {
         Lin L = clt ? relu_clt(s.c[nn], s.r[nn]) : relu_sound(s.c[nn], s.r[nn], s.delta[nn], infl);
         al[nn] = L.alpha;
         ga[nn] = L.gamma;
         s.a[nn] = L.center;
+        s.Inew[nn] = L.alpha * wout[nn];          // alpha_H * w_out (x of the v GEMV)
       }
       math_sync();
-      const float* wout = args.W[H];
       if (mt == 0) trace(args, 0, cell / gridDim.x, 40);
-      const float* WHm1 = args.W[H - 1];                 // row-major [n][k]
-      const float* alm1 = s.alpha + ((H - 1) % 3) * w;
-      // v = W_{H-1}^T (alpha_H * w_out), |v|abs, u = alpha_{H-1} * v  (4 k per thread, n split in halves)
+      const float* alm1 = s.alpha + ((H - 1) % 3) * W;
+      float* v = s.imp;
+      float* u = s.ig;
+      float* vabs = s.ie;
       {
-        const int LG = w / 4, grp = mt / LG, ln = mt % LG, nh = w / 2;
-        float4 vv = make_float4(0.f, 0.f, 0.f, 0.f), va = vv;
-        if (mt < 2 * LG) {
-          const float4* Wp = reinterpret_cast<const float4*>(WHm1) + ln;
-#pragma unroll 8
-          for (int nn = grp * nh; nn < grp * nh + nh; ++nn) {
-            const float4 wv = __ldg(Wp + (size_t)nn * LG);
-            const float aw = al[nn] * wout[nn], awa = fabsf(aw);
-            vv.x = fmaf(wv.x, aw, vv.x); vv.y = fmaf(wv.y, aw, vv.y); vv.z = fmaf(wv.z, aw, vv.z); vv.w = fmaf(wv.w, aw, vv.w);
-            va.x = fmaf(fabsf(wv.x), awa, va.x); va.y = fmaf(fabsf(wv.y), awa, va.y);
-            va.z = fmaf(fabsf(wv.z), awa, va.z); va.w = fmaf(fabsf(wv.w), awa, va.w);
-          }
-          if (grp == 1) {
-            reinterpret_cast<float4*>(s.v)[ln] = vv;
-            reinterpret_cast<float4*>(s.tmp)[ln] = va;
-          }
-        }
+        // v_k = sum_n W_{H-1}[n][k] alpha_H,n w_out,n (rows n of W_{H-1} through the ring)
+        float acc[1][NPT], aacc[NPT];
+#pragma unroll
+        for (int e = 0; e < NPT; ++e) acc[0][e] = aacc[e] = 0.f;
+        if (!ring_gemv<W, 1, NPT>(s, args.status, ms, mph, mt, lane, s.Inew, al, acc, aacc, true)) ok = false;
         math_sync();
-        if (mt < LG) {
-          const float4 t1 = reinterpret_cast<const float4*>(s.v)[ln], t2 = reinterpret_cast<const float4*>(s.tmp)[ln];
-          const float x[4] = {vv.x + t1.x, vv.y + t1.y, vv.z + t1.z, vv.w + t1.w};
-          const float y[4] = {va.x + t2.x, va.y + t2.y, va.z + t2.z, va.w + t2.w};
-          for (int e4 = 0; e4 < 4; ++e4) {
-            const int k = 4 * ln + e4;
-            s.v[k] = x[e4];
-            s.tmp[k] = y[e4];
-            s.u[k] = alm1[k] * x[e4];
-          }
+        if (!ok) break;
+#pragma unroll
+        for (int e = 0; e < NPT; ++e) {
+          const int k = mt + e * kMathThreads;
+          v[k] = acc[0][e];
+          vabs[k] = aacc[e];
+          u[k] = alm1[k] * acc[0][e];
         }
       }
       math_sync();
-      const int TO = out_tiles(H, w);
+      const int TO = out_tiles(H, W);
       if (TO > 0) {
-        // Bout row 0 = bf16(u) in the 128-byte-swizzled K-major layout (row 0 is not permuted)
-        for (int k = mt; k < w; k += kMathThreads) {
-          const int c = k / 64, unit = (k % 64) / 8;
-          __nv_bfloat16* p = reinterpret_cast<__nv_bfloat16*>(s.Bout + (size_t)c * 16 * 128 + unit * 16) + (k % 8);
-          *p = __float2bfloat16_rn(s.u[k]);
+        // Bs row 0 = bf16(u), rows 1-5 cleared
+        __nv_bfloat16* bs = reinterpret_cast<__nv_bfloat16*>(s.Bs);
+        for (int k = mt; k < W; k += kMathThreads) {
+          bs[swz(16, 0, k) / 2] = __float2bfloat16_rn(u[k]);
+          for (int rr = 1; rr < 6; ++rr) bs[swz(16, rr, k) / 2] = __float2bfloat16_rn(0.0f);
         }
         fence_async_shared();
         math_sync();
         if (mt == 0) mbar_arrive(&s.bar[BAR_BOUTREADY]);
       }
-      // implicit G_{H-2} at z_{H-1} (through u): y_m = gamma_{H-2,m} sum_n W_{H-2}[n][m] u_n
+      float gsum[NPT];
+#pragma unroll
+      for (int e = 0; e < NPT; ++e) gsum[e] = 0.f;
       if (H >= 3) {
-        const int LG = w / 4, grp = mt / LG, ln = mt % LG, nh = w / 2;
-        float4 dd = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (mt < 2 * LG) {
-          const float4* Wp = reinterpret_cast<const float4*>(args.W[H - 2]) + ln;
-#pragma unroll 8
-          for (int nn = grp * nh; nn < grp * nh + nh; ++nn) {
-            const float4 wv = __ldg(Wp + (size_t)nn * LG);
-            const float un = s.u[nn];
-            dd.x = fmaf(wv.x, un, dd.x); dd.y = fmaf(wv.y, un, dd.y); dd.z = fmaf(wv.z, un, dd.z); dd.w = fmaf(wv.w, un, dd.w);
-          }
-          if (grp == 1) reinterpret_cast<float4*>(s.rpart)[ln] = dd;
-        }
-        math_sync();
-        if (mt < LG) {
-          const float4 t = reinterpret_cast<const float4*>(s.rpart)[ln];
-          s.spart[4 * ln] = dd.x + t.x;
-          s.spart[4 * ln + 1] = dd.y + t.y;
-          s.spart[4 * ln + 2] = dd.z + t.z;
-          s.spart[4 * ln + 3] = dd.w + t.w;
-        }
-        math_sync();
+        // implicit G_{H-2} at z_{H-1}: sum_n W_{H-2}[n][m] u_n (rows n of W_{H-2} through the ring)
+        float dummy[NPT], g1[1][NPT];
+#pragma unroll
+        for (int e = 0; e < NPT; ++e) g1[0][e] = dummy[e] = 0.f;
+        if (!ring_gemv<W, 1, NPT>(s, args.status, ms, mph, mt, lane, u, al, g1, dummy, false)) ok = false;
+        if (!ok) { math_sync(); break; }
+#pragma unroll
+        for (int e = 0; e < NPT; ++e) gsum[e] = g1[0][e];
       }
-      // CUDA-core rows: G_{H-2} at z_{H-1} (above), G_{H-1} at z_H (v), fresh G_H, and the I rows of
-      // z_H (through alpha_H * w_out)
       float acc = 0.f, eabs = 0.f, x0p = 0.f, cen = 0.f;
-      const float* gam1 = s.gamma + ((H - 1) % 3) * w;
-      for (int m = mt; m < w; m += kMathThreads) {
+      const float* gam1 = s.gamma + ((H - 1) % 3) * W;
+      const float* gam2 = s.gamma + ((H - 2) % 3) * W;
+#pragma unroll
+      for (int e = 0; e < NPT; ++e) {
+        const int m = mt + e * kMathThreads;
         if (H >= 3) {
-          const float* gam2 = s.gamma + ((H - 2) % 3) * w;
-          const float y = gam2[m] * s.spart[m];
+          const float y = gam2[m] * gsum[e];
           acc += sq ? y * y : fabsf(y);
         }
-        const float y1 = gam1[m] * s.v[m];
+        const float y1 = gam1[m] * v[m];
         const float y2 = ga[m] * wout[m];
         acc += sq ? y1 * y1 + y2 * y2 : fabsf(y1) + fabsf(y2);
         x0p = fmaf(wout[m], s.a[m], x0p);
         if (infl) {
-          eabs += s.rprev[m] * alm1[m] * s.tmp[m] + gam1[m] * s.tmp[m] + (s.r[m] * al[m] + ga[m]) * fabsf(wout[m]);
+          eabs += s.rprev[m] * alm1[m] * vabs[m] + gam1[m] * vabs[m] + (s.r[m] * al[m] + ga[m]) * fabsf(wout[m]);
           cen = fmaf(fabsf(wout[m]), fabsf(s.a[m]), cen);
         }
       }
       if (mt < 3) {
         float y = 0.f;
-        for (int k = 0; k < w; ++k) y = fmaf(s.I[mt * w + k], al[k] * wout[k], y);
+        for (int k = 0; k < W; ++k) y = fmaf(s.I[mt * W + k], s.Inew[k], y);   // I rows of z_H . alpha_H w_out
         acc += sq ? y * y : fabsf(y);
       }
       float vals[4] = {acc, eabs, x0p, cen};
+#pragma unroll
       for (int qv = 0; qv < 4; ++qv) {
         float x = vals[qv];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) s.scal[qv * 4 + (mt >> 5)] = x;
+        if (lane == 0) s.scal[qv * 4 + mwarp] = x;
       }
       if (mt == 0) trace(args, 0, cell / gridDim.x, 41);
       if (TO > 0) {
@@ -760,14 +824,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
           xp += s.scal[8 + i];
           ce += s.scal[12 + i];
         }
-        if (TO > 0) tot += s.red[0] + s.red[w] + s.red[2 * w] + s.red[3 * w];
+        if (TO > 0) tot += s.red[0] + s.red[W] + s.red[2 * W] + s.red[3 * W];
         const float x0 = xp + args.bout;
         float sp;
         if (mode == ISX_BOUND_SOUND) {
           sp = tot;
           if (infl)
             sp = __fadd_ru(__fmul_ru(sp, kLinSafe),
-                           (args.kappa_out * ea + gamma_k(w + 2, kLinU) * (ce + fabsf(args.bout))) * 1.01f);
+                           (args.kappa_out * ea + gamma_k(W + 2, kLinU) * (ce + fabsf(args.bout))) * 1.01f);
         } else if (mode == ISX_BOUND_CLT) {
           sp = sqrtf(tot);
         } else {
@@ -832,6 +896,30 @@ isx_status make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t o
 
 }  // namespace
 
+namespace {
+// Weight tensor maps, shared-memory opt-in and the launch of the width-specialised kernel.
+isx_status launch_tc(isx_inr inr, const TcArgs& a, TcMaps& maps, int grid, cudaStream_t st) {
+  const int w = inr->w;
+  for (int l = 1; l < inr->n_layers - 1; ++l) {
+    ISX_TRY(make_map(&maps.wt[l], inr->Wt_bf16[l], w, w, 64, 128));
+    ISX_TRY(make_map(&maps.wrow[l], inr->W_bf16[l], w, w, 64, w));
+    ISX_TRY(make_map(&maps.wa[l], inr->W_bf16[l], w, w, 64, 128));
+    ISX_TRY(make_map(&maps.wabs[l], inr->Wabs_bf16[l], w, w, 64, 128));
+    ISX_TRY(make_map(&maps.wsq[l], inr->Wsq_bf16[l], w, w, 64, 128));
+  }
+  const size_t smem = smem_bytes(w);
+  if (w == 256) {
+    ISX_CUDA(cudaFuncSetAttribute(k_bound_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_bound_tc<256><<<grid, kThreads, smem, st>>>(a, maps);
+  } else {
+    ISX_CUDA(cudaFuncSetAttribute(k_bound_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_bound_tc<128><<<grid, kThreads, smem, st>>>(a, maps);
+  }
+  ISX_LAUNCH_CHECK("k_bound_tc");
+  return ISX_OK;
+}
+}  // namespace
+
 isx_status tensor_map_bf16(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
                            uint32_t box_outer) {
   return make_map(m, base, inner, outer, box_inner, box_outer);
@@ -884,10 +972,6 @@ isx_status bound_bf16(isx_inr inr, const CellSource& src, int64_t n, isx_bound_m
   TcMaps maps;
   std::memset(&maps, 0, sizeof(maps));
   ISX_TRY(make_map(&maps.scratch, a.scratch, w, (uint64_t)sms * rows, 64, 128));
-  for (int l = 1; l < inr->n_layers - 1; ++l) {
-    ISX_TRY(make_map(&maps.wt[l], inr->Wt_bf16[l], w, w, 64, 128));
-    ISX_TRY(make_map(&maps.wrow[l], inr->W_bf16[l], w, w, 64, w));
-  }
   ISX_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), st));
   const bool tracing = std::getenv("ISX_TRACE") != nullptr;
   a.trace = nullptr;
@@ -896,15 +980,12 @@ isx_status bound_bf16(isx_inr inr, const CellSource& src, int64_t n, isx_bound_m
     a.trace = ws[WS_AUX].as<long long>();
     ISX_CUDA(cudaMemsetAsync(a.trace, 0, 3 * kTraceCells * kTraceEvents * sizeof(long long), st));
   }
-  const size_t smem = smem_bytes(w);
-  ISX_CUDA(cudaFuncSetAttribute(k_bound_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   {
     const double cells = (double)n;
     const double rows_gemm = (double)w * (H - 1) * (H - 2) / 2.0;   // G rows over layers 2..H-1
     prof::Scope ps(K_BOUND_TC, st, cells * 2.0 * w * w * (3.0 * (H - 1) + rows_gemm), 0);
-    k_bound_tc<<<grid, kThreads, smem, st>>>(a, maps);
+    ISX_TRY(launch_tc(inr, a, maps, grid, st));
   }
-  ISX_LAUNCH_CHECK("k_bound_tc");
   int status = 0;
   ISX_CUDA(cudaMemcpyAsync(&status, a.status, sizeof(int), cudaMemcpyDeviceToHost, st));
   ISX_CUDA(cudaStreamSynchronize(st));
@@ -1035,21 +1116,14 @@ extern "C" isx_status isx_bound_cells_noalloc(isx_inr inr, const float* d_lo, co
   TcMaps maps;
   std::memset(&maps, 0, sizeof(maps));
   ISX_TRY(make_map(&maps.scratch, a.scratch, w, (uint64_t)grid * a.rows_per_cta, 64, 128));
-  for (int l = 1; l < inr->n_layers - 1; ++l) {
-    ISX_TRY(make_map(&maps.wt[l], inr->Wt_bf16[l], w, w, 64, 128));
-    ISX_TRY(make_map(&maps.wrow[l], inr->W_bf16[l], w, w, 64, w));
-  }
   // the status word must start at zero on every call; the slices need no clearing (every row is
   // written before it is read)
   ISX_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), st));
-  const size_t smem = smem_bytes(w);
-  ISX_CUDA(cudaFuncSetAttribute(k_bound_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   {
     const double rows_gemm = (double)w * (H - 1) * (H - 2) / 2.0;
     prof::Scope ps(K_BOUND_TC, st, (double)n * 2.0 * w * w * (3.0 * (H - 1) + rows_gemm), 0);
-    k_bound_tc<<<grid, kThreads, smem, st>>>(a, maps);
+    ISX_TRY(launch_tc(inr, a, maps, grid, st));
   }
-  ISX_LAUNCH_CHECK("k_bound_tc (static scratch)");
   int status = 0;
   ISX_CUDA(cudaMemcpyAsync(&status, a.status, sizeof(int), cudaMemcpyDeviceToHost, st));
   ISX_CUDA(cudaStreamSynchronize(st));

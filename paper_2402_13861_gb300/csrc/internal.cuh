@@ -66,6 +66,8 @@ struct isx_inr_s {
   std::vector<float*> W, Wt, b;
   std::vector<__nv_bfloat16*> Wt_bf16;   // W[l]^T in bfloat16, for the tensor-core path
   std::vector<__nv_bfloat16*> W_bf16;    // W[l] in bfloat16 (row-major [out][in])
+  std::vector<__nv_bfloat16*> Wabs_bf16; // |W[l]| in bfloat16 (row-major)
+  std::vector<__nv_bfloat16*> Wsq_bf16;  // W[l]^2 in bfloat16 (row-major)
   std::vector<float*> absW_rowsum;       // sum_k |W[l][n][k]| per output neuron
   std::vector<std::vector<float>> hW, hb;  // host copies
   isx::Buf ws[isx::WS_N_SLOTS];

@@ -106,12 +106,13 @@ def load_peaks():
         return {}
 
 
-def traffic_for(kernel, src_file):
-    """ncu DRAM bytes per launch recorded in profiles/traffic.json, if the kernel source is unchanged."""
+def traffic_per_cell(kernel, src_file):
+    """ncu DRAM bytes per bounded cell recorded in profiles/traffic.json (from a capture of a smaller
+    launch of the same kernel), if the kernel source is unchanged since the capture."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
         sha = hashlib.sha256(open(src_file, "rb").read()).hexdigest()[:16]
-        return rec["dram_bytes_per_launch"] if rec.get("src_sha") == sha else None
+        return rec["dram_bytes_per_cell"] if rec.get("src_sha") == sha else None
     except Exception:
         return None
 
@@ -220,6 +221,7 @@ def main():
     clocks = sampler.stop()
     pkg.profile_enable(False)
     stats = pkg.profile_read()
+    cells_local = cells
     t = torch.tensor([total_ms, float(cells)], dtype=torch.float64, device="cuda")
     if world > 1:
         tmax = t.clone()
@@ -272,7 +274,8 @@ def main():
         roof = {"bound": "alu", "unit": "TFLOP/s", "peak_source": "152 SM x 128 FP32 lanes x 2 x max SM clock"}
         src = os.path.join(ROOT, "paper_2402_13861_gb300", "csrc", "bound_fp32.cu")
     achieved = ds["flops"] / (ds["ms"] / 1e3) / 1e12 if ds["ms"] > 0 else 0.0
-    tr = traffic_for(dom, src)
+    bpc = traffic_per_cell(dom, src)
+    tr = bpc * cells_local / max(ds["launches"], 1) if bpc is not None else None
     roof.update({"kernel": dom, "achieved": achieved, "peak": peak, "frac": achieved / peak,
                  "launches": ds["launches"], "avg_launch_ms": ds["ms"] / max(ds["launches"], 1),
                  "traffic": tr})

@@ -33,6 +33,7 @@ extern "C" {
 #define ISX_MC_MAX_TRI 5
 
 typedef struct isx_inr_s* isx_inr;
+typedef struct isx_proposer_s* isx_proposer;
 
 typedef enum {
   ISX_OK = 0,
@@ -108,7 +109,12 @@ isx_status isx_bound_cells_noalloc(isx_inr inr, const float* d_lo, const float* 
                                    isx_bound_mode mode, int inflate, float* d_center, float* d_spread,
                                    void* stream);
 
-/* Evaluates the INR at n points (device float32 [n][3]) into d_out (device float32 [n]). */
+/* Evaluates the INR at n points (device float32 [n][3]) into d_out (device float32 [n]).
+ * ISX_PREC_FP32: FP32 FMAs on the CUDA cores.  ISX_PREC_BF16: tcgen05 tensor cores with every operand
+ * split into two BF16 terms (x = x_hi + x_lo) and three products per multiply-add
+ * (a_hi b_hi + a_hi b_lo + a_lo b_hi), FP32 accumulation: relative error per layer below about
+ * 2^-15 of the absolute-value propagation, i.e. FP32-class; widths 128 and 256 only
+ * (ISX_ERR_UNSUPPORTED otherwise). */
 isx_status isx_eval_points(isx_inr inr, const float* d_xyz, int64_t n, isx_precision prec,
                            float* d_out, void* stream);
 
@@ -122,6 +128,16 @@ typedef struct {
   int inflate;                   /* SOUND only: rounding-error inflation (see isx_bound_cells)  */
   int bound_stop_level;          /* levels deeper than this keep every child without bounding;
                                     < 0 or >= max_level: bound every level (the paper's setting) */
+  /* learned proposal (no counterpart in the paper; NULL: plain range analysis at every level).
+     At levels >= proposer_level (>= 1) every (cell, iso) pair of a cell's mask is scored first:
+     p <= tau_lo drops the iso, p >= tau_hi keeps it without a bound, and a cell with any pair in
+     between is bounded, its bound then deciding all of its isos. */
+  isx_proposer proposer;
+  int proposer_level;
+  float tau_lo, tau_hi;
+  /* corner / lattice evaluation: ISX_PREC_FP32 (CUDA cores, the default) or ISX_PREC_BF16
+     (tensor cores with two-term BF16 operands, FP32-class accuracy; see isx_eval_points) */
+  isx_precision eval_prec;
 } isx_extract_params;
 
 typedef struct {
@@ -138,10 +154,11 @@ typedef struct {
   int64_t n_active;              /* predicted active cells                                        */
   int64_t n_tris;                /* triangles over all iso-values                                 */
   int64_t n_points;              /* distinct lattice corners evaluated                            */
-  int64_t cells_bounded[ISX_MAX_LEVEL + 1];
+  int64_t cells_bounded[ISX_MAX_LEVEL + 1];   /* cells whose affine bound was computed        */
   int64_t cells_kept[ISX_MAX_LEVEL + 1];
   float ms_acp, ms_inr, ms_mc, ms_total;   /* active-cell prediction, corner evaluation, marching
                                               cubes, whole call (CUDA events on `stream`)        */
+  int64_t cells_visited[ISX_MAX_LEVEL + 1];   /* cells considered per level (>= cells_bounded)  */
 } isx_mesh;
 
 /* Hierarchical extraction (Algorithm 1 run level by level over octree cubes, then corner queries
@@ -165,6 +182,37 @@ isx_status isx_extract_dense(isx_inr inr, const isx_extract_params* params, isx_
  * (c & 1, c >> 1 & 1, c >> 2 & 1); edge 4a + t runs along axis a from the corner with bit a clear;
  * the two other axes p < q take bits t & 1 and t >> 1.  Host-only; needs no GPU. */
 isx_status isx_mc_table(int8_t* ntri, int8_t* tris);
+
+/* ---- learned proposal ------------------------------------------------------------------------
+ * A cell-subdivision proposer (an addition; the paper decides by range analysis alone): an
+ * 8 -> 64 -> 64 -> 64 -> 1 ReLU MLP with a sigmoid output giving, for a (cell, iso) pair, the
+ * probability that the cell's subtree holds a finest cell crossed by that iso-surface.  BF16 weights
+ * and activations with FP32 accumulation; FP32 master weights and Adam state on the device.
+ * Parameters are packed FP32, row-major [out][in] weights each followed by its bias:
+ * W1[64][8] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[1][64] b4[1].
+ * Feature rows (float32 [n][8]): cell centre x, y, z; log2 of the half-width (= -level); iso-value
+ * c; (centre of the nearest bounded ancestor's bound) - c; that bound's spread (radius or sigma);
+ * level gap to that ancestor.  Features are standardised with (x - mean) / std before layer 1. */
+#define ISX_PROPOSER_NPARAM 8961
+/* Copies `params` (host, ISX_PROPOSER_NPARAM floats) and the standardisation (host, 8 + 8 floats,
+ * std > 0) to the current device; Adam state starts at zero.  Synchronous. */
+isx_status isx_proposer_create(const float* params, const float* feat_mean, const float* feat_std,
+                               isx_proposer* out);
+isx_status isx_proposer_destroy(isx_proposer p);
+/* Current FP32 master parameters into host memory (ISX_PROPOSER_NPARAM floats).  Synchronous. */
+isx_status isx_proposer_get_params(isx_proposer p, float* host_out);
+/* Logits of n feature rows (device float32 [n][8]) into d_logit (device float32 [n]). */
+isx_status isx_proposer_predict(isx_proposer p, const float* d_feat, int64_t n, float* d_logit,
+                                void* stream);
+/* Gradient of the mean binary cross-entropy over n labelled rows (labels device float32 [n], 0 or 1)
+ * into d_grad (device float32 [ISX_PROPOSER_NPARAM], overwritten) and the loss into d_loss (device
+ * float32 [1], overwritten).  The parameters are not changed. */
+isx_status isx_proposer_grad(isx_proposer p, const float* d_feat, const float* d_label, int64_t n,
+                             float* d_grad, float* d_loss, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the mean BCE of n labelled rows;
+ * d_loss (nullable, device float32 [1]) receives the loss before the step. */
+isx_status isx_proposer_train_step(isx_proposer p, const float* d_feat, const float* d_label, int64_t n,
+                                   float lr, float* d_loss, void* stream);
 
 /* ---- measurement ----------------------------------------------------------------------------
  * Per-kernel accounting.  Launch counts and the algorithmic work of every launch (FLOPs and bytes

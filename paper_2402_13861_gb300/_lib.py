@@ -46,7 +46,8 @@ class InrDesc(C.Structure):
 class ExtractParams(C.Structure):
     _fields_ = [("max_level", C.c_int), ("n_iso", C.c_int), ("iso", C.c_float * ISX_MAX_ISO),
                 ("mode", C.c_int), ("k", C.c_float), ("prec", C.c_int), ("inflate", C.c_int),
-                ("bound_stop_level", C.c_int)]
+                ("bound_stop_level", C.c_int), ("proposer", C.c_void_p), ("proposer_level", C.c_int),
+                ("tau_lo", C.c_float), ("tau_hi", C.c_float), ("eval_prec", C.c_int)]
 
 
 class Mesh(C.Structure):
@@ -56,7 +57,8 @@ class Mesh(C.Structure):
                 ("n_active", C.c_int64), ("n_tris", C.c_int64), ("n_points", C.c_int64),
                 ("cells_bounded", C.c_int64 * (ISX_MAX_LEVEL + 1)),
                 ("cells_kept", C.c_int64 * (ISX_MAX_LEVEL + 1)),
-                ("ms_acp", C.c_float), ("ms_inr", C.c_float), ("ms_mc", C.c_float), ("ms_total", C.c_float)]
+                ("ms_acp", C.c_float), ("ms_inr", C.c_float), ("ms_mc", C.c_float), ("ms_total", C.c_float),
+                ("cells_visited", C.c_int64 * (ISX_MAX_LEVEL + 1))]
 
 
 _lib = None
@@ -91,8 +93,16 @@ def load(path: Path | None = None):
     lib.isx_profile_reset.restype = None
     lib.isx_profile_read.argtypes = [C.POINTER(KernelStats), C.c_int]
     lib.isx_profile_read.restype = C.c_int
+    lib.isx_proposer_create.argtypes = [f32p, f32p, f32p, C.POINTER(vp)]
+    lib.isx_proposer_destroy.argtypes = [vp]
+    lib.isx_proposer_get_params.argtypes = [vp, f32p]
+    lib.isx_proposer_predict.argtypes = [vp, vp, i64, vp, vp]
+    lib.isx_proposer_grad.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+    lib.isx_proposer_train_step.argtypes = [vp, vp, vp, i64, C.c_float, vp, vp]
     for name in ("isx_create_inr", "isx_destroy_inr", "isx_bound_cells", "isx_eval_points",
-                 "isx_extract_isosurface", "isx_extract_dense", "isx_mc_table"):
+                 "isx_extract_isosurface", "isx_extract_dense", "isx_mc_table", "isx_proposer_create",
+                 "isx_proposer_destroy", "isx_proposer_get_params", "isx_proposer_predict", "isx_proposer_grad",
+                 "isx_proposer_train_step"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -194,7 +204,8 @@ class Inr:
         return out
 
     @staticmethod
-    def params(max_level, isos, mode="sound", k=3.0, prec="fp32", inflate=False, bound_stop_level=-1):
+    def params(max_level, isos, mode="sound", k=3.0, prec="fp32", inflate=False, bound_stop_level=-1,
+               proposer=None, proposer_level=1, tau_lo=0.0, tau_hi=1.0, eval_prec="fp32"):
         p = ExtractParams()
         p.max_level = max_level
         isos = list(np.atleast_1d(np.asarray(isos, dtype=np.float32)))
@@ -206,14 +217,21 @@ class Inr:
         p.prec = PRECS[prec]
         p.inflate = int(bool(inflate))
         p.bound_stop_level = bound_stop_level
+        p.proposer = proposer.handle if proposer is not None else None
+        p.proposer_level = int(proposer_level)
+        p.tau_lo = float(tau_lo)
+        p.tau_hi = float(tau_hi)
+        p.eval_prec = PRECS[eval_prec]
         return p
 
     def extract(self, max_level, isos, mode="sound", k=3.0, prec="fp32", inflate=False, bound_stop_level=-1,
-                active_cap=1 << 16, tri_cap=1 << 18, dense=False, stream=None, buffers=None):
+                active_cap=1 << 16, tri_cap=1 << 18, dense=False, stream=None, buffers=None, proposer=None,
+                proposer_level=1, tau_lo=0.0, tau_hi=1.0, eval_prec="fp32"):
         """Hierarchical (or, with dense=True, dense) extraction.  Grows the output buffers and
         retries once if a capacity is exceeded.  Returns a dict of tensors and counters."""
         import torch
-        p = self.params(max_level, isos, mode, k, prec, inflate, bound_stop_level)
+        p = self.params(max_level, isos, mode, k, prec, inflate, bound_stop_level, proposer, proposer_level,
+                        tau_lo, tau_hi, eval_prec)
         fn = load().isx_extract_dense if dense else load().isx_extract_isosurface
         dev = torch.device("cuda", torch.cuda.current_device())
         bufs = buffers if buffers is not None else {}
@@ -250,4 +268,71 @@ class Inr:
             tri_vert=bufs["vert"][:nt], tri_edge=bufs["edge"][:nt], tri_iso=bufs["iso"][:nt], tri_cell=bufs["cell"][:nt],
             n_active=na, n_tris=nt, n_points=int(m.n_points),
             cells_bounded=list(m.cells_bounded)[:max_level + 1], cells_kept=list(m.cells_kept)[:max_level + 1],
+            cells_visited=list(m.cells_visited)[:max_level + 1],
             ms_acp=m.ms_acp, ms_inr=m.ms_inr, ms_mc=m.ms_mc, ms_total=m.ms_total, buffers=bufs)
+
+
+PROPOSER_NPARAM = 8961
+
+
+class Proposer:
+    """The cell-subdivision proposer on the current CUDA device (wraps isx_proposer).
+
+    ``params``: packed float32 vector of ISX_PROPOSER_NPARAM values (W1[64][8] b1 W2[64][64] b2
+    W3[64][64] b3 W4[1][64] b4); ``mean`` / ``std``: the 8 feature standardisation constants."""
+
+    def __init__(self, params, mean, std):
+        lib = load()
+        params = np.ascontiguousarray(params, dtype=np.float32).reshape(-1)
+        assert params.size == PROPOSER_NPARAM
+        self.mean = np.ascontiguousarray(mean, dtype=np.float32).reshape(8)
+        self.std = np.ascontiguousarray(std, dtype=np.float32).reshape(8)
+        h = C.c_void_p()
+        f32p = C.POINTER(C.c_float)
+        _check(lib.isx_proposer_create(params.ctypes.data_as(f32p), self.mean.ctypes.data_as(f32p),
+                                       self.std.ctypes.data_as(f32p), C.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().isx_proposer_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        out = np.zeros(PROPOSER_NPARAM, dtype=np.float32)
+        _check(load().isx_proposer_get_params(self._h, out.ctypes.data_as(C.POINTER(C.c_float))))
+        return out
+
+    def predict(self, feat, out=None, stream=None):
+        """Logits of feature rows (float32 CUDA tensor [n, 8])."""
+        import torch
+        n = feat.shape[0]
+        assert feat.is_cuda and feat.dtype == torch.float32 and feat.is_contiguous()
+        if out is None:
+            out = torch.empty(n, dtype=torch.float32, device=feat.device)
+        _check(load().isx_proposer_predict(self._h, _ptr(feat), n, _ptr(out), _stream_ptr(stream)))
+        return out
+
+    def grad(self, feat, label, stream=None):
+        """(gradient [NPARAM], mean BCE) of labelled rows, without updating the parameters."""
+        import torch
+        g = torch.empty(PROPOSER_NPARAM, dtype=torch.float32, device=feat.device)
+        loss = torch.empty(1, dtype=torch.float32, device=feat.device)
+        _check(load().isx_proposer_grad(self._h, _ptr(feat), _ptr(label), feat.shape[0], _ptr(g), _ptr(loss),
+                                        _stream_ptr(stream)))
+        return g, loss
+
+    def train_step(self, feat, label, lr, loss=None, stream=None):
+        """One Adam step on a labelled mini-batch; ``loss`` (CUDA float32 [1]) receives its loss."""
+        _check(load().isx_proposer_train_step(self._h, _ptr(feat), _ptr(label), feat.shape[0], float(lr),
+                                              _ptr(loss), _stream_ptr(stream)))

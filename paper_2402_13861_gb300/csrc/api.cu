@@ -105,7 +105,29 @@ isx_status validate_params(const isx_extract_params* p, const isx_mesh* m) {
     set_error("k must be >= 0");
     return ISX_ERR_ARG;
   }
+  if (p->eval_prec < ISX_PREC_FP32 || p->eval_prec > ISX_PREC_BF16) {
+    set_error("bad evaluation precision");
+    return ISX_ERR_ARG;
+  }
+  if (p->proposer && !(p->tau_lo >= 0.0f && p->tau_lo < p->tau_hi && p->tau_hi <= 1.0f)) {
+    set_error("proposer thresholds must satisfy 0 <= tau_lo < tau_hi <= 1");
+    return ISX_ERR_ARG;
+  }
   return ISX_OK;
+}
+
+// Lattice-point evaluation in the requested precision.
+isx_status eval_dispatch(isx_inr inr, isx_precision prec, const uint32_t* ids, int R, int64_t n, float* out,
+                         cudaStream_t st) {
+  if (prec == ISX_PREC_BF16) return eval_points_tc(inr, nullptr, ids, R, n, out, st);
+  return eval_points_fp32(inr, nullptr, ids, R, n, out, st);
+}
+
+// Logit of a probability threshold (0 -> -inf, 1 -> +inf).
+float logit_of(float p) {
+  if (p <= 0.0f) return -INFINITY;
+  if (p >= 1.0f) return INFINITY;
+  return std::log(p / (1.0f - p));
 }
 
 IsoSet iso_of(const isx_extract_params* p) {
@@ -177,6 +199,7 @@ isx_status isx_create_inr(const isx_inr_desc* d, isx_inr* out) {
   inr->W_bf16.assign(L, nullptr);
   inr->Wabs_bf16.assign(L, nullptr);
   inr->Wsq_bf16.assign(L, nullptr);
+  inr->Wlo_bf16.assign(L, nullptr);
   inr->absW_rowsum.assign(L, nullptr);
   inr->hW.resize(L);
   inr->hb.resize(L);
@@ -189,13 +212,15 @@ isx_status isx_create_inr(const isx_inr_desc* d, isx_inr* out) {
     inr->hW[l].assign(d->W[l], d->W[l] + (size_t)fi * fo);
     inr->hb[l].assign(d->b[l], d->b[l] + fo);
     std::vector<float> t((size_t)fi * fo);
-    std::vector<__nv_bfloat16> tb((size_t)fi * fo), rb((size_t)fi * fo), ab((size_t)fi * fo), sb((size_t)fi * fo);
+    std::vector<__nv_bfloat16> tb((size_t)fi * fo), rb((size_t)fi * fo), ab((size_t)fi * fo), sb((size_t)fi * fo),
+        lb((size_t)fi * fo);
     for (int o = 0; o < fo; ++o)
       for (int i = 0; i < fi; ++i) {
         const float x = d->W[l][(size_t)o * fi + i];
         t[(size_t)i * fo + o] = x;
         tb[(size_t)i * fo + o] = __float2bfloat16_rn(x);
         rb[(size_t)o * fi + i] = __float2bfloat16_rn(x);
+        lb[(size_t)o * fi + i] = __float2bfloat16_rn(x - __bfloat162float(rb[(size_t)o * fi + i]));
         ab[(size_t)o * fi + i] = __float2bfloat16_rn(std::fabs(x));
         sb[(size_t)o * fi + i] = __float2bfloat16_rn(x * x);
       }
@@ -211,6 +236,9 @@ isx_status isx_create_inr(const isx_inr_desc* d, isx_inr* out) {
       return fail(cuda_fail(e, "W bf16", __FILE__, __LINE__));
     if ((e = cudaMemcpy(inr->W_bf16[l], rb.data(), (size_t)fi * fo * 2, cudaMemcpyHostToDevice)) != cudaSuccess)
       return fail(cuda_fail(e, "W bf16 copy", __FILE__, __LINE__));
+    if ((e = cudaMalloc(&inr->Wlo_bf16[l], (size_t)fi * fo * 2)) != cudaSuccess ||
+        (e = cudaMemcpy(inr->Wlo_bf16[l], lb.data(), (size_t)fi * fo * 2, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return fail(cuda_fail(e, "W low bf16", __FILE__, __LINE__));
     if ((e = cudaMalloc(&inr->Wabs_bf16[l], (size_t)fi * fo * 2)) != cudaSuccess ||
         (e = cudaMalloc(&inr->Wsq_bf16[l], (size_t)fi * fo * 2)) != cudaSuccess)
       return fail(cuda_fail(e, "|W| / W^2 bf16", __FILE__, __LINE__));
@@ -239,6 +267,7 @@ isx_status isx_destroy_inr(isx_inr inr) {
   for (auto* p : inr->W_bf16) if (p) cudaFree(p);
   for (auto* p : inr->Wabs_bf16) if (p) cudaFree(p);
   for (auto* p : inr->Wsq_bf16) if (p) cudaFree(p);
+  for (auto* p : inr->Wlo_bf16) if (p) cudaFree(p);
   for (auto* p : inr->absW_rowsum) if (p) cudaFree(p);
   for (auto& buf : inr->ws) buf.release();
   if (prev >= 0) cudaSetDevice(prev);
@@ -271,7 +300,11 @@ isx_status isx_eval_points(isx_inr inr, const float* d_xyz, int64_t n, isx_preci
     set_error("bad size or null pointer");
     return ISX_ERR_ARG;
   }
-  (void)prec;
+  if (prec == ISX_PREC_BF16) return eval_points_tc(inr, d_xyz, nullptr, 0, n, d_out, (cudaStream_t)stream);
+  if (prec != ISX_PREC_FP32) {
+    set_error("bad precision");
+    return ISX_ERR_ARG;
+  }
   return eval_points_fp32(inr, d_xyz, nullptr, 0, n, d_out, (cudaStream_t)stream);
 }
 
@@ -287,8 +320,12 @@ isx_status isx_extract_isosurface(isx_inr inr, const isx_extract_params* p, isx_
   const int R = 1 << L;
   const IsoSet iso = iso_of(p);
   const int stop = (p->bound_stop_level < 0 || p->bound_stop_level >= L) ? L : p->bound_stop_level;
-  for (int l = 0; l <= ISX_MAX_LEVEL; ++l) mesh->cells_bounded[l] = mesh->cells_kept[l] = 0;
+  for (int l = 0; l <= ISX_MAX_LEVEL; ++l) mesh->cells_bounded[l] = mesh->cells_kept[l] = mesh->cells_visited[l] = 0;
   mesh->n_active = mesh->n_tris = mesh->n_points = 0;
+  // learned proposal: levels >= plevel (and <= stop) are gated; their ancestors' bounds are carried
+  const bool use_prop = p->proposer != nullptr;
+  const int plevel = use_prop ? std::max(1, p->proposer_level) : L + 1;
+  const float z_lo = use_prop ? logit_of(p->tau_lo) : 0.0f, z_hi = use_prop ? logit_of(p->tau_hi) : 0.0f;
   Timer tm;
   ISX_TRY(tm.init());
   ISX_CUDA(cudaEventRecord(tm.ev[0], st));
@@ -302,33 +339,87 @@ isx_status isx_extract_isosurface(isx_inr inr, const isx_extract_params* p, isx_
   int64_t* d_count = ws[WS_COUNT].as<int64_t>();
   int64_t n = 1;
   Slot ca = WS_CODES_A, cb = WS_CODES_B, ma = WS_MASK_A, mb = WS_MASK_B;
+  Slot aca = WS_ANC_C_A, acb = WS_ANC_C_B, asa = WS_ANC_S_A, asb = WS_ANC_S_B, aga = WS_ANC_G_A, agb = WS_ANC_G_B;
   for (int level = 0; level <= L; ++level) {
-    bool bounded = level <= stop;
-    bool expand = level < L;
+    const bool bounded = level <= stop;
+    const bool expand = level < L;
+    const bool gated = use_prop && bounded && level >= plevel;
+    const bool carry = use_prop && expand && level + 1 >= plevel && level + 1 <= stop;
+    mesh->cells_visited[level] = n;
     mesh->cells_bounded[level] = bounded ? n : 0;
+    const uint32_t* step_masks = ws[ma].as<uint32_t>();
+    bool step_bounded = bounded;
+    AncIO anc;
     if (n > 0) {
       ISX_TRY(ws[WS_CENTER].ensure((size_t)n * 4, "center"));
       ISX_TRY(ws[WS_SPREAD].ensure((size_t)n * 4, "spread"));
-      if (bounded) {
+      if (gated) {
+        // proposer first; the undecided cells are compacted and bounded, and their bound decides
+        ISX_TRY(ws[WS_PROP_KEEP].ensure((size_t)n * 4, "proposer keep"));
+        ISX_TRY(ws[WS_PROP_NEED].ensure((size_t)n, "proposer need"));
+        ISX_TRY(ws[WS_PROP_IDX].ensure((size_t)n * 4, "proposer index"));
+        ISX_TRY(ws[WS_PROP_CODES].ensure((size_t)n * 4, "proposer codes"));
+        uint32_t* keep = ws[WS_PROP_KEEP].as<uint32_t>();
+        ISX_TRY(proposer_gate(p->proposer, ws[ca].as<uint32_t>(), ws[ma].as<uint32_t>(), ws[aca].as<float>(),
+                              ws[asa].as<float>(), ws[aga].as<uint8_t>(), n, level, iso, z_lo, z_hi, keep,
+                              ws[WS_PROP_NEED].as<uint8_t>(), st));
+        ISX_TRY(compact_flags(inr, ws[WS_PROP_NEED].as<uint8_t>(), n, ws[WS_PROP_IDX].as<uint32_t>(), nullptr,
+                              d_count, st));
+        int64_t nneed = 0;
+        ISX_CUDA(cudaMemcpyAsync(&nneed, d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        ISX_CUDA(cudaStreamSynchronize(st));
+        if (nneed > 0) {
+          ISX_TRY(gather_codes(ws[ca].as<uint32_t>(), ws[WS_PROP_IDX].as<uint32_t>(), nneed,
+                               ws[WS_PROP_CODES].as<uint32_t>(), st));
+          CellSource src;
+          src.codes = ws[WS_PROP_CODES].as<uint32_t>();
+          src.level = level;
+          ISX_TRY(bound_dispatch(inr, src, nneed, p->mode, p->prec, p->inflate, ws[WS_CENTER].as<float>(),
+                                 ws[WS_SPREAD].as<float>(), st));
+          ISX_TRY(proposer_merge(ws[WS_PROP_IDX].as<uint32_t>(), nneed, ws[ma].as<uint32_t>(),
+                                 ws[WS_CENTER].as<float>(), ws[WS_SPREAD].as<float>(), iso, p->mode, p->k,
+                                 p->inflate, keep, ws[aca].as<float>(), ws[asa].as<float>(), ws[aga].as<uint8_t>(),
+                                 st));
+        }
+        mesh->cells_bounded[level] = nneed;
+        step_masks = keep;
+        step_bounded = false;
+        anc.in_c = ws[aca].as<float>();
+        anc.in_s = ws[asa].as<float>();
+        anc.in_gap = ws[aga].as<uint8_t>();
+      } else if (bounded) {
         CellSource src;
         src.codes = ws[ca].as<uint32_t>();
         src.level = level;
         ISX_TRY(bound_dispatch(inr, src, n, p->mode, p->prec, p->inflate, ws[WS_CENTER].as<float>(),
                                ws[WS_SPREAD].as<float>(), st));
+        anc.in_c = ws[WS_CENTER].as<float>();
+        anc.in_s = ws[WS_SPREAD].as<float>();
       }
       size_t need = (size_t)(expand ? 8 : 1) * n * 4;
       ISX_TRY(ws[cb].ensure(need, "codes"));
       ISX_TRY(ws[mb].ensure(need, "masks"));
+      if (carry) {
+        ISX_TRY(ws[acb].ensure(need, "ancestor centre"));
+        ISX_TRY(ws[asb].ensure(need, "ancestor spread"));
+        ISX_TRY(ws[agb].ensure(need / 4, "ancestor gap"));
+        anc.out_c = ws[acb].as<float>();
+        anc.out_s = ws[asb].as<float>();
+        anc.out_gap = ws[agb].as<uint8_t>();
+      }
     }
-    ISX_TRY(level_step(inr, ws[ca].as<uint32_t>(), ws[ma].as<uint32_t>(), n, ws[WS_CENTER].as<float>(),
-                       ws[WS_SPREAD].as<float>(), bounded, iso, p->mode, p->k, p->inflate, expand,
-                       ws[cb].as<uint32_t>(), ws[mb].as<uint32_t>(), d_count, st));
+    ISX_TRY(level_step(inr, ws[ca].as<uint32_t>(), step_masks, n, ws[WS_CENTER].as<float>(),
+                       ws[WS_SPREAD].as<float>(), step_bounded, iso, p->mode, p->k, p->inflate, expand,
+                       ws[cb].as<uint32_t>(), ws[mb].as<uint32_t>(), d_count, st, carry ? &anc : nullptr));
     int64_t cnt = 0;
     ISX_CUDA(cudaMemcpyAsync(&cnt, d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     ISX_CUDA(cudaStreamSynchronize(st));
     mesh->cells_kept[level] = expand ? cnt / 8 : cnt;
     std::swap(ca, cb);
     std::swap(ma, mb);
+    std::swap(aca, acb);
+    std::swap(asa, asb);
+    std::swap(aga, agb);
     n = cnt;
   }
   ISX_CUDA(cudaEventRecord(tm.ev[1], st));
@@ -362,7 +453,7 @@ isx_status isx_extract_isosurface(isx_inr inr, const isx_extract_params* p, isx_
   ISX_CUDA(cudaStreamSynchronize(st));
   mesh->n_points = npts;
   ISX_TRY(ws[WS_VALUES].ensure((size_t)std::max<int64_t>(npts, 1) * 4, "values"));
-  ISX_TRY(eval_points_fp32(inr, nullptr, ws[WS_POINTS].as<uint32_t>(), R, npts, ws[WS_VALUES].as<float>(), st));
+  ISX_TRY(eval_dispatch(inr, p->eval_prec, ws[WS_POINTS].as<uint32_t>(), R, npts, ws[WS_VALUES].as<float>(), st));
   ISX_CUDA(cudaEventRecord(tm.ev[2], st));
   isx_status s = marching_cubes(inr, codes, masks, n, R, ws[WS_LATTICE_IDX].as<uint32_t>(),
                                 ws[WS_VALUES].as<float>(), iso, mesh, false, st);
@@ -382,7 +473,7 @@ isx_status isx_extract_dense(isx_inr inr, const isx_extract_params* p, isx_mesh*
   const int L = p->max_level;
   const int R = 1 << L;
   const IsoSet iso = iso_of(p);
-  for (int l = 0; l <= ISX_MAX_LEVEL; ++l) mesh->cells_bounded[l] = mesh->cells_kept[l] = 0;
+  for (int l = 0; l <= ISX_MAX_LEVEL; ++l) mesh->cells_bounded[l] = mesh->cells_kept[l] = mesh->cells_visited[l] = 0;
   mesh->n_active = mesh->n_tris = 0;
   Timer tm;
   ISX_TRY(tm.init());
@@ -395,7 +486,7 @@ isx_status isx_extract_dense(isx_inr inr, const isx_extract_params* p, isx_mesh*
   // lattice ids are 0..nlat-1: evaluate with an identity id list
   ISX_TRY(ws[WS_POINTS].ensure((size_t)nlat * 4, "points"));
   ISX_TRY(iota_u32(ws[WS_POINTS].as<uint32_t>(), nlat, st));
-  ISX_TRY(eval_points_fp32(inr, nullptr, ws[WS_POINTS].as<uint32_t>(), R, nlat, ws[WS_VALUES].as<float>(), st));
+  ISX_TRY(eval_dispatch(inr, p->eval_prec, ws[WS_POINTS].as<uint32_t>(), R, nlat, ws[WS_VALUES].as<float>(), st));
   ISX_CUDA(cudaEventRecord(tm.ev[2], st));
   isx_status s = marching_cubes(inr, nullptr, nullptr, (int64_t)R * R * R, R, nullptr, ws[WS_VALUES].as<float>(),
                                 iso, mesh, true, st);

@@ -245,6 +245,44 @@ __device__ __forceinline__ bool ring_gemv(const Smem& s, int* status, uint32_t& 
   return true;
 }
 
+// B = D_j W_j^T in place: the 16-byte units of B (K-major, 128-byte swizzle) from index g on, with
+// stride kScaleThreads, scaled by alpha along K (the math warps run it with g = mt, mt + 128, ...;
+// four units in flight per thread).
+constexpr int kScaleThreads = 3 * kMathThreads;
+template <int W>
+__device__ __forceinline__ void scale_b(const Smem& s, const float* al, int g) {
+  constexpr int UNITS = (W / 64) * W * 8;
+  for (int u0 = g; u0 < UNITS; u0 += 4 * kScaleThreads) {
+    uint4 val[4];
+    int k0[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int uidx = u0 + e * kScaleThreads;
+      if (uidx < UNITS) {
+        const int c = uidx / (W * 8), rem = uidx % (W * 8), nrow = rem >> 3, pu = rem & 7;
+        k0[e] = c * 64 + 8 * (pu ^ (nrow & 7));
+        val[e] = *reinterpret_cast<const uint4*>(s.B + (size_t)uidx * 16);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int uidx = u0 + e * kScaleThreads;
+      if (uidx < UNITS) {
+        const float4 a0 = *reinterpret_cast<const float4*>(al + k0[e]);
+        const float4 a1 = *reinterpret_cast<const float4*>(al + k0[e] + 4);
+        __nv_bfloat162* hv = reinterpret_cast<__nv_bfloat162*>(&val[e]);
+        float2 f0 = __bfloat1622float2(hv[0]), f1 = __bfloat1622float2(hv[1]);
+        float2 f2 = __bfloat1622float2(hv[2]), f3 = __bfloat1622float2(hv[3]);
+        hv[0] = __floats2bfloat162_rn(f0.x * a0.x, f0.y * a0.y);
+        hv[1] = __floats2bfloat162_rn(f1.x * a0.z, f1.y * a0.w);
+        hv[2] = __floats2bfloat162_rn(f2.x * a1.x, f2.y * a1.y);
+        hv[3] = __floats2bfloat162_rn(f3.x * a1.z, f3.y * a1.w);
+        *reinterpret_cast<uint4*>(s.B + (size_t)uidx * 16) = val[e];
+      }
+    }
+  }
+}
+
 // ---- the kernel ------------------------------------------------------------------------------------------
 template <int W>
 __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant__ TcArgs args,
@@ -637,38 +675,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
           bs[swz(16, 4, k) / 2] = __float2bfloat16_rn(s.rada[k]);
           bs[swz(16, 5, k) / 2] = __float2bfloat16_rn(infl ? fabsf(s.a[k]) : 0.0f);
         }
+        if (mt == 0) trace(args, 0, cell / gridDim.x, 24 + 2 * (j - 1));
         if (j >= 2) {
           // ---- B = D_j W_j^T: scale the bf16 rows of W_j in place by alpha_j ----
           if (!group_wait(&s.bar[BAR_WLOADED], wl_n & 1)) { ok = false; break; }
           ++wl_n;
-          constexpr int UNITS = KC * W * 8;     // 16-byte units
-          for (int u0 = mt; u0 < UNITS; u0 += 4 * kMathThreads) {
-            uint4 val[4];
-            int k0[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int uidx = u0 + e * kMathThreads;
-              const int c = uidx / (W * 8), rem = uidx % (W * 8), nrow = rem >> 3, pu = rem & 7;
-              k0[e] = c * 64 + 8 * (pu ^ (nrow & 7));
-              val[e] = *reinterpret_cast<const uint4*>(s.B + (size_t)uidx * 16);
-            }
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const float4 a0 = *reinterpret_cast<const float4*>(al + k0[e]);
-              const float4 a1 = *reinterpret_cast<const float4*>(al + k0[e] + 4);
-              __nv_bfloat162* hv = reinterpret_cast<__nv_bfloat162*>(&val[e]);
-              float2 f0 = __bfloat1622float2(hv[0]), f1 = __bfloat1622float2(hv[1]);
-              float2 f2 = __bfloat1622float2(hv[2]), f3 = __bfloat1622float2(hv[3]);
-              hv[0] = __floats2bfloat162_rn(f0.x * a0.x, f0.y * a0.y);
-              hv[1] = __floats2bfloat162_rn(f1.x * a0.z, f1.y * a0.w);
-              hv[2] = __floats2bfloat162_rn(f2.x * a1.x, f2.y * a1.y);
-              hv[3] = __floats2bfloat162_rn(f3.x * a1.z, f3.y * a1.w);
-              *reinterpret_cast<uint4*>(s.B + (size_t)(u0 + e * kMathThreads) * 16) = val[e];
-            }
-          }
+          if (mt == 0) trace(args, 0, cell / gridDim.x, 25 + 2 * (j - 1));
+          for (int g = mt; g < kScaleThreads; g += kMathThreads) scale_b<W>(s, al, g);
+          fence_async_shared();
+          math_sync();
+        } else {
+          fence_async_shared();
+          math_sync();
         }
-        fence_async_shared();
-        math_sync();
         if (mt == 0) mbar_arrive(&s.bar[BAR_BREADY]);
         if (mt == 0) trace(args, 0, cell / gridDim.x, 2 + 4 * (j - 1));
         // ---- centre and I rows of z_{j+1} in float32: W_j a_j + b_j and I_j D_j W_j^T (weights via the ring) ----

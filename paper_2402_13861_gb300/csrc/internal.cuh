@@ -51,6 +51,8 @@ enum Slot {
   WS_COUNT, WS_C, WS_X0, WS_X1, WS_RAD, WS_ALPHA, WS_GAMMA, WS_DELTA, WS_AUX,
   WS_LATTICE_FLAG, WS_LATTICE_IDX, WS_POINTS, WS_VALUES, WS_TRI_COUNT, WS_TRI_OFFSET,
   WS_TC_SCRATCH, WS_TC_STATE, WS_TC_STATUS,
+  WS_ANC_C_A, WS_ANC_C_B, WS_ANC_S_A, WS_ANC_S_B, WS_ANC_G_A, WS_ANC_G_B, WS_PROP_KEEP, WS_PROP_NEED,
+  WS_PROP_IDX, WS_PROP_CODES,
   WS_N_SLOTS
 };
 
@@ -68,6 +70,7 @@ struct isx_inr_s {
   std::vector<__nv_bfloat16*> W_bf16;    // W[l] in bfloat16 (row-major [out][in])
   std::vector<__nv_bfloat16*> Wabs_bf16; // |W[l]| in bfloat16 (row-major)
   std::vector<__nv_bfloat16*> Wsq_bf16;  // W[l]^2 in bfloat16 (row-major)
+  std::vector<__nv_bfloat16*> Wlo_bf16;  // W[l] - float(W_bf16[l]) in bfloat16: low part of a two-term split
   std::vector<float*> absW_rowsum;       // sum_k |W[l][n][k]| per output neuron
   std::vector<std::vector<float>> hW, hb;  // host copies
   isx::Buf ws[isx::WS_N_SLOTS];
@@ -81,7 +84,7 @@ namespace isx {
 enum KernelId {
   K_INPUT, K_RELU, K_GEMV, K_GEMM_FP32, K_FRESH, K_REDUCE, K_OUTPUT, K_CULL, K_SCAN, K_SCATTER, K_MARK,
   K_FLAGCOUNT, K_SCATTER_FLAGS, K_EVAL_FP32, K_MC_COUNT, K_MC_EMIT, K_IOTA, K_BOUND_TC, K_TC_PREP, K_TC_OUTPUT,
-  K_EVAL_TC, K_BOUND_COV, K_COUNT
+  K_EVAL_TC, K_BOUND_COV, K_PROP_GATE, K_PROP_MERGE, K_PROP_FWD, K_PROP_GRAD, K_PROP_ADAM, K_COUNT
 };
 namespace prof {
 // RAII bracket around one kernel launch: counts it, adds its algorithmic work, and (when
@@ -118,6 +121,11 @@ bool bf16_supported(isx_inr inr);
 // 2-D bfloat16 tensor map [outer][inner] (row stride inner * 2 bytes), 128-byte swizzle.
 isx_status tensor_map_bf16(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
                            uint32_t box_outer);
+// MLP values at points on tcgen05 with two-term BF16 operands (eval_tc.cu); ISX_ERR_UNSUPPORTED for
+// widths other than 128 / 256.  Points as in eval_points_fp32.
+isx_status eval_points_tc(isx_inr inr, const float* xyz, const uint32_t* lattice_ids, int R, int64_t n,
+                          float* out, cudaStream_t st);
+bool eval_tc_supported(isx_inr inr);
 // CLT bound by covariance propagation on tcgen05 (bound_cov.cu).
 isx_status bound_bf16_clt_cov(isx_inr inr, const CellSource& src, int64_t n, float* d_center, float* d_spread,
                               cudaStream_t st);
@@ -131,10 +139,21 @@ struct IsoSet {
 // writes the 8 children of every survivor (child c = 2 (i,j,k) + bits of c) with the parent's
 // mask; otherwise writes the survivors themselves.  `bounded` = 0 keeps every cell with its mask.
 // The number of written cells goes to *d_count (device int64).
+// Ancestor bounds carried to the children (for the proposer's features): in_c / in_s / in_gap per
+// input cell (in_gap == nullptr: 0, i.e. the cell itself was bounded), written with gap + 1 to
+// every child; out_c == nullptr: nothing carried.
+struct AncIO {
+  const float* in_c = nullptr;
+  const float* in_s = nullptr;
+  const uint8_t* in_gap = nullptr;
+  float* out_c = nullptr;
+  float* out_s = nullptr;
+  uint8_t* out_gap = nullptr;
+};
 isx_status level_step(isx_inr inr, const uint32_t* codes, const uint32_t* masks, int64_t n,
                       const float* center, const float* spread, bool bounded, const IsoSet& iso,
                       isx_bound_mode mode, float k, int inflate, bool expand, uint32_t* out_codes,
-                      uint32_t* out_masks, int64_t* d_count, cudaStream_t st);
+                      uint32_t* out_masks, int64_t* d_count, cudaStream_t st, const AncIO* anc = nullptr);
 
 // Stable compaction of the indices i < n with flags[i] != 0 into out_idx; count to *d_count.
 isx_status compact_flags(isx_inr inr, const uint8_t* flags, int64_t n, uint32_t* out_idx,
@@ -145,6 +164,19 @@ isx_status scan_block_counts(isx_inr inr, const int* counts, int64_t nb, int64_t
                              cudaStream_t st);
 // out[i] = i for i < n.
 isx_status iota_u32(uint32_t* out, int64_t n, cudaStream_t st);
+
+// ---- proposer (proposer.cu) ----------------------------------------------------------------------
+// keep[i] = iso bits of cell i kept without a bound (logit >= z_hi), need[i] = 1 if some bit of its
+// mask is undecided (z_lo < logit < z_hi); bits with logit <= z_lo are dropped.
+isx_status proposer_gate(isx_proposer p, const uint32_t* codes, const uint32_t* masks, const float* anc_c,
+                         const float* anc_s, const uint8_t* anc_gap, int64_t n, int level, const IsoSet& iso,
+                         float z_lo, float z_hi, uint32_t* keep, uint8_t* need, cudaStream_t st);
+// For the bounded cells idx[j]: keep[idx[j]] = masks[idx[j]] & cull(bound j); their bound becomes
+// the ancestor bound (gap 0).
+isx_status proposer_merge(const uint32_t* idx, int64_t nb, const uint32_t* masks, const float* c_sub,
+                          const float* s_sub, const IsoSet& iso, isx_bound_mode mode, float k, int inflate,
+                          uint32_t* keep, float* anc_c, float* anc_s, uint8_t* anc_gap, cudaStream_t st);
+isx_status gather_codes(const uint32_t* codes, const uint32_t* idx, int64_t nb, uint32_t* out, cudaStream_t st);
 
 // ---- mesh (mesh.cu) ----------------------------------------------------------------------------
 // flags[lattice id] = 1 for the 8 corners of every listed cell of the R^3 grid.

@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(1024) k_scan_counts(const int* counts, int64_t
 
 __global__ void __launch_bounds__(kThreads) k_scatter_cells(const uint32_t* codes, const uint32_t* newmask,
                                                             int64_t n, const int64_t* offsets, int expand,
-                                                            uint32_t* out_codes, uint32_t* out_masks) {
+                                                            uint32_t* out_codes, uint32_t* out_masks, AncIO anc) {
   __shared__ int warp_sums[32];
   __shared__ int total;
   int64_t base = (int64_t)blockIdx.x * kTile;
@@ -170,9 +170,24 @@ __global__ void __launch_bounds__(kThreads) k_scatter_cells(const uint32_t* code
           out_codes[8 * o + c] = cc;
           out_masks[8 * o + c] = m;
         }
+        if (anc.out_c) {
+          const float ac = anc.in_c[i], as = anc.in_s[i];
+          const int g = anc.in_gap ? anc.in_gap[i] : 0;
+          const uint8_t gc = (uint8_t)min(g + 1, 255);
+          for (int c = 0; c < 8; ++c) {
+            anc.out_c[8 * o + c] = ac;
+            anc.out_s[8 * o + c] = as;
+            anc.out_gap[8 * o + c] = gc;
+          }
+        }
       } else {
         out_codes[o] = code;
         out_masks[o] = m;
+        if (anc.out_c) {
+          anc.out_c[o] = anc.in_c[i];
+          anc.out_s[o] = anc.in_s[i];
+          anc.out_gap[o] = anc.in_gap ? anc.in_gap[i] : 0;
+        }
       }
     }
     off += total;
@@ -227,7 +242,7 @@ isx_status iota_u32(uint32_t* out, int64_t n, cudaStream_t st) {
 isx_status level_step(isx_inr inr, const uint32_t* codes, const uint32_t* masks, int64_t n,
                       const float* center, const float* spread, bool bounded, const IsoSet& iso,
                       isx_bound_mode mode, float k, int inflate, bool expand, uint32_t* out_codes,
-                      uint32_t* out_masks, int64_t* d_count, cudaStream_t st) {
+                      uint32_t* out_masks, int64_t* d_count, cudaStream_t st, const AncIO* anc) {
   if (n == 0) {
     ISX_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int64_t), st));
     return ISX_OK;
@@ -253,7 +268,8 @@ isx_status level_step(isx_inr inr, const uint32_t* codes, const uint32_t* masks,
   ISX_LAUNCH_CHECK("k_scan_counts");
   {
     prof::Scope _ps(K_SCATTER, st, 0, 0);
-    k_scatter_cells<<<(unsigned)nb, kThreads, 0, st>>>(codes, nm, n, boff, expand ? 1 : 0, out_codes, out_masks);
+    k_scatter_cells<<<(unsigned)nb, kThreads, 0, st>>>(codes, nm, n, boff, expand ? 1 : 0, out_codes, out_masks,
+                                                       anc ? *anc : AncIO());
   }
   ISX_LAUNCH_CHECK("k_scatter_cells");
   return ISX_OK;

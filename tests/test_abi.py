@@ -57,3 +57,41 @@ def test_argument_errors_without_gpu(lib):
     desc = _lib.InrDesc(2, dims, W, W)
     assert lib.isx_create_inr(C.byref(desc), C.byref(h)) == 5
     assert lib.isx_version() == 100
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """The ctypes mirrors of isx_extract_params and isx_mesh have the C compiler's sizes and offsets."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    from paper_2402_13861_gb300 import _lib
+    src = tmp_path / "layout.c"
+    fields_p = [f for f, _ in _lib.ExtractParams._fields_]
+    fields_m = [f for f, _ in _lib.Mesh._fields_]
+    body = "\n".join([f'printf("P {f} %zu\\n", offsetof(isx_extract_params, {f}));' for f in fields_p] +
+                     [f'printf("M {f} %zu\\n", offsetof(isx_mesh, {f}));' for f in fields_m] +
+                     ['printf("SP %zu\\nSM %zu\\n", sizeof(isx_extract_params), sizeof(isx_mesh));'])
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "isx.h"\nint main(void){' + body + 'return 0;}\n')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                          check=True).stdout.splitlines())
+    for f in fields_p:
+        assert int(out[f"P {f}"]) == getattr(_lib.ExtractParams, f).offset, f
+    for f in fields_m:
+        assert int(out[f"M {f}"]) == getattr(_lib.Mesh, f).offset, f
+    assert int(out["SP"]) == C.sizeof(_lib.ExtractParams) and int(out["SM"]) == C.sizeof(_lib.Mesh)
+
+
+def test_proposer_argument_errors_without_gpu(lib):
+    h = C.c_void_p()
+    f32p = C.POINTER(C.c_float)
+    assert lib.isx_proposer_create(None, None, None, C.byref(h)) == 1
+    params = np.zeros(8961, dtype=np.float32)
+    mean = np.zeros(8, dtype=np.float32)
+    std = np.zeros(8, dtype=np.float32)          # std must be > 0
+    assert lib.isx_proposer_create(params.ctypes.data_as(f32p), mean.ctypes.data_as(f32p),
+                                   std.ctypes.data_as(f32p), C.byref(h)) == 1
+    assert b"standard deviation" in lib.isx_last_error()
+    assert lib.isx_proposer_predict(None, None, 0, None, None) == 1

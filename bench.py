@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--max-level", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
     return ap.parse_args()
 
 
@@ -115,6 +116,58 @@ def traffic_per_cell(kernel, src_file):
         return rec["dram_bytes_per_cell"] if rec.get("src_sha") == sha else None
     except Exception:
         return None
+
+
+def extraction_forms(pkg, net, L, isos, plain, plain_ms, mode, k, prec):
+    """End-to-end time of the other extraction forms on the same INR and isos, and the crossing
+    (cell, iso) pairs of the dense extraction each form misses: bounding stopped at level 6 with
+    tensor-core corner values, the proposer-assisted form (committed proposer), dense extraction
+    (FP32 and tensor-core evaluation).  Each form runs once after a warm-up of the same call."""
+    import torch
+    from paper_2402_13861_gb300 import proposer as gp
+    from paper_2402_13861_gb300.train_proposer import missed
+    st = torch.cuda.current_stream()
+    bufs = {}
+
+    def timed(**kw):
+        for rep in range(2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            r = net.extract(L, isos, buffers=bufs, active_cap=1 << 27, tri_cap=1 << 25, **kw)
+            b.record(st)
+            torch.cuda.synchronize()
+        return r, a.elapsed_time(b)
+
+    dense32, ms_d32 = timed(prec="fp32", dense=True)
+    cross = None
+    cell = dense32["tri_cell"].to(torch.int64) & 0xFFFFFFFF
+    tiso = dense32["tri_iso"].to(torch.int64)
+    key = torch.unique(cell)
+    masks = torch.zeros_like(key)
+    for q in range(len(isos)):
+        kq = torch.unique(cell[tiso == q])
+        if kq.numel():
+            masks[torch.searchsorted(key, kq)] |= 1 << q
+    cross = (key, masks)
+    out = {}
+    mp, tot = missed(plain["codes"], plain["masks"], cross)
+    out["plain"] = {"ms": plain_ms, "cells_bounded": int(sum(plain["cells_bounded"])), "missed_pairs": mp,
+                    "missed_rate": mp / max(tot, 1)}
+    r, ms = timed(mode=mode, k=k, prec=prec, bound_stop_level=6, eval_prec="bf16")
+    m, _ = missed(r["codes"], r["masks"], cross)
+    out["bound_to_level6_tc_eval"] = {"ms": ms, "cells_bounded": int(sum(r["cells_bounded"])),
+                                      "n_active": r["n_active"], "missed_pairs": m, "missed_rate": m / max(tot, 1)}
+    prop, meta = gp.load(os.path.join(ROOT, "synth", "data", "proposer.npz"))
+    r, ms = timed(mode=mode, k=k, prec=prec, proposer=prop, proposer_level=meta["proposer_level"],
+                  tau_lo=meta["tau_lo"], tau_hi=meta["tau_hi"])
+    m, _ = missed(r["codes"], r["masks"], cross)
+    out["proposer"] = {"ms": ms, "cells_bounded": int(sum(r["cells_bounded"])), "missed_pairs": m,
+                       "missed_rate": m / max(tot, 1), **meta}
+    prop.close()
+    _, ms_dtc = timed(prec="fp32", dense=True, eval_prec="bf16")
+    out["dense_fp32_eval"] = {"ms": ms_d32, "crossing_pairs": tot}
+    out["dense_tc_eval"] = {"ms": ms_dtc}
+    return out
 
 
 def cpu_baseline(layers, mode, k, budget_s=12.0):
@@ -294,6 +347,8 @@ def main():
             "cells_bounded_per_step": cells / args.steps / world, "n_active": res["n_active"],
             "n_tris": res["n_tris"], "cells_bounded_per_level": res["cells_bounded"],
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "kernel_time_share": shares}
+    if rank == 0 and world == 1 and not args.no_forms:
+        line["forms"] = extraction_forms(pkg, net, L, isos, res, ms_per_step, args.mode, args.k, prec)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(layers, args.mode, args.k)
     if rank == 0:

@@ -257,3 +257,12 @@ def choose_thresholds(prop, feat, label, miss=2e-4):
         return 0.01, 0.5
     lo = float(torch.quantile(pos.float(), miss)) if pos.numel() > 10 else 0.0
     return max(0.0, min(lo, 0.49)), 0.5
+
+
+def load(path):
+    """(Proposer, metadata) from an .npz written by train_proposer: the parameters, the feature
+    standardisation and the decision settings (tau_lo, tau_hi, proposer_level)."""
+    z = np.load(path)
+    prop = _lib.Proposer(z["params"], z["mean"], z["std"])
+    meta = {"tau_lo": float(z["tau_lo"]), "tau_hi": float(z["tau_hi"]), "proposer_level": int(z["proposer_level"])}
+    return prop, meta

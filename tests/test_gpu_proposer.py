@@ -185,3 +185,29 @@ def test_bad_thresholds_are_rejected(pkg):
     assert e.value.status == 1
     net.close()
     prop.close()
+
+
+def test_trained_proposer_on_held_out_field(pkg):
+    """The committed proposer (trained on fields seeded 2000-2011) on the committed scientific INR
+    (field seed 2, held out) at 128^3: fewer cells bounded than plain extraction, and no more
+    crossing (cell, iso) pairs of the dense extraction missed than plain extraction misses plus 1 %."""
+    import os
+    from paper_2402_13861_gb300 import proposer as gp
+    from paper_2402_13861_gb300.train_proposer import missed
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    layers, isos, _ = inr.load_inr("scientific")
+    net = pkg.Inr(layers)
+    prop, meta = gp.load(os.path.join(root, "synth", "data", "proposer.npz"))
+    L = 7
+    kw = dict(mode="clt", k=3.0, prec="bf16", active_cap=1 << 22, tri_cap=1 << 23)
+    plain = net.extract(L, isos, **kw)
+    assisted = net.extract(L, isos, proposer=prop, proposer_level=meta["proposer_level"], tau_lo=meta["tau_lo"],
+                           tau_hi=meta["tau_hi"], **kw)
+    cross = gp.crossing_cells(net, L, isos)
+    mp, tot = missed(plain["codes"], plain["masks"], cross)
+    ma, _ = missed(assisted["codes"], assisted["masks"], cross)
+    bp, ba = sum(plain["cells_bounded"]), sum(assisted["cells_bounded"])
+    print(f"bounded {bp} -> {ba}; missed pairs plain {mp}, proposer {ma} of {tot}")
+    assert ba < bp and ma <= mp + 0.01 * tot
+    net.close()
+    prop.close()

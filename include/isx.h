@@ -171,6 +171,28 @@ typedef struct {
 isx_status isx_extract_isosurface(isx_inr inr, const isx_extract_params* params, isx_mesh* mesh,
                                   void* stream);
 
+/* ---- batched extraction ----------------------------------------------------------------------
+ * Many extractions run together: the octrees of all entries are walked level-synchronously
+ * (Algorithm 1 for every entry, one level of all of them at a time) and the cells of a level are
+ * bounded by one persistent tensor-core launch per hidden width present, whatever their INR; culling
+ * and compaction run on one list of all entries' cells.  Entries may differ in INR (widths 128 and
+ * 256, any depth), iso-values, k and max_level; they share mode and inflation and use BF16 bounds.
+ * No counterpart in the paper (it extracts one INR at a time).
+ * With use_graph, the first run sizes the level lists (reading each level's count) and later runs
+ * capture the whole level loop once as a CUDA graph and replay it; a replay whose counts exceed the
+ * sized capacities (e.g. INR weights changed in place) is detected on the device and redone sized.
+ * Outputs per entry are as for isx_extract_isosurface (meshes[i] for entry i); ms_acp is the level
+ * loop of the whole batch, cells_bounded / cells_kept are not filled.  The INRs must outlive the
+ * batch.  Errors: ISX_ERR_ARG (mixed devices, modes or inflation; n outside 1..65535),
+ * ISX_ERR_UNSUPPORTED (FP32 bounds, other widths, proposer or bound_stop_level), ISX_ERR_CAPACITY
+ * (an entry's active cells or triangles exceed its caps: its counts are filled, the others run),
+ * ISX_ERR_TIMEOUT, ISX_ERR_CUDA.  isx_batch_run synchronises `stream`. */
+typedef struct isx_batch_s* isx_batch;
+isx_status isx_batch_create(const isx_inr* inrs, const isx_extract_params* params, int n, int use_graph,
+                            isx_batch* out);
+isx_status isx_batch_run(isx_batch batch, isx_mesh* meshes, void* stream);
+isx_status isx_batch_destroy(isx_batch batch);
+
 /* The dense baseline of Sec. V-A.4: evaluates every lattice point of the (2^max_level + 1)^3 grid
  * and runs marching cubes in every cell.  d_active_* are not written (n_active = cells with at least
  * one triangle).  mode, k, inflate and bound_stop_level are ignored. */

@@ -93,6 +93,9 @@ def load(path: Path | None = None):
     lib.isx_profile_reset.restype = None
     lib.isx_profile_read.argtypes = [C.POINTER(KernelStats), C.c_int]
     lib.isx_profile_read.restype = C.c_int
+    lib.isx_batch_create.argtypes = [C.POINTER(vp), C.POINTER(ExtractParams), C.c_int, C.c_int, C.POINTER(vp)]
+    lib.isx_batch_run.argtypes = [vp, C.POINTER(Mesh), vp]
+    lib.isx_batch_destroy.argtypes = [vp]
     lib.isx_proposer_create.argtypes = [f32p, f32p, f32p, C.POINTER(vp)]
     lib.isx_proposer_destroy.argtypes = [vp]
     lib.isx_proposer_get_params.argtypes = [vp, f32p]
@@ -102,7 +105,7 @@ def load(path: Path | None = None):
     for name in ("isx_create_inr", "isx_destroy_inr", "isx_bound_cells", "isx_eval_points",
                  "isx_extract_isosurface", "isx_extract_dense", "isx_mc_table", "isx_proposer_create",
                  "isx_proposer_destroy", "isx_proposer_get_params", "isx_proposer_predict", "isx_proposer_grad",
-                 "isx_proposer_train_step"):
+                 "isx_proposer_train_step", "isx_batch_create", "isx_batch_run", "isx_batch_destroy"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -336,3 +339,72 @@ class Proposer:
         """One Adam step on a labelled mini-batch; ``loss`` (CUDA float32 [1]) receives its loss."""
         _check(load().isx_proposer_train_step(self._h, _ptr(feat), _ptr(label), feat.shape[0], float(lr),
                                               _ptr(loss), _stream_ptr(stream)))
+
+
+class Batch:
+    """Many extractions run level-synchronously (wraps isx_batch).  ``nets``: Inr objects; ``params``:
+    one dict of Inr.params keyword arguments per entry (max_level, isos, mode, k, prec, ...)."""
+
+    def __init__(self, nets, params, use_graph=True):
+        lib = load()
+        self.nets = list(nets)
+        self.params = [Inr.params(**p) for p in params]
+        self.max_levels = [p["max_level"] for p in params]
+        n = len(self.nets)
+        hs = (C.c_void_p * n)(*[net.handle for net in self.nets])
+        ps = (ExtractParams * n)(*self.params)
+        h = C.c_void_p()
+        _check(lib.isx_batch_create(hs, ps, n, int(bool(use_graph)), C.byref(h)))
+        self._h = h
+        self._bufs = [dict() for _ in range(n)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().isx_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, active_cap=1 << 16, tri_cap=1 << 18, stream=None):
+        """Runs every entry; grows the per-entry output buffers and reruns on a capacity error."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        n = len(self.nets)
+        caps = [[active_cap, tri_cap] for _ in range(n)]
+        for attempt in range(3):
+            meshes = (Mesh * n)()
+            for i, b in enumerate(self._bufs):
+                ac, tc = caps[i]
+                if b.get("active_cap", -1) < ac:
+                    b["code"] = torch.empty(max(ac, 1), dtype=torch.int32, device=dev)
+                    b["mask"] = torch.empty(max(ac, 1), dtype=torch.int32, device=dev)
+                    b["active_cap"] = ac
+                if b.get("tri_cap", -1) < tc:
+                    b["vert"] = torch.empty((max(tc, 1), 3, 3), dtype=torch.float32, device=dev)
+                    b["edge"] = torch.empty((max(tc, 1), 3), dtype=torch.int64, device=dev)
+                    b["iso"] = torch.empty(max(tc, 1), dtype=torch.int32, device=dev)
+                    b["cell"] = torch.empty(max(tc, 1), dtype=torch.int32, device=dev)
+                    b["tri_cap"] = tc
+                m = meshes[i]
+                m.d_active_code, m.d_active_mask, m.active_cap = b["code"].data_ptr(), b["mask"].data_ptr(), b["active_cap"]
+                m.d_tri_vert, m.d_tri_edge = b["vert"].data_ptr(), b["edge"].data_ptr()
+                m.d_tri_iso, m.d_tri_cell, m.tri_cap = b["iso"].data_ptr(), b["cell"].data_ptr(), b["tri_cap"]
+            st = load().isx_batch_run(self._h, meshes, _stream_ptr(stream))
+            if st == 3 and attempt < 2:
+                for i in range(n):
+                    caps[i] = [max(caps[i][0], int(meshes[i].n_active)), max(caps[i][1], int(meshes[i].n_tris))]
+                continue
+            _check(st)
+            break
+        out = []
+        for i, b in enumerate(self._bufs):
+            m = meshes[i]
+            na, nt = int(m.n_active), int(m.n_tris)
+            out.append(dict(codes=b["code"][:na], masks=b["mask"][:na], tri_vert=b["vert"][:nt],
+                            tri_edge=b["edge"][:nt], tri_iso=b["iso"][:nt], tri_cell=b["cell"][:nt], n_active=na,
+                            n_tris=nt, n_points=int(m.n_points), ms_acp=m.ms_acp, ms_inr=m.ms_inr, ms_mc=m.ms_mc))
+        return out

@@ -72,17 +72,6 @@ isx_status bound_dispatch(isx_inr inr, const CellSource& src, int64_t n, isx_bou
   return bound_fp32(inr, src, n, mode, inflate, center, spread, st);
 }
 
-struct Timer {
-  cudaEvent_t ev[4] = {};
-  isx_status init() {
-    for (auto& e : ev) ISX_CUDA(cudaEventCreate(&e));
-    return ISX_OK;
-  }
-  ~Timer() {
-    for (auto& e : ev)
-      if (e) cudaEventDestroy(e);
-  }
-};
 
 isx_status validate_params(const isx_extract_params* p, const isx_mesh* m) {
   if (!p || !m) {
@@ -141,6 +130,63 @@ IsoSet iso_of(const isx_extract_params* p) {
 }  // namespace isx
 
 using namespace isx;
+
+namespace isx {
+isx_status validate_extract_params(const isx_extract_params* p, const isx_mesh* m) { return validate_params(p, m); }
+IsoSet iso_set_of(const isx_extract_params* p) { return iso_of(p); }
+
+// Active cells -> mesh (Sec. IV-D): copies the active list to the caller's buffers, evaluates the
+// distinct lattice corners of the active cells and runs marching cubes in them.  `codes` / `masks`
+// hold n cells of level p->max_level; timer event 0 was recorded by the caller.
+isx_status mesh_from_active(isx_inr inr, const isx_extract_params* p, const uint32_t* codes, const uint32_t* masks,
+                            int64_t n, isx_mesh* mesh, Timer& tm, cudaStream_t st) {
+  const int R = 1 << p->max_level;
+  const IsoSet iso = iso_of(p);
+  auto& ws = inr->ws;
+  ISX_TRY(ws[WS_COUNT].ensure(64, "count"));
+  int64_t* d_count = ws[WS_COUNT].as<int64_t>();
+  ISX_CUDA(cudaEventRecord(tm.ev[1], st));
+  mesh->n_active = n;
+  if (n > mesh->active_cap) {
+    set_error("active-cell capacity exceeded");
+    return ISX_ERR_CAPACITY;
+  }
+  if (n > 0) {
+    if (!mesh->d_active_code || !mesh->d_active_mask) {
+      set_error("null active-cell output buffer");
+      return ISX_ERR_ARG;
+    }
+    ISX_CUDA(cudaMemcpyAsync(mesh->d_active_code, codes, n * 4, cudaMemcpyDeviceToDevice, st));
+    ISX_CUDA(cudaMemcpyAsync(mesh->d_active_mask, masks, n * 4, cudaMemcpyDeviceToDevice, st));
+  }
+  // distinct corners of the active cells
+  int64_t nlat = (int64_t)(R + 1) * (R + 1) * (R + 1);
+  ISX_TRY(ws[WS_LATTICE_FLAG].ensure((size_t)nlat, "lattice flags"));
+  ISX_TRY(ws[WS_LATTICE_IDX].ensure((size_t)nlat * 4, "lattice map"));
+  ISX_CUDA(cudaMemsetAsync(ws[WS_LATTICE_FLAG].ptr, 0, (size_t)nlat, st));
+  ISX_TRY(mark_corners(codes, n, R, ws[WS_LATTICE_FLAG].as<uint8_t>(), st));
+  int64_t npts_cap = std::min<int64_t>(nlat, 8 * std::max<int64_t>(n, 1));
+  ISX_TRY(ws[WS_POINTS].ensure((size_t)npts_cap * 4, "points"));
+  ISX_TRY(compact_flags(inr, ws[WS_LATTICE_FLAG].as<uint8_t>(), nlat, ws[WS_POINTS].as<uint32_t>(),
+                        ws[WS_LATTICE_IDX].as<uint32_t>(), d_count, st));
+  int64_t npts = 0;
+  ISX_CUDA(cudaMemcpyAsync(&npts, d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  ISX_CUDA(cudaStreamSynchronize(st));
+  mesh->n_points = npts;
+  ISX_TRY(ws[WS_VALUES].ensure((size_t)std::max<int64_t>(npts, 1) * 4, "values"));
+  ISX_TRY(eval_dispatch(inr, p->eval_prec, ws[WS_POINTS].as<uint32_t>(), R, npts, ws[WS_VALUES].as<float>(), st));
+  ISX_CUDA(cudaEventRecord(tm.ev[2], st));
+  isx_status s = marching_cubes(inr, codes, masks, n, R, ws[WS_LATTICE_IDX].as<uint32_t>(),
+                                ws[WS_VALUES].as<float>(), iso, mesh, false, st);
+  ISX_CUDA(cudaEventRecord(tm.ev[3], st));
+  ISX_CUDA(cudaEventSynchronize(tm.ev[3]));
+  cudaEventElapsedTime(&mesh->ms_acp, tm.ev[0], tm.ev[1]);
+  cudaEventElapsedTime(&mesh->ms_inr, tm.ev[1], tm.ev[2]);
+  cudaEventElapsedTime(&mesh->ms_mc, tm.ev[2], tm.ev[3]);
+  cudaEventElapsedTime(&mesh->ms_total, tm.ev[0], tm.ev[3]);
+  return s;
+}
+}  // namespace isx
 
 extern "C" {
 
@@ -251,6 +297,11 @@ isx_status isx_create_inr(const isx_inr_desc* d, isx_inr* out) {
         (e = cudaMemcpy(inr->Wt_bf16[l], tb.data(), (size_t)fi * fo * 2, cudaMemcpyHostToDevice)) != cudaSuccess)
       return fail(cuda_fail(e, "weight copy", __FILE__, __LINE__));
   }
+  if (bf16_supported(inr)) {
+    const void* net = nullptr;
+    isx_status st = tc_net_of(inr, &net);
+    if (st != ISX_OK) return fail(st);
+  }
   *out = inr;
   return ISX_OK;
 }
@@ -268,6 +319,7 @@ isx_status isx_destroy_inr(isx_inr inr) {
   for (auto* p : inr->Wabs_bf16) if (p) cudaFree(p);
   for (auto* p : inr->Wsq_bf16) if (p) cudaFree(p);
   for (auto* p : inr->Wlo_bf16) if (p) cudaFree(p);
+  if (inr->tc_net) cudaFree(inr->tc_net);
   for (auto* p : inr->absW_rowsum) if (p) cudaFree(p);
   for (auto& buf : inr->ws) buf.release();
   if (prev >= 0) cudaSetDevice(prev);
@@ -422,48 +474,7 @@ isx_status isx_extract_isosurface(isx_inr inr, const isx_extract_params* p, isx_
     std::swap(aga, agb);
     n = cnt;
   }
-  ISX_CUDA(cudaEventRecord(tm.ev[1], st));
-  mesh->n_active = n;
-  if (n > mesh->active_cap) {
-    set_error("active-cell capacity exceeded");
-    return ISX_ERR_CAPACITY;
-  }
-  const uint32_t* codes = ws[ca].as<uint32_t>();
-  const uint32_t* masks = ws[ma].as<uint32_t>();
-  if (n > 0) {
-    if (!mesh->d_active_code || !mesh->d_active_mask) {
-      set_error("null active-cell output buffer");
-      return ISX_ERR_ARG;
-    }
-    ISX_CUDA(cudaMemcpyAsync(mesh->d_active_code, codes, n * 4, cudaMemcpyDeviceToDevice, st));
-    ISX_CUDA(cudaMemcpyAsync(mesh->d_active_mask, masks, n * 4, cudaMemcpyDeviceToDevice, st));
-  }
-  // distinct corners of the active cells
-  int64_t nlat = (int64_t)(R + 1) * (R + 1) * (R + 1);
-  ISX_TRY(ws[WS_LATTICE_FLAG].ensure((size_t)nlat, "lattice flags"));
-  ISX_TRY(ws[WS_LATTICE_IDX].ensure((size_t)nlat * 4, "lattice map"));
-  ISX_CUDA(cudaMemsetAsync(ws[WS_LATTICE_FLAG].ptr, 0, (size_t)nlat, st));
-  ISX_TRY(mark_corners(codes, n, R, ws[WS_LATTICE_FLAG].as<uint8_t>(), st));
-  int64_t npts_cap = std::min<int64_t>(nlat, 8 * std::max<int64_t>(n, 1));
-  ISX_TRY(ws[WS_POINTS].ensure((size_t)npts_cap * 4, "points"));
-  ISX_TRY(compact_flags(inr, ws[WS_LATTICE_FLAG].as<uint8_t>(), nlat, ws[WS_POINTS].as<uint32_t>(),
-                        ws[WS_LATTICE_IDX].as<uint32_t>(), d_count, st));
-  int64_t npts = 0;
-  ISX_CUDA(cudaMemcpyAsync(&npts, d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  ISX_CUDA(cudaStreamSynchronize(st));
-  mesh->n_points = npts;
-  ISX_TRY(ws[WS_VALUES].ensure((size_t)std::max<int64_t>(npts, 1) * 4, "values"));
-  ISX_TRY(eval_dispatch(inr, p->eval_prec, ws[WS_POINTS].as<uint32_t>(), R, npts, ws[WS_VALUES].as<float>(), st));
-  ISX_CUDA(cudaEventRecord(tm.ev[2], st));
-  isx_status s = marching_cubes(inr, codes, masks, n, R, ws[WS_LATTICE_IDX].as<uint32_t>(),
-                                ws[WS_VALUES].as<float>(), iso, mesh, false, st);
-  ISX_CUDA(cudaEventRecord(tm.ev[3], st));
-  ISX_CUDA(cudaEventSynchronize(tm.ev[3]));
-  cudaEventElapsedTime(&mesh->ms_acp, tm.ev[0], tm.ev[1]);
-  cudaEventElapsedTime(&mesh->ms_inr, tm.ev[1], tm.ev[2]);
-  cudaEventElapsedTime(&mesh->ms_mc, tm.ev[2], tm.ev[3]);
-  cudaEventElapsedTime(&mesh->ms_total, tm.ev[0], tm.ev[3]);
-  return s;
+  return mesh_from_active(inr, p, ws[ca].as<uint32_t>(), ws[ma].as<uint32_t>(), n, mesh, tm, st);
 }
 
 isx_status isx_extract_dense(isx_inr inr, const isx_extract_params* p, isx_mesh* mesh, void* stream) {

@@ -67,14 +67,28 @@ constexpr float kUb = 0.00390625f;                                 // 2^-8
 constexpr float kUa = 7.62939453125e-06f;                          // 2^-17
 constexpr float kGemvSafe = 1.015625f;                             // 1 + 2^-6: bf16 GEMV results bounded above
 
-struct TcArgs {
-  CellSource src;
-  int64_t n;
-  int mode, inflate, w, H;
+// One network of a launch: its weights and the tensor maps of its BF16 copies (device memory,
+// 64-byte aligned; written by the host before the launch).
+struct alignas(64) TcNet {
+  CUtensorMap wt[ISX_MAX_LAYERS];      // W_l^T bf16, box {64, 128}: A of implicit blocks
+  CUtensorMap wrow[ISX_MAX_LAYERS];    // W_l bf16, box {64, w}: source of B = D W^T
+  CUtensorMap wabs[ISX_MAX_LAYERS];    // |W_l| bf16, box {64, 128}: A of the sound reduction pass
+  CUtensorMap wsq[ISX_MAX_LAYERS];     // W_l^2 bf16, box {64, 128}: A of the CLT reduction pass
   const float* W[ISX_MAX_LAYERS];
   const float* Wt[ISX_MAX_LAYERS];
   const float* b[ISX_MAX_LAYERS];
   float bout;
+  int H;
+  int w;                               // cells of networks of another width are skipped
+};
+
+struct TcArgs {
+  CellSource src;
+  int64_t n;
+  const int64_t* n_dev;                // if set, the cell count is read from device memory
+  int mode, inflate, w;
+  const TcNet* nets;                   // device array of networks
+  const uint16_t* cell_net;            // network of every cell (nullptr: all cells use nets[0])
   __nv_bfloat16* scratch;
   int rows_per_cta;
   float* center;
@@ -89,11 +103,6 @@ __device__ __forceinline__ void math_sync() { asm volatile("bar.sync 1, %0;" ::"
 
 struct TcMaps {
   CUtensorMap scratch;                 // [rows][w] bf16, box {64, 128}
-  CUtensorMap wt[ISX_MAX_LAYERS];      // W_l^T bf16, box {64, 128}: A of implicit blocks
-  CUtensorMap wrow[ISX_MAX_LAYERS];    // W_l bf16, box {64, w}: source of B = D W^T
-  CUtensorMap wa[ISX_MAX_LAYERS];      // W_l bf16, box {64, 128}: A of the I-row pass
-  CUtensorMap wabs[ISX_MAX_LAYERS];    // |W_l| bf16, box {64, 128}: A of the sound reduction pass
-  CUtensorMap wsq[ISX_MAX_LAYERS];     // W_l^2 bf16, box {64, 128}: A of the CLT reduction pass
 };
 
 // ---- shared-memory layout ------------------------------------------------------------------------------
@@ -291,7 +300,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
   constexpr int MT = W / 128;              // 128-row tiles per block of w rows
   constexpr int KC = W / 64;               // 64-wide K chunks
   constexpr int R = kRingBytes / (4 * W);  // weight rows per ring stage
-  const int H = args.H;
+  const int64_t ncell = args.n_dev ? *args.n_dev : args.n;
   Smem s = carve(smem_raw, W);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int mode = args.mode;
@@ -346,14 +355,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
         if (++stage == kStages) { stage = 0; sphase ^= 1; }
         return true;
       };
-      for (int64_t cell = blockIdx.x; cell < args.n && ok; cell += gridDim.x) {
+      for (int64_t cell = blockIdx.x; cell < ncell && ok; cell += gridDim.x) {
+        const TcNet& N = args.nets[args.cell_net ? args.cell_net[cell] : 0];
+        const int H = N.H;
+        if (N.w != W) continue;
         for (int j = 1; j <= H - 1 && ok; ++j) {
           if (j >= 2) {
             // B source: W_j once the previous layer's MMAs no longer read B
             if (!wait_bar(s, &s.bar[BAR_BFREE], (bfree_n & 1) ^ 1, args.status)) { ok = false; break; }
             ++bfree_n;
             mbar_expect_tx(&s.bar[BAR_WLOADED], (uint32_t)(W * W * 2));
-            for (int c = 0; c < KC; ++c) tma_load_2d(s.B + (size_t)c * W * 128, &maps.wrow[j], &s.bar[BAR_WLOADED], c * 64, 0);
+            for (int c = 0; c < KC; ++c) tma_load_2d(s.B + (size_t)c * W * 128, &N.wrow[j], &s.bar[BAR_WLOADED], c * 64, 0);
             // the previous layer is complete (its stored rows are read below); the proxy fence
             // orders the epilogue's generic stores, acquired through RED, before this thread's TMA reads
             if (!wait_bar(s, &s.bar[BAR_RED], red_n & 1, args.status)) { ok = false; break; }
@@ -362,7 +374,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
           }
           // reduction pass: A = |W_j| (sound) or W_j^2 (CLT) against the small B columns
           {
-            const CUtensorMap* m = clt ? &maps.wsq[j] : &maps.wabs[j];
+            const CUtensorMap* m = clt ? &N.wsq[j] : &N.wabs[j];
             for (int mt = 0; mt < MT && ok; ++mt)
               for (int c = 0; c < KC; ++c)
                 if (!load_a(m, c * 64, mt * 128)) { ok = false; break; }
@@ -373,7 +385,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
               const int blk = t / MT + 1, sub = t % MT;      // G_blk
               const bool implicit = (blk == j - 1);
               for (int c = 0; c < KC; ++c) {
-                bool good = implicit ? load_a(&maps.wt[j - 1], c * 64, sub * 128)
+                bool good = implicit ? load_a(&N.wt[j - 1], c * 64, sub * 128)
                                      : load_a(&maps.scratch, c * 64, scratch_row0 + (blk - 1) * W + sub * 128);
                 if (!good) { ok = false; break; }
               }
@@ -408,10 +420,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
         }
         return true;
       };
-      for (int64_t cell = blockIdx.x; cell < args.n && ok; cell += gridDim.x) {
-        for (int j = 1; j <= H - 1 && ok; ++j) ok = push(args.Wt[j]);      // centre of z_{j+1}
-        if (ok) ok = push(args.W[H - 1]);                                   // v
-        if (ok && H >= 3) ok = push(args.W[H - 2]);                         // implicit G_{H-2}
+      for (int64_t cell = blockIdx.x; cell < ncell && ok; cell += gridDim.x) {
+        const TcNet& N = args.nets[args.cell_net ? args.cell_net[cell] : 0];
+        const int H = N.H;
+        if (N.w != W) continue;
+        for (int j = 1; j <= H - 1 && ok; ++j) ok = push(N.Wt[j]);      // centre of z_{j+1}
+        if (ok) ok = push(N.W[H - 1]);                                   // v
+        if (ok && H >= 3) ok = push(N.W[H - 2]);                         // implicit G_{H-2}
       }
     }
   } else if (warp == 1) {
@@ -441,7 +456,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
         ++tiles_done;
         return true;
       };
-      for (int64_t cell = blockIdx.x; cell < args.n && ok; cell += gridDim.x) {
+      for (int64_t cell = blockIdx.x; cell < ncell && ok; cell += gridDim.x) {
+        const TcNet& N = args.nets[args.cell_net ? args.cell_net[cell] : 0];
+        const int H = N.H;
+        if (N.w != W) continue;
         for (int j = 1; j <= H - 1 && ok; ++j) {
           if (!wait_bar(s, &s.bar[BAR_BREADY], bready_n & 1, args.status)) { ok = false; break; }
           ++bready_n;
@@ -482,7 +500,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
       if (lane == 0) mbar_arrive(&s.bar[BAR_TEMPTY + acc]);
       ++tiles_done;
     };
-    for (int64_t cell = blockIdx.x; cell < args.n; cell += gridDim.x) {
+    for (int64_t cell = blockIdx.x; cell < ncell; cell += gridDim.x) {
+      const TcNet& N = args.nets[args.cell_net ? args.cell_net[cell] : 0];
+      const int H = N.H;
+      if (N.w != W) continue;
       if (__shfl_sync(0xffffffffu, *(volatile int*)s.abort, 0)) break;
       bool ok = true;
       for (int j = 1; j <= H - 1 && ok; ++j) {
@@ -607,7 +628,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
       math_sync();
       return s.scal[63] == 0.f;
     };
-    for (int64_t cell = blockIdx.x; cell < args.n; cell += gridDim.x) {
+    for (int64_t cell = blockIdx.x; cell < ncell; cell += gridDim.x) {
+      const TcNet& N = args.nets[args.cell_net ? args.cell_net[cell] : 0];
+      const int H = N.H;
+      if (N.w != W) continue;
       if (mt == 0) s.scal[63] = *(volatile int*)s.abort ? 1.f : 0.f;
       math_sync();
       if (s.scal[63] != 0.f) break;
@@ -635,9 +659,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
         if (clt)
           for (int d = 0; d < 3; ++d) h[d] *= 0.57735026918962576f;
       }
-      const float* W0 = args.W[0];
+      const float* W0 = N.W[0];
       for (int nn = mt; nn < W; nn += kMathThreads) {
-        float w0 = W0[3 * nn], w1 = W0[3 * nn + 1], w2 = W0[3 * nn + 2], b0 = args.b[0][nn];
+        float w0 = W0[3 * nn], w1 = W0[3 * nn + 1], w2 = W0[3 * nn + 2], b0 = N.b[0][nn];
         float c = fmaf(w2, xc[2], fmaf(w1, xc[1], fmaf(w0, xc[0], b0)));
         float x0 = h[0] * w0, x1 = h[1] * w1, x2 = h[2] * w2;
         s.I[nn] = x0;
@@ -704,7 +728,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
 #pragma unroll
           for (int e = 0; e < NPT; ++e) {
             const int nn = mt + e * kMathThreads;
-            s.c[nn] = acc[0][e] + args.b[j][nn];
+            s.c[nn] = acc[0][e] + N.b[j][nn];
             s.Inew[nn] = acc[1][e];
             s.Inew[W + nn] = acc[2][e];
             s.Inew[2 * W + nn] = acc[3][e];
@@ -716,7 +740,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
         ++red_n;
         if (mt == 0) trace(args, 0, cell / gridDim.x, 4 + 4 * (j - 1));
         const bool stored = (j >= 2) && (j < H - 1);
-        const float* bj = args.b[j];
+        const float* bj = N.b[j];
         for (int nn = mt; nn < W; nn += kMathThreads) {
           const float tc = (j >= 2) ? s.red[nn] + s.red[W + nn] + s.red[2 * W + nn] + s.red[3 * W + nn] : 0.f;
           const float i0 = s.Inew[nn], i1 = s.Inew[W + nn], i2 = s.Inew[2 * W + nn];
@@ -739,7 +763,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
       // ---- ReLU H, then the output layer (through layer H-1 for the G rows) ----
       float* al = s.alpha + (H % 3) * W;
       float* ga = s.gamma + (H % 3) * W;
-      const float* wout = args.W[H];
+      const float* wout = N.W[H];
       for (int nn = mt; nn < W; nn += kMathThreads) {
         Lin L = clt ? relu_clt(s.c[nn], s.r[nn]) : relu_sound(s.c[nn], s.r[nn], s.delta[nn], infl);
         al[nn] = L.alpha;
@@ -844,13 +868,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
           ce += s.scal[12 + i];
         }
         if (TO > 0) tot += s.red[0] + s.red[W] + s.red[2 * W] + s.red[3 * W];
-        const float x0 = xp + args.bout;
+        const float x0 = xp + N.bout;
         float sp;
         if (mode == ISX_BOUND_SOUND) {
           sp = tot;
           if (infl)
             sp = __fadd_ru(__fmul_ru(sp, kLinSafe),
-                           (args.kappa_out * ea + gamma_k(W + 2, kLinU) * (ce + fabsf(args.bout))) * 1.01f);
+                           (args.kappa_out * ea + gamma_k(W + 2, kLinU) * (ce + fabsf(N.bout))) * 1.01f);
         } else if (mode == ISX_BOUND_CLT) {
           sp = sqrtf(tot);
         } else {
@@ -916,16 +940,30 @@ isx_status make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t o
 }  // namespace
 
 namespace {
-// Weight tensor maps, shared-memory opt-in and the launch of the width-specialised kernel.
-isx_status launch_tc(isx_inr inr, const TcArgs& a, TcMaps& maps, int grid, cudaStream_t st) {
+// The network descriptor of an INR (tensor maps of its BF16 copies, weight pointers), built once
+// and kept in device memory with the INR.
+isx_status build_net(isx_inr inr, TcNet* h) {
+  std::memset(h, 0, sizeof(*h));
   const int w = inr->w;
   for (int l = 1; l < inr->n_layers - 1; ++l) {
-    ISX_TRY(make_map(&maps.wt[l], inr->Wt_bf16[l], w, w, 64, 128));
-    ISX_TRY(make_map(&maps.wrow[l], inr->W_bf16[l], w, w, 64, w));
-    ISX_TRY(make_map(&maps.wa[l], inr->W_bf16[l], w, w, 64, 128));
-    ISX_TRY(make_map(&maps.wabs[l], inr->Wabs_bf16[l], w, w, 64, 128));
-    ISX_TRY(make_map(&maps.wsq[l], inr->Wsq_bf16[l], w, w, 64, 128));
+    ISX_TRY(make_map(&h->wt[l], inr->Wt_bf16[l], w, w, 64, 128));
+    ISX_TRY(make_map(&h->wrow[l], inr->W_bf16[l], w, w, 64, w));
+    ISX_TRY(make_map(&h->wabs[l], inr->Wabs_bf16[l], w, w, 64, 128));
+    ISX_TRY(make_map(&h->wsq[l], inr->Wsq_bf16[l], w, w, 64, 128));
   }
+  for (int l = 0; l < inr->n_layers; ++l) {
+    h->W[l] = inr->W[l];
+    h->Wt[l] = inr->Wt[l];
+    h->b[l] = inr->b[l];
+  }
+  h->bout = inr->hb[inr->n_layers - 1][0];
+  h->H = inr->H;
+  h->w = inr->w;
+  return ISX_OK;
+}
+
+// Shared-memory opt-in and the launch of the width-specialised kernel.
+isx_status launch_tc(int w, const TcArgs& a, TcMaps& maps, int grid, cudaStream_t st) {
   const size_t smem = smem_bytes(w);
   if (w == 256) {
     ISX_CUDA(cudaFuncSetAttribute(k_bound_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -937,7 +975,65 @@ isx_status launch_tc(isx_inr inr, const TcArgs& a, TcMaps& maps, int grid, cudaS
   ISX_LAUNCH_CHECK("k_bound_tc");
   return ISX_OK;
 }
+
+void set_kappas(TcArgs& a, int w) {
+  const float ub = kUb, ua = kUa, u = kLinU;
+  const float gK = (w * ua) / (1.0f - w * ua), gK32 = (w * u) / (1.0f - w * u);
+  a.kappa = (1 + ub) * (1 + ub) * (1 + ub) * (1 + gK) * (1 + u) - 1;
+  a.kappa_out = (1 + ub) * (1 + gK) * (1 + gK32) * (1 + gK32) * (1 + u) * (1 + u) - 1;
+}
 }  // namespace
+
+// Device copy of the INR's network descriptor (built on first use).
+isx_status tc_net_of(isx_inr inr, const void** out) {
+  if (!inr->tc_net) {
+    TcNet h;
+    ISX_TRY(build_net(inr, &h));
+    void* d = nullptr;
+    ISX_CUDA(cudaMalloc(&d, sizeof(TcNet)));
+    cudaError_t e = cudaMemcpy(d, &h, sizeof(TcNet), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(d);
+      return cuda_fail(e, "network descriptor", __FILE__, __LINE__);
+    }
+    inr->tc_net = d;
+  }
+  *out = inr->tc_net;
+  return ISX_OK;
+}
+
+size_t tc_net_bytes() { return sizeof(TcNet); }
+
+// Bounds the cells of a batch: packed codes at `level`, the network of each cell (an index into
+// d_nets, a device array of descriptors copied from tc_net_of), count read from *n_dev.  Cells of
+// networks of another width than w are skipped.  `scratch` holds grid * rows_per_cta rows of w
+// bf16.  No synchronisation (stream-capturable); a timeout raises *status.
+isx_status bound_bf16_batch(const void* d_nets, int w, int rows_per_cta, const uint32_t* codes,
+                            const uint16_t* cell_net, int level, const int64_t* n_dev, isx_bound_mode mode,
+                            int inflate, float* center, float* spread, __nv_bfloat16* scratch, int grid, int* status,
+                            cudaStream_t st) {
+  TcArgs a{};
+  a.src.codes = codes;
+  a.src.level = level;
+  a.n = 0;
+  a.n_dev = n_dev;
+  a.mode = (int)mode;
+  a.inflate = (mode == ISX_BOUND_SOUND) ? inflate : 0;
+  a.w = w;
+  a.nets = static_cast<const TcNet*>(d_nets);
+  a.cell_net = cell_net;
+  a.scratch = scratch;
+  a.rows_per_cta = rows_per_cta;
+  a.center = center;
+  a.spread = spread;
+  a.status = status;
+  a.trace = nullptr;
+  set_kappas(a, w);
+  TcMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  ISX_TRY(make_map(&maps.scratch, scratch, w, (uint64_t)grid * rows_per_cta, 64, 128));
+  return launch_tc(w, a, maps, grid, st);
+}
 
 isx_status tensor_map_bf16(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
                            uint32_t box_outer) {
@@ -966,28 +1062,21 @@ isx_status bound_bf16(isx_inr inr, const CellSource& src, int64_t n, isx_bound_m
   auto& ws = inr->ws;
   ISX_TRY(ws[WS_TC_SCRATCH].ensure((size_t)sms * rows * w * 2, "tc scratch"));
   ISX_TRY(ws[WS_TC_STATUS].ensure(64, "tc status"));
+  const void* net = nullptr;
+  ISX_TRY(tc_net_of(inr, &net));
   TcArgs a{};
   a.src = src;
   a.n = n;
   a.mode = (int)mode;
   a.inflate = (mode == ISX_BOUND_SOUND) ? inflate : 0;
   a.w = w;
-  a.H = H;
-  for (int l = 0; l < inr->n_layers; ++l) {
-    a.W[l] = inr->W[l];
-    a.Wt[l] = inr->Wt[l];
-    a.b[l] = inr->b[l];
-  }
-  a.bout = inr->hb[inr->n_layers - 1][0];
+  a.nets = static_cast<const TcNet*>(net);
   a.scratch = ws[WS_TC_SCRATCH].as<__nv_bfloat16>();
   a.rows_per_cta = rows;
   a.center = d_center;
   a.spread = d_spread;
   a.status = ws[WS_TC_STATUS].as<int>();
-  const float ub = kUb, ua = kUa, u = kLinU;
-  const float gK = (w * ua) / (1.0f - w * ua), gK32 = (w * u) / (1.0f - w * u);
-  a.kappa = (1 + ub) * (1 + ub) * (1 + ub) * (1 + gK) * (1 + u) - 1;
-  a.kappa_out = (1 + ub) * (1 + gK) * (1 + gK32) * (1 + gK32) * (1 + u) * (1 + u) - 1;
+  set_kappas(a, w);
   TcMaps maps;
   std::memset(&maps, 0, sizeof(maps));
   ISX_TRY(make_map(&maps.scratch, a.scratch, w, (uint64_t)sms * rows, 64, 128));
@@ -1003,7 +1092,7 @@ isx_status bound_bf16(isx_inr inr, const CellSource& src, int64_t n, isx_bound_m
     const double cells = (double)n;
     const double rows_gemm = (double)w * (H - 1) * (H - 2) / 2.0;   // G rows over layers 2..H-1
     prof::Scope ps(K_BOUND_TC, st, cells * 2.0 * w * w * (3.0 * (H - 1) + rows_gemm), 0);
-    ISX_TRY(launch_tc(inr, a, maps, grid, st));
+    ISX_TRY(launch_tc(w, a, maps, grid, st));
   }
   int status = 0;
   ISX_CUDA(cudaMemcpyAsync(&status, a.status, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1115,23 +1204,18 @@ extern "C" isx_status isx_bound_cells_noalloc(isx_inr inr, const float* d_lo, co
   a.mode = (int)mode;
   a.inflate = (mode == ISX_BOUND_SOUND) ? inflate : 0;
   a.w = w;
-  a.H = H;
-  for (int l = 0; l < inr->n_layers; ++l) {
-    a.W[l] = inr->W[l];
-    a.Wt[l] = inr->Wt[l];
-    a.b[l] = inr->b[l];
+  if (!inr->tc_net) {
+    set_error("isx_bound_cells_noalloc: the INR has no network descriptor (created with the INR)");
+    return ISX_ERR_UNSUPPORTED;
   }
-  a.bout = inr->hb[inr->n_layers - 1][0];
+  a.nets = static_cast<const TcNet*>(inr->tc_net);
   a.status = reinterpret_cast<int*>(base);
   a.scratch = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<uint8_t*>(base) + kStaticStatusBytes);
   a.rows_per_cta = (int)(per_cta / (w * 2));
   a.center = d_center;
   a.spread = d_spread;
   a.trace = nullptr;
-  const float ub = kUb, ua = kUa, u = kLinU;
-  const float gK = (w * ua) / (1.0f - w * ua), gK32 = (w * u) / (1.0f - w * u);
-  a.kappa = (1 + ub) * (1 + ub) * (1 + ub) * (1 + gK) * (1 + u) - 1;
-  a.kappa_out = (1 + ub) * (1 + gK) * (1 + gK32) * (1 + gK32) * (1 + u) * (1 + u) - 1;
+  set_kappas(a, w);
   TcMaps maps;
   std::memset(&maps, 0, sizeof(maps));
   ISX_TRY(make_map(&maps.scratch, a.scratch, w, (uint64_t)grid * a.rows_per_cta, 64, 128));
@@ -1141,7 +1225,7 @@ extern "C" isx_status isx_bound_cells_noalloc(isx_inr inr, const float* d_lo, co
   {
     const double rows_gemm = (double)w * (H - 1) * (H - 2) / 2.0;
     prof::Scope ps(K_BOUND_TC, st, (double)n * 2.0 * w * w * (3.0 * (H - 1) + rows_gemm), 0);
-    ISX_TRY(launch_tc(inr, a, maps, grid, st));
+    ISX_TRY(launch_tc(w, a, maps, grid, st));
   }
   int status = 0;
   ISX_CUDA(cudaMemcpyAsync(&status, a.status, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -71,6 +71,7 @@ struct isx_inr_s {
   std::vector<__nv_bfloat16*> Wabs_bf16; // |W[l]| in bfloat16 (row-major)
   std::vector<__nv_bfloat16*> Wsq_bf16;  // W[l]^2 in bfloat16 (row-major)
   std::vector<__nv_bfloat16*> Wlo_bf16;  // W[l] - float(W_bf16[l]) in bfloat16: low part of a two-term split
+  void* tc_net = nullptr;                // device network descriptor of the tensor-core bound kernel
   std::vector<float*> absW_rowsum;       // sum_k |W[l][n][k]| per output neuron
   std::vector<std::vector<float>> hW, hb;  // host copies
   isx::Buf ws[isx::WS_N_SLOTS];
@@ -118,6 +119,13 @@ isx_status bound_fp32(isx_inr inr, const CellSource& src, int64_t n, isx_bound_m
 isx_status bound_bf16(isx_inr inr, const CellSource& src, int64_t n, isx_bound_mode mode,
                       int inflate, float* d_center, float* d_spread, cudaStream_t st);
 bool bf16_supported(isx_inr inr);
+// Device copy of the INR's network descriptor for the tensor-core bound kernel (built on first use).
+isx_status tc_net_of(isx_inr inr, const void** out);
+size_t tc_net_bytes();
+isx_status bound_bf16_batch(const void* d_nets, int w, int rows_per_cta, const uint32_t* codes,
+                            const uint16_t* cell_net, int level, const int64_t* n_dev, isx_bound_mode mode,
+                            int inflate, float* center, float* spread, __nv_bfloat16* scratch, int grid, int* status,
+                            cudaStream_t st);
 // 2-D bfloat16 tensor map [outer][inner] (row stride inner * 2 bytes), 128-byte swizzle.
 isx_status tensor_map_bf16(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
                            uint32_t box_outer);
@@ -177,6 +185,26 @@ isx_status proposer_merge(const uint32_t* idx, int64_t nb, const uint32_t* masks
                           const float* s_sub, const IsoSet& iso, isx_bound_mode mode, float k, int inflate,
                           uint32_t* keep, float* anc_c, float* anc_s, uint8_t* anc_gap, cudaStream_t st);
 isx_status gather_codes(const uint32_t* codes, const uint32_t* idx, int64_t nb, uint32_t* out, cudaStream_t st);
+
+// CUDA events bracketing the phases of one extraction (prediction, corner evaluation, marching cubes).
+struct Timer {
+  cudaEvent_t ev[4] = {};
+  isx_status init() {
+    for (auto& e : ev) ISX_CUDA(cudaEventCreate(&e));
+    return ISX_OK;
+  }
+  ~Timer() {
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
+// Active cells -> mesh: copy to the caller, corner evaluation, marching cubes (api.cu).
+isx_status mesh_from_active(isx_inr inr, const isx_extract_params* p, const uint32_t* codes, const uint32_t* masks,
+                            int64_t n, isx_mesh* mesh, Timer& tm, cudaStream_t st);
+// Batched level step helpers need the parameter checks of the single extraction (api.cu).
+isx_status validate_extract_params(const isx_extract_params* p, const isx_mesh* m);
+IsoSet iso_set_of(const isx_extract_params* p);
 
 // ---- mesh (mesh.cu) ----------------------------------------------------------------------------
 // flags[lattice id] = 1 for the 8 corners of every listed cell of the R^3 grid.

@@ -170,6 +170,50 @@ def extraction_forms(pkg, net, L, isos, plain, plain_ms, mode, k, prec):
     return out
 
 
+def batched_form(pkg, mode, k):
+    """The batched form: 8 INRs of mixed shape (hidden widths 128 / 256, 3-5 hidden layers), each fitted
+    for 300 Adam steps to its own field of the scientific kind (32-256 anisotropic Gaussians + sine),
+    16 iso-values over the 10-90 % quantiles, octrees to 64^3 or 128^3.  Reports the time of running
+    the 8 extractions one after another and as one batch replayed from its CUDA graph (after a
+    sizing run and a capture run)."""
+    import torch
+    from synth import fields, inr
+    specs = [(128, 3, 7, 32), (256, 4, 6, 64), (128, 5, 7, 128), (256, 3, 7, 256), (128, 4, 6, 48),
+             (256, 5, 6, 96), (128, 3, 7, 192), (256, 4, 7, 160)]
+    nets, params = [], []
+    for i, (w, H, L, nb) in enumerate(specs):
+        layers, _ = inr.fit([3] + [w] * H + [1], fields.anisotropic_blobs(4000 + i, nb), 300, init_seed=4000 + i,
+                            sample_seed=5000 + i)
+        isos = inr.quantile_isos(layers, 16, grid=64)
+        nets.append(pkg.Inr(layers))
+        params.append(dict(max_level=L, isos=isos, mode=mode, k=k, prec="bf16"))
+    st = torch.cuda.current_stream()
+
+    def ev_ms(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        out = fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        return out, a.elapsed_time(b)
+
+    bufs = [dict() for _ in nets]
+    for net, p, bf in zip(nets, params, bufs):
+        net.extract(buffers=bf, **p)                            # warm-up, sizes the buffers
+    singles, seq_ms = ev_ms(lambda: [net.extract(buffers=bf, **p) for net, p, bf in zip(nets, params, bufs)])
+    batch = pkg.Batch(nets, params, use_graph=True)
+    batch.run()                                                 # sized run
+    batch.run()                                                 # capture and first replay
+    res, batch_ms = ev_ms(batch.run)
+    same = all(r["n_active"] == s["n_active"] and r["n_tris"] == s["n_tris"] for r, s in zip(res, singles))
+    batch.close()
+    for net in nets:
+        net.close()
+    return {"entries": len(specs), "shapes": [f"w{w}xH{H}@{1 << L}^3" for w, H, L, _ in specs], "isos_each": 16,
+            "sequential_ms": seq_ms, "batched_graph_ms": batch_ms, "same_meshes": bool(same),
+            "cells_bounded_sequential": int(sum(sum(s["cells_bounded"]) for s in singles))}
+
+
 def cpu_baseline(layers, mode, k, budget_s=12.0):
     """Float64 oracle bounding random cells of levels 6-9 of the same workload for ~budget_s."""
     import numpy as np
@@ -349,6 +393,8 @@ def main():
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "kernel_time_share": shares}
     if rank == 0 and world == 1 and not args.no_forms:
         line["forms"] = extraction_forms(pkg, net, L, isos, res, ms_per_step, args.mode, args.k, prec)
+        if prec == "bf16":
+            line["forms"]["batched"] = batched_form(pkg, args.mode, args.k)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(layers, args.mode, args.k)
     if rank == 0:

@@ -254,6 +254,21 @@ void isx_profile_reset(void);
 /* Fills up to `max` entries and returns how many kernels the library knows. */
 int isx_profile_read(isx_kernel_stats* out, int max);
 
+/* ---- launch-shape autotuner ------------------------------------------------------------------
+ * Kernels with interchangeable tile shapes (the FP32 coefficient GEMM of the FP32 bound: 64x64,
+ * 32x64, 16x64, 128x64 and 64x128 output tiles, identical results) time every shape once per key
+ * (kernel, hidden width, row-count bucket) on the real operands and keep the fastest for the process;
+ * ISX_TUNE=0 in the environment disables tuning (first shape always).  isx_tune_read fills up to
+ * `max` entries and returns how many keys are cached; strings stay valid until isx_tune_reset. */
+typedef struct {
+  const char* key;               /* e.g. "gemm_fp32 w=64 rows<=128"                              */
+  const char* choice;            /* chosen tile shape                                             */
+  int variant, n_variants;
+  float ms_best, ms_first;       /* timed launch of the chosen and of the first shape            */
+} isx_tune_entry;
+int isx_tune_read(isx_tune_entry* out, int max);
+void isx_tune_reset(void);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* isx_last_error(void);
 

@@ -4,4 +4,4 @@ The computation lives in the CUDA library ``libisx.so`` (C interface: include/is
 only builds it and marshals arguments to it (``_lib``).
 """
 from ._lib import (BF16, CLT, FP32, RAUA, SOUND, Batch, Inr, IsxError, Proposer, load, mc_table,  # noqa: F401
-                   profile_enable, profile_read, profile_reset)
+                   profile_enable, profile_read, profile_reset, tune_read, tune_reset)

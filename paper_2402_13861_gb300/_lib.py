@@ -43,6 +43,11 @@ class InrDesc(C.Structure):
                 ("W", C.POINTER(C.POINTER(C.c_float))), ("b", C.POINTER(C.POINTER(C.c_float)))]
 
 
+class TuneEntry(C.Structure):
+    _fields_ = [("key", C.c_char_p), ("choice", C.c_char_p), ("variant", C.c_int), ("n_variants", C.c_int),
+                ("ms_best", C.c_float), ("ms_first", C.c_float)]
+
+
 class ExtractParams(C.Structure):
     _fields_ = [("max_level", C.c_int), ("n_iso", C.c_int), ("iso", C.c_float * ISX_MAX_ISO),
                 ("mode", C.c_int), ("k", C.c_float), ("prec", C.c_int), ("inflate", C.c_int),
@@ -93,6 +98,10 @@ def load(path: Path | None = None):
     lib.isx_profile_reset.restype = None
     lib.isx_profile_read.argtypes = [C.POINTER(KernelStats), C.c_int]
     lib.isx_profile_read.restype = C.c_int
+    lib.isx_tune_read.argtypes = [C.POINTER(TuneEntry), C.c_int]
+    lib.isx_tune_read.restype = C.c_int
+    lib.isx_tune_reset.argtypes = []
+    lib.isx_tune_reset.restype = None
     lib.isx_batch_create.argtypes = [C.POINTER(vp), C.POINTER(ExtractParams), C.c_int, C.c_int, C.POINTER(vp)]
     lib.isx_batch_run.argtypes = [vp, C.POINTER(Mesh), vp]
     lib.isx_batch_destroy.argtypes = [vp]
@@ -139,6 +148,19 @@ def profile_read():
     n = load().isx_profile_read(arr, 64)
     return {arr[i].name.decode(): dict(launches=arr[i].launches, ms=arr[i].ms, flops=arr[i].flops,
                                        bytes=arr[i].bytes) for i in range(n)}
+
+
+def tune_read():
+    """{key: dict(choice, variant, n_variants, ms_best, ms_first)} of the autotuner's cached choices."""
+    arr = (TuneEntry * 256)()
+    n = min(load().isx_tune_read(arr, 256), 256)
+    return {arr[i].key.decode(): dict(choice=arr[i].choice.decode(), variant=arr[i].variant,
+                                      n_variants=arr[i].n_variants, ms_best=arr[i].ms_best, ms_first=arr[i].ms_first)
+            for i in range(n)}
+
+
+def tune_reset():
+    load().isx_tune_reset()
 
 
 def _stream_ptr(stream):

@@ -18,6 +18,8 @@
 // standard error analysis: a K-term dot product errs by at most gamma_K sum |a_k b_k| with
 // gamma_K = K u / (1 - K u), u = 2^-24; products alpha_k W_nk rounded once more add u.
 #include "internal.cuh"
+
+#include <string>
 #include "linearise.cuh"
 
 #include <algorithm>
@@ -135,52 +137,86 @@ __global__ void k_center_gemv(int nc, int win, int wout, const float* __restrict
   }
 }
 
-// X_out[r] = X_in[r] diag(alpha) W^T for the S_in carried rows (64 x 64 tiles, K step 16).
-__global__ void __launch_bounds__(256) k_gemm_fp32(const float* __restrict__ Xin, float* __restrict__ Xout,
-                                                   int S_in, int S_out, int w, const float* __restrict__ Wt,
-                                                   const float* __restrict__ ALPHA) {
-  __shared__ float As[16][68];
-  __shared__ float Bs[16][64];
-  int cell = blockIdx.z;
-  int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+// X_out[r] = X_in[r] diag(alpha) W^T for the S_in carried rows: BM x BN output tiles, K step 16,
+// TM x TN outputs per thread.  Every output accumulates over K in the same order whatever the tile,
+// so all variants give bit-identical results and the autotuner may pick any of them.
+template <int BM, int BN, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm_fp32(const float* __restrict__ Xin,
+                                                                     float* __restrict__ Xout, int S_in, int S_out,
+                                                                     int w, const float* __restrict__ Wt,
+                                                                     const float* __restrict__ ALPHA) {
+  constexpr int T = (BM / TM) * (BN / TN), TX = BN / TN;
+  static_assert(TN % 4 == 0, "float4 stores");
+  __shared__ float As[16][BM + 4];
+  __shared__ float Bs[16][BN];
+  const int cell = blockIdx.z;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const float* A = Xin + (size_t)cell * S_in * w;
   const float* al = ALPHA + (size_t)cell * w;
   float* Y = Xout + (size_t)cell * S_out * w;
-  int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  float acc[4][4] = {};
+  const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+  float acc[TM][TN] = {};
   for (int k0 = 0; k0 < w; k0 += 16) {
-    {
-      int row = tid >> 2, kq = (tid & 3) * 4;
+    for (int q = tid; q < BM * 4; q += T) {
+      const int row = q >> 2, kq = (q & 3) * 4;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (m0 + row < S_in) v = *reinterpret_cast<const float4*>(A + (size_t)(m0 + row) * w + k0 + kq);
       As[kq + 0][row] = v.x; As[kq + 1][row] = v.y; As[kq + 2][row] = v.z; As[kq + 3][row] = v.w;
-      int kk = tid >> 4, nq = (tid & 15) * 4;
+    }
+    for (int q = tid; q < 4 * BN; q += T) {
+      const int kk = q / (BN / 4), nq = (q % (BN / 4)) * 4;
       float4 bv = make_float4(0.f, 0.f, 0.f, 0.f);
       if (n0 + nq < w) bv = *reinterpret_cast<const float4*>(Wt + (size_t)(k0 + kk) * w + n0 + nq);
-      float s = al[k0 + kk];
-      Bs[kk][nq + 0] = bv.x * s; Bs[kk][nq + 1] = bv.y * s; Bs[kk][nq + 2] = bv.z * s; Bs[kk][nq + 3] = bv.w * s;
+      const float sc = al[k0 + kk];
+      Bs[kk][nq + 0] = bv.x * sc; Bs[kk][nq + 1] = bv.y * sc; Bs[kk][nq + 2] = bv.z * sc; Bs[kk][nq + 3] = bv.w * sc;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      float a4[4], b4[4];
+      float a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a4[i] = As[kk][ty * 4 + i];
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b4[j] = Bs[kk][tx * 4 + j];
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a4[i], b4[j], acc[i][j]);
+        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    int r = m0 + ty * 4 + i;
-    if (r < S_in && n0 + tx * 4 < w)
-      *reinterpret_cast<float4*>(Y + (size_t)r * w + n0 + tx * 4) =
-          make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+  for (int i = 0; i < TM; ++i) {
+    const int r = m0 + ty * TM + i;
+#pragma unroll
+    for (int jc = 0; jc < TN; jc += 4) {
+      const int c = n0 + tx * TN + jc;
+      if (r < S_in && c < w)
+        *reinterpret_cast<float4*>(Y + (size_t)r * w + c) =
+            make_float4(acc[i][jc], acc[i][jc + 1], acc[i][jc + 2], acc[i][jc + 3]);
+    }
+  }
+}
+
+// Tile variants of the FP32 coefficient GEMM the autotuner chooses from.
+struct GemmShape {
+  int bm, bn;
+  const char* name;
+};
+constexpr GemmShape kGemmShapes[] = {{64, 64, "64x64/4x4"}, {32, 64, "32x64/2x4"}, {16, 64, "16x64/1x4"},
+                                     {128, 64, "128x64/8x4"}, {64, 128, "64x128/4x8"}};
+constexpr int kGemmVariants = sizeof(kGemmShapes) / sizeof(kGemmShapes[0]);
+
+void launch_gemm(int v, int nc, int S, int S_out, int w, const float* Xa, float* Xb, const float* Wt,
+                 const float* AL, cudaStream_t st) {
+  const GemmShape g = kGemmShapes[v];
+  const dim3 grid((w + g.bn - 1) / g.bn, (S + g.bm - 1) / g.bm, nc);
+  switch (v) {
+    case 0: k_gemm_fp32<64, 64, 4, 4><<<grid, 256, 0, st>>>(Xa, Xb, S, S_out, w, Wt, AL); break;
+    case 1: k_gemm_fp32<32, 64, 2, 4><<<grid, 256, 0, st>>>(Xa, Xb, S, S_out, w, Wt, AL); break;
+    case 2: k_gemm_fp32<16, 64, 1, 4><<<grid, 256, 0, st>>>(Xa, Xb, S, S_out, w, Wt, AL); break;
+    case 3: k_gemm_fp32<128, 64, 8, 4><<<grid, 256, 0, st>>>(Xa, Xb, S, S_out, w, Wt, AL); break;
+    default: k_gemm_fp32<64, 128, 4, 8><<<grid, 256, 0, st>>>(Xa, Xb, S, S_out, w, Wt, AL); break;
   }
 }
 
@@ -334,13 +370,23 @@ isx_status bound_fp32(isx_inr inr, const CellSource& src, int64_t n, isx_bound_m
       }
       ISX_LAUNCH_CHECK("k_center_gemv");
       int S_out = S + w;
-      dim3 g((w + 63) / 64, (S + 63) / 64, nc);
-      // the coefficient buffers are laid out with the final stride S_out per cell
+      // the coefficient buffers are laid out with the final stride S_out per cell; the tile shape
+      // comes from the autotuner (timed once per width and row-count bucket)
       {
+        int bucket = 1;
+        while (bucket < S) bucket <<= 1;
+        const std::string key = "gemm_fp32 w=" + std::to_string(w) + " rows<=" + std::to_string(bucket);
+        const float* Wt = inr->Wt[j];
+        auto run = [&](int v) -> isx_status {
+          launch_gemm(v, nc, S, S_out, w, Xa, Xb, Wt, AL, st);
+          ISX_LAUNCH_CHECK("k_gemm_fp32");
+          return ISX_OK;
+        };
+        int v = 0;
+        ISX_TRY(tune::pick(key, kGemmVariants, [&](int i) { return kGemmShapes[i].name; }, run, st, &v));
         prof::Scope _ps(K_GEMM_FP32, st, 2.0 * nc * (double)S * w * w, 8.0 * nc * (double)S * w);
-        k_gemm_fp32<<<g, 256, 0, st>>>(Xa, Xb, S, S_out, w, inr->Wt[j], AL);
+        ISX_TRY(run(v));
       }
-      ISX_LAUNCH_CHECK("k_gemm_fp32");
       {
         prof::Scope _ps(K_FRESH, st, 0, 4.0 * nc * w * w);
         k_fresh_rows<<<dim3(w, nc), bt, 0, st>>>(Xb, S, S_out, w, inr->Wt[j], GA);

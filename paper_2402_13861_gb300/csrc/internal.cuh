@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -205,6 +206,14 @@ isx_status mesh_from_active(isx_inr inr, const isx_extract_params* p, const uint
 // Batched level step helpers need the parameter checks of the single extraction (api.cu).
 isx_status validate_extract_params(const isx_extract_params* p, const isx_mesh* m);
 IsoSet iso_set_of(const isx_extract_params* p);
+
+// ---- launch-shape autotuner (tune.cu) -------------------------------------------------------------
+namespace tune {
+// Variant to launch for `key` among n interchangeable ones (identical results): timed on first use
+// with run(v) on stream st, cached for the process.
+isx_status pick(const std::string& key, int n, const std::function<const char*(int)>& name,
+                const std::function<isx_status(int)>& run, cudaStream_t st, int* out);
+}  // namespace tune
 
 // ---- mesh (mesh.cu) ----------------------------------------------------------------------------
 // flags[lattice id] = 1 for the 8 corners of every listed cell of the R^3 grid.

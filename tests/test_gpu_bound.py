@@ -120,3 +120,25 @@ def test_eval_points_matches_oracle(small, pkg):
     ref = mlp.mlp_forward(wide, x)
     assert np.all(np.abs(v - ref) <= 1e-5 * (1 + np.abs(ref)) * 10)
     net2.close()
+
+
+def test_fp32_gemm_autotuner_picks_a_shape_and_keeps_results(pkg):
+    """The autotuner times the FP32 GEMM tile shapes on first use of a (width, rows) key and caches
+    one; bounds computed with the cached shape equal the first (tuning) call bit for bit and the
+    float64 oracle within the FP32 band."""
+    pkg.tune_reset()
+    layers = inr.random_inr([3, 64, 64, 64, 1], 12)
+    net = pkg.Inr(layers)
+    lo, hi = boxes.random_boxes(300, 13, -8, -2)
+    dlo, dhi = torch.tensor(lo, device="cuda"), torch.tensor(hi, device="cuda")
+    c1, s1 = [x.clone() for x in net.bound_cells(dlo, dhi, mode="clt", prec="fp32")]
+    table = pkg.tune_read()
+    keys = [k for k in table if k.startswith("gemm_fp32 w=64")]
+    print({k: (table[k]["choice"], round(table[k]["ms_best"], 4), round(table[k]["ms_first"], 4)) for k in keys})
+    assert keys and all(0 <= table[k]["variant"] < table[k]["n_variants"] == 5 for k in keys)
+    c2, s2 = net.bound_cells(dlo, dhi, mode="clt", prec="fp32")
+    assert torch.equal(c1, c2) and torch.equal(s1, s2)
+    oc, os_ = affine.bound(layers, lo[:50], hi[:50], "clt", batch=25)
+    s = s2.cpu().numpy()[:50].astype(np.float64)
+    assert np.all(np.abs(s - os_) <= 1e-4 * os_ + 1e-7)
+    net.close()

@@ -420,7 +420,7 @@ isx_status isx_batch_create(const isx_inr* inrs, const isx_extract_params* param
     b->Lmax = std::max(b->Lmax, params[i].max_level);
     const int w = inrs[i]->w, g = (w == 256) ? 1 : 0;
     b->widths[g] = w;
-    b->rows[g] = std::max(b->rows[g], std::max(1, w * std::max(0, inrs[i]->H - 3)));
+    b->rows[g] = std::max(b->rows[g], std::max(128, w * std::max(0, inrs[i]->H - 3)));
   }
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

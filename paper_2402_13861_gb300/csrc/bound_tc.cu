@@ -62,6 +62,7 @@ constexpr int kMathBase = 32 * (2 + kEpiWarps);                    // first math
 constexpr uint32_t kStageBytes = 128 * 128;                        // 128 rows x 64 bf16
 constexpr uint32_t kRingBytes = 8192;                              // one stage of float32 weight rows
 constexpr int kRingStages = 2;
+constexpr int kBigStages = 4;                                      // the B buffer as a ring while B is idle
 constexpr uint64_t kWaitNs = 2000000000ull;                        // 2 s per wait
 constexpr float kUb = 0.00390625f;                                 // 2^-8
 constexpr float kUa = 7.62939453125e-06f;                          // 2^-17
@@ -69,7 +70,7 @@ constexpr float kGemvSafe = 1.015625f;                             // 1 + 2^-6: 
 
 // One network of a launch: its weights and the tensor maps of its BF16 copies (device memory,
 // 64-byte aligned; written by the host before the launch).
-struct alignas(64) TcNet {
+struct TcNet {
   CUtensorMap wt[ISX_MAX_LAYERS];      // W_l^T bf16, box {64, 128}: A of implicit blocks
   CUtensorMap wrow[ISX_MAX_LAYERS];    // W_l bf16, box {64, w}: source of B = D W^T
   CUtensorMap wabs[ISX_MAX_LAYERS];    // |W_l| bf16, box {64, 128}: A of the sound reduction pass
@@ -134,7 +135,8 @@ struct Smem {
 enum Bars {
   BAR_FULL = 0, BAR_EMPTY = kStages, BAR_TFULL = 2 * kStages, BAR_TEMPTY = 2 * kStages + 2,
   BAR_BREADY = 2 * kStages + 4, BAR_BFREE, BAR_WLOADED, BAR_RED, BAR_BOUTREADY,
-  BAR_MFULL, BAR_MEMPTY = BAR_MFULL + kRingStages, BAR_COUNT = BAR_MEMPTY + kRingStages
+  BAR_MFULL, BAR_MEMPTY = BAR_MFULL + kRingStages, BAR_BMFULL = BAR_MEMPTY + kRingStages,
+  BAR_BMEMPTY = BAR_BMFULL + kBigStages, BAR_RINGBFREE = BAR_BMEMPTY + kBigStages, BAR_COUNT
 };
 
 __host__ __device__ inline size_t smem_bytes(int w) {
@@ -215,14 +217,27 @@ __device__ __forceinline__ uint32_t swz(int rows, int row, int k) {
 // acc[v][e] += sum_k row_k[col_e] * x_v[k] for col_e = mt + e * 128 and NX vectors x_v, where
 // x_0 = x and, with NX == 4, x_{1..3}[k] = I[r][k] * al[k] (the input-symbol rows times alpha);
 // with `with_abs`, aacc[e] += sum_k |row_k[col_e]| |x[k]|.
-template <int W, int NX, int NPT>
+// Two rings carry the rows: the small one (kRingStages x 8 KB) and, while B is idle (the first
+// layer's GEMV and the output GEMVs), the B buffer itself (kBigStages stages of W W / 2 bytes).
+struct Ring {
+  const float* base;
+  int stage_floats, nstages, full, empty;
+};
+template <int W, bool BIG>
+__device__ __forceinline__ Ring ring_of(const Smem& s) {
+  if constexpr (BIG) return Ring{reinterpret_cast<const float*>(s.B), W * W / 8, kBigStages, BAR_BMFULL, BAR_BMEMPTY};
+  else return Ring{s.ring, (int)(kRingBytes / 4), kRingStages, BAR_MFULL, BAR_MEMPTY};
+}
+
+template <int W, int NX, int NPT, bool BIG>
 __device__ __forceinline__ bool ring_gemv(const Smem& s, int* status, uint32_t& ms, uint32_t& mph, int mt, int lane,
                                           const float* x, const float* al, float (&acc)[NX][NPT], float (&aacc)[NPT],
                                           bool with_abs) {
-  constexpr int R = kRingBytes / (4 * W);
+  const Ring rg = ring_of<W, BIG>(s);
+  constexpr int R = BIG ? W / 8 : (int)(kRingBytes / (4 * W));   // rows per stage
   for (int r0 = 0; r0 < W; r0 += R) {
-    if (!wait_bar(s, &s.bar[BAR_MFULL + ms], mph, status)) return false;
-    const float* rows = s.ring + (size_t)ms * (kRingBytes / 4);
+    if (!wait_bar(s, &s.bar[rg.full + ms], mph, status)) return false;
+    const float* rows = rg.base + (size_t)ms * rg.stage_floats;
 #pragma unroll
     for (int rr = 0; rr < R; ++rr) {
       const int k = r0 + rr;
@@ -248,8 +263,8 @@ __device__ __forceinline__ bool ring_gemv(const Smem& s, int* status, uint32_t& 
     // writing stored G rows) were observed to return the next stage's rows.
     fence_async_shared();
     __syncwarp();
-    if (lane == 0) mbar_arrive(&s.bar[BAR_MEMPTY + ms]);
-    if (++ms == kRingStages) { ms = 0; mph ^= 1; }
+    if (lane == 0) mbar_arrive(&s.bar[rg.empty + ms]);
+    if (++ms == (uint32_t)rg.nstages) { ms = 0; mph ^= 1; }
   }
   return true;
 }
@@ -299,7 +314,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
   extern __shared__ uint8_t smem_raw[];
   constexpr int MT = W / 128;              // 128-row tiles per block of w rows
   constexpr int KC = W / 64;               // 64-wide K chunks
-  constexpr int R = kRingBytes / (4 * W);  // weight rows per ring stage
   const int64_t ncell = args.n_dev ? *args.n_dev : args.n;
   Smem s = carve(smem_raw, W);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -320,6 +334,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
       mbar_init(&s.bar[BAR_MFULL + i], 1);
       mbar_init(&s.bar[BAR_MEMPTY + i], kMathWarps);
     }
+    for (int i = 0; i < kBigStages; ++i) {
+      mbar_init(&s.bar[BAR_BMFULL + i], 1);
+      mbar_init(&s.bar[BAR_BMEMPTY + i], kMathWarps);
+    }
+    mbar_init(&s.bar[BAR_RINGBFREE], 1);
     mbar_init(&s.bar[BAR_BREADY], 1);
     mbar_init(&s.bar[BAR_BFREE], 1);
     mbar_init(&s.bar[BAR_WLOADED], 1);
@@ -341,17 +360,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
   tc_fence_after();
   const uint32_t tmem = *s.tmem_slot;
   __nv_bfloat16* scratch = args.scratch + (size_t)blockIdx.x * args.rows_per_cta * W;
-  const int scratch_row0 = blockIdx.x * args.rows_per_cta;
 
   if (warp == 0) {
     // ============================ TMA producer: B source and A tiles ============================
     if (lane == 0) {
-      uint32_t stage = 0, sphase = 0, bfree_n = 0, red_n = 0;
+      uint32_t stage = 0, sphase = 0, bfree_n = 0, red_n = 0, rb_n = 0;
       bool ok = true;
       auto load_a = [&](const CUtensorMap* m, int x, int y) -> bool {
         if (!wait_bar(s, &s.bar[BAR_EMPTY + stage], sphase ^ 1, args.status)) return false;
         mbar_expect_tx(&s.bar[BAR_FULL + stage], kStageBytes);
         tma_load_2d(s.A + (size_t)stage * kStageBytes, m, &s.bar[BAR_FULL + stage], x, y);
+        if (++stage == kStages) { stage = 0; sphase ^= 1; }
+        return true;
+      };
+      // a 128-row tile of this CTA's stored rows (unit-major scratch), K chunk c: lands in the
+      // stage as 8 x [128 rows x 16 bytes] core-matrix columns (no swizzle)
+      auto load_s = [&](int row, int c) -> bool {
+        if (!wait_bar(s, &s.bar[BAR_EMPTY + stage], sphase ^ 1, args.status)) return false;
+        mbar_expect_tx(&s.bar[BAR_FULL + stage], kStageBytes);
+        tma_load_3d(s.A + (size_t)stage * kStageBytes, &maps.scratch, &s.bar[BAR_FULL + stage], 0, row,
+                    (int)blockIdx.x * (W / 8) + c * 8);
         if (++stage == kStages) { stage = 0; sphase ^= 1; }
         return true;
       };
@@ -361,9 +389,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
         if (N.w != W) continue;
         for (int j = 1; j <= H - 1 && ok; ++j) {
           if (j >= 2) {
-            // B source: W_j once the previous layer's MMAs no longer read B
+            // B source: W_j once the previous layer's MMAs no longer read B, and (for W_2) once the
+            // math warps' first-layer GEMV no longer reads B as its ring
             if (!wait_bar(s, &s.bar[BAR_BFREE], (bfree_n & 1) ^ 1, args.status)) { ok = false; break; }
             ++bfree_n;
+            if (j == 2 && !wait_bar(s, &s.bar[BAR_RINGBFREE], rb_n & 1, args.status)) { ok = false; break; }
             mbar_expect_tx(&s.bar[BAR_WLOADED], (uint32_t)(W * W * 2));
             for (int c = 0; c < KC; ++c) tma_load_2d(s.B + (size_t)c * W * 128, &N.wrow[j], &s.bar[BAR_WLOADED], c * 64, 0);
             // the previous layer is complete (its stored rows are read below); the proxy fence
@@ -386,20 +416,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
               const bool implicit = (blk == j - 1);
               for (int c = 0; c < KC; ++c) {
                 bool good = implicit ? load_a(&N.wt[j - 1], c * 64, sub * 128)
-                                     : load_a(&maps.scratch, c * 64, scratch_row0 + (blk - 1) * W + sub * 128);
+                                     : load_s((blk - 1) * W + sub * 128, c);
                 if (!good) { ok = false; break; }
               }
             }
           }
         }
         if (!ok) break;
+        ++rb_n;                           // the math warps release B once per cell (after GEMV 1)
         if (!wait_bar(s, &s.bar[BAR_RED], red_n & 1, args.status)) break;   // layer H-1
         ++red_n;
         fence_async_global();
         const int TO = out_tiles(H, W);
         for (int t = 0; t < TO && ok; ++t)
           for (int c = 0; c < KC; ++c)
-            if (!load_a(&maps.scratch, c * 64, scratch_row0 + t * 128)) { ok = false; break; }
+            if (!load_s(t * 128, c)) { ok = false; break; }
         if (ok && TO > 0) {
           if (!wait_bar(s, &s.bar[BAR_RED], red_n & 1, args.status)) break;
           ++red_n;
@@ -409,14 +440,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
   } else if (warp == kRingWarp) {
     // ============================ bulk producer: float32 weight rows for the math warps ============================
     if (lane == 0) {
-      uint32_t ms = 0, mph = 0;
+      uint32_t ms = 0, mph = 0, bms = 0, bmph = 0;
+      uint64_t bfree_total = 0;           // B releases (one per layer >= 2) of the cells so far
       bool ok = true;
-      auto push = [&](const float* src) -> bool {
-        for (int r0 = 0; r0 < W; r0 += R) {
-          if (!wait_bar(s, &s.bar[BAR_MEMPTY + ms], mph ^ 1, args.status)) return false;
-          mbar_expect_tx(&s.bar[BAR_MFULL + ms], kRingBytes);
-          bulk_load(s.ring + (size_t)ms * (kRingBytes / 4), src + (size_t)r0 * W, kRingBytes, &s.bar[BAR_MFULL + ms]);
-          if (++ms == kRingStages) { ms = 0; mph ^= 1; }
+      auto push = [&](const float* src, bool big) -> bool {
+        const int stage_bytes = big ? W * W / 2 : (int)kRingBytes, rows = stage_bytes / (4 * W);
+        const int nst = big ? kBigStages : kRingStages, full = big ? BAR_BMFULL : BAR_MFULL,
+                  empty = big ? BAR_BMEMPTY : BAR_MEMPTY;
+        float* base = big ? reinterpret_cast<float*>(s.B) : s.ring;
+        uint32_t& st = big ? bms : ms;
+        uint32_t& ph = big ? bmph : mph;
+        for (int r0 = 0; r0 < W; r0 += rows) {
+          if (!wait_bar(s, &s.bar[empty + st], ph ^ 1, args.status)) return false;
+          mbar_expect_tx(&s.bar[full + st], (uint32_t)stage_bytes);
+          bulk_load(base + (size_t)st * (stage_bytes / 4), src + (size_t)r0 * W, (uint32_t)stage_bytes, &s.bar[full + st]);
+          if (++st == (uint32_t)nst) { st = 0; ph ^= 1; }
         }
         return true;
       };
@@ -424,9 +462,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
         const TcNet& N = args.nets[args.cell_net ? args.cell_net[cell] : 0];
         const int H = N.H;
         if (N.w != W) continue;
-        for (int j = 1; j <= H - 1 && ok; ++j) ok = push(N.Wt[j]);      // centre of z_{j+1}
-        if (ok) ok = push(N.W[H - 1]);                                   // v
-        if (ok && H >= 3) ok = push(N.W[H - 2]);                         // implicit G_{H-2}
+        // layer 1: B is idle (the previous cell's MMAs released it, this cell's W_2 waits for this GEMV)
+        ok = push(N.Wt[1], true);                                        // centre of z_2
+        for (int j = 2; j <= H - 1 && ok; ++j) ok = push(N.Wt[j], false); // centre of z_{j+1}
+        if (!ok) break;
+        if (H >= 3) {
+          // the output GEMVs reuse B once the last layer's MMAs have released it
+          bfree_total += (uint64_t)(H - 2);
+          if (!wait_bar(s, &s.bar[BAR_BFREE], (uint32_t)((bfree_total - 1) & 1), args.status)) break;
+        }
+        ok = push(N.W[H - 1], true);                                     // v
+        if (ok && H >= 3) ok = push(N.W[H - 2], true);                   // implicit G_{H-2}
       }
     }
   } else if (warp == 1) {
@@ -436,7 +482,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
       const uint32_t id_main = idesc(W), id_small = idesc(16);
       bool ok = true;
       // one 128-row tile: K chunks from the A ring against B (bsmem, rows of the B operand)
-      auto tile = [&](uint8_t* bsm, int brows, uint32_t id) -> bool {
+      auto tile = [&](uint8_t* bsm, int brows, uint32_t id, bool a_noswz) -> bool {
         const uint32_t acc = tiles_done & 1;
         if (!wait_bar(s, &s.bar[BAR_TEMPTY + acc], ((tiles_done >> 1) & 1) ^ 1, args.status)) return false;
         tc_fence_after();
@@ -447,8 +493,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
           const uint32_t a0 = su32(s.A + (size_t)stage * kStageBytes);
           const uint32_t b0 = su32(bsm + (size_t)c * brows * 128);
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk)
-            mma_bf16(d, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), id, (c > 0 || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < 4; ++kk) {
+            // A: 128-byte swizzled rows (weight tiles) or unit-major core matrices (stored rows:
+            // 16 K-elements = 2 core-matrix columns of 128 x 16 bytes)
+            const uint64_t ad = a_noswz ? sdesc_noswz(a0 + kk * 2 * 2048, 2048, 128) : sdesc(a0 + kk * 32);
+            mma_bf16(d, ad, sdesc(b0 + kk * 32), id, (c > 0 || kk > 0) ? 1u : 0u);
+          }
           mma_commit(&s.bar[BAR_EMPTY + stage]);
           if (++stage == kStages) { stage = 0; sphase ^= 1; }
         }
@@ -465,10 +515,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
           ++bready_n;
           trace(args, 1, cell / gridDim.x, 2 * j);
           tc_fence_after();
-          for (int t = 0; t < MT && ok; ++t) ok = tile(s.Bs, 16, id_small);
+          for (int t = 0; t < MT && ok; ++t) ok = tile(s.Bs, 16, id_small, false);
           if (j >= 2) {
             const int T = (j - 1) * MT;
-            for (int t = 0; t < T && ok; ++t) ok = tile(s.B, W, id_main);
+            for (int t = 0; t < T && ok; ++t) ok = tile(s.B, W, id_main, t / MT + 1 != j - 1);
             if (ok) mma_commit(&s.bar[BAR_BFREE]);
           }
           trace(args, 1, cell / gridDim.x, 2 * j + 1);
@@ -479,7 +529,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
           if (!wait_bar(s, &s.bar[BAR_BOUTREADY], bout_n & 1, args.status)) break;
           ++bout_n;
           tc_fence_after();
-          for (int t = 0; t < TO && ok; ++t) ok = tile(s.Bs, 16, id_small);
+          for (int t = 0; t < TO && ok; ++t) ok = tile(s.Bs, 16, id_small, true);
         }
       }
     }
@@ -540,7 +590,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
             const int blk = t / MT + 1, sub = t % MT;
             const bool implicit = (blk == j - 1);
             const float rs = implicit ? gprev[sub * 128 + row] : 1.0f;
-            __nv_bfloat16* dst = scratch + (size_t)((blk - 1) * W + sub * 128 + row) * W;
+            // unit-major slice: 16-byte unit u (columns 8u .. 8u+7) of slice row r at [u * rows + r], so the
+            // 32 lanes (consecutive rows) of every store below write 512 contiguous bytes
+            const int rowg = (blk - 1) * W + sub * 128 + row;
+            uint4* slice4 = reinterpret_cast<uint4*>(scratch);
 #pragma unroll
             for (int ch = 0; ch < NCH; ++ch) {
               const int col0 = hf * HALF + ch * 32;
@@ -556,9 +609,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
                   v[2 * i] = f2.x;
                   v[2 * i + 1] = f2.y;
                 }
-                uint4* d4 = reinterpret_cast<uint4*>(dst + col0);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) d4[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+                for (int i = 0; i < 4; ++i)
+                  slice4[(size_t)(col0 / 8 + i) * args.rows_per_cta + rowg] =
+                      make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
               } else {
 #pragma unroll
                 for (int i = 0; i < 32; ++i) v[i] *= rs;
@@ -617,7 +671,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
     const int mt = threadIdx.x - kMathBase;    // 0..127
     const int mwarp = mt >> 5;
     constexpr int NPT = W / kMathThreads;      // neurons per thread (1 or 2)
-    uint32_t wl_n = 0, red_n = 0, ms = 0, mph = 0;
+    uint32_t wl_n = 0, red_n = 0, ms = 0, mph = 0, bms = 0, bmph = 0;
     const float kap = args.kappa;
     const bool sq = clt || mode == ISX_BOUND_RAUA;
     auto group_wait = [&](uint64_t* b, uint32_t parity) -> bool {
@@ -722,9 +776,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
             acc[0][e] = acc[1][e] = acc[2][e] = acc[3][e] = 0.f;
             dummy[e] = 0.f;
           }
-          if (!ring_gemv<W, 4, NPT>(s, args.status, ms, mph, mt, lane, s.a, al, acc, dummy, false)) ok = false;
+          const bool gok = (j == 1)
+                               ? ring_gemv<W, 4, NPT, true>(s, args.status, bms, bmph, mt, lane, s.a, al, acc, dummy, false)
+                               : ring_gemv<W, 4, NPT, false>(s, args.status, ms, mph, mt, lane, s.a, al, acc, dummy, false);
+          if (!gok) ok = false;
           math_sync();     // every thread has read a, c and I
           if (!ok) break;
+          // B is free again for W_2 (the TMA producer waits for this before loading it)
+          if (j == 1 && mt == 0) mbar_arrive(&s.bar[BAR_RINGBFREE]);
 #pragma unroll
           for (int e = 0; e < NPT; ++e) {
             const int nn = mt + e * kMathThreads;
@@ -782,7 +841,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
         float acc[1][NPT], aacc[NPT];
 #pragma unroll
         for (int e = 0; e < NPT; ++e) acc[0][e] = aacc[e] = 0.f;
-        if (!ring_gemv<W, 1, NPT>(s, args.status, ms, mph, mt, lane, s.Inew, al, acc, aacc, true)) ok = false;
+        if (!ring_gemv<W, 1, NPT, true>(s, args.status, bms, bmph, mt, lane, s.Inew, al, acc, aacc, true)) ok = false;
         math_sync();
         if (!ok) break;
 #pragma unroll
@@ -814,7 +873,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
         float dummy[NPT], g1[1][NPT];
 #pragma unroll
         for (int e = 0; e < NPT; ++e) g1[0][e] = dummy[e] = 0.f;
-        if (!ring_gemv<W, 1, NPT>(s, args.status, ms, mph, mt, lane, u, al, g1, dummy, false)) ok = false;
+        if (!ring_gemv<W, 1, NPT, true>(s, args.status, bms, bmph, mt, lane, u, al, g1, dummy, false)) ok = false;
         if (!ok) { math_sync(); break; }
 #pragma unroll
         for (int e = 0; e < NPT; ++e) gsum[e] = g1[0][e];
@@ -916,6 +975,10 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
+// The stored-row scratch of `grid` CTAs, unit-major per CTA (16-byte unit u of slice row r at
+// [u * rows + r]): a 3-D map {8 elements, rows, units x CTAs} with box {8, 128, 8}, no swizzle.
+isx_status make_scratch_map(CUtensorMap* m, const void* base, int w, int rows, int grid);
+
 isx_status make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
                     uint32_t box_outer) {
   EncodeTiledFn fn = encode_fn();
@@ -932,6 +995,26 @@ isx_status make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t o
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+    return ISX_ERR_CUDA;
+  }
+  return ISX_OK;
+}
+
+isx_status make_scratch_map(CUtensorMap* m, const void* base, int w, int rows, int grid) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is not available");
+    return ISX_ERR_CUDA;
+  }
+  cuuint64_t dims[3] = {8, (cuuint64_t)rows, (cuuint64_t)(w / 8) * (cuuint64_t)grid};
+  cuuint64_t strides[2] = {16, (cuuint64_t)rows * 16};
+  cuuint32_t box[3] = {8, 128, 8};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled (scratch) failed with code " + std::to_string((int)r));
     return ISX_ERR_CUDA;
   }
   return ISX_OK;
@@ -1031,7 +1114,7 @@ isx_status bound_bf16_batch(const void* d_nets, int w, int rows_per_cta, const u
   set_kappas(a, w);
   TcMaps maps;
   std::memset(&maps, 0, sizeof(maps));
-  ISX_TRY(make_map(&maps.scratch, scratch, w, (uint64_t)grid * rows_per_cta, 64, 128));
+  ISX_TRY(make_scratch_map(&maps.scratch, scratch, w, rows_per_cta, grid));
   return launch_tc(w, a, maps, grid, st);
 }
 
@@ -1058,7 +1141,7 @@ isx_status bound_bf16(isx_inr inr, const CellSource& src, int64_t n, isx_bound_m
   int dev = inr->device, sms = 0;
   ISX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int grid = (int)std::min<int64_t>(n, sms);
-  const int rows = std::max(1, w * std::max(0, H - 3));
+  const int rows = std::max(128, w * std::max(0, H - 3));   // >= one 128-row TMA box
   auto& ws = inr->ws;
   ISX_TRY(ws[WS_TC_SCRATCH].ensure((size_t)sms * rows * w * 2, "tc scratch"));
   ISX_TRY(ws[WS_TC_STATUS].ensure(64, "tc status"));
@@ -1079,7 +1162,7 @@ isx_status bound_bf16(isx_inr inr, const CellSource& src, int64_t n, isx_bound_m
   set_kappas(a, w);
   TcMaps maps;
   std::memset(&maps, 0, sizeof(maps));
-  ISX_TRY(make_map(&maps.scratch, a.scratch, w, (uint64_t)sms * rows, 64, 128));
+  ISX_TRY(make_scratch_map(&maps.scratch, a.scratch, w, rows, sms));
   ISX_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), st));
   const bool tracing = std::getenv("ISX_TRACE") != nullptr;
   a.trace = nullptr;
@@ -1183,7 +1266,7 @@ extern "C" isx_status isx_bound_cells_noalloc(isx_inr inr, const float* d_lo, co
   }
   if (n == 0) return ISX_OK;
   const int w = inr->w, H = inr->H;
-  const int rows = std::max(1, w * std::max(0, H - 3));
+  const int rows = std::max(128, w * std::max(0, H - 3));   // >= one 128-row TMA box
   const size_t per_cta = (((size_t)rows * w * 2) + 255) & ~size_t(255);
   if (per_cta > kStaticScratchBytes - kStaticStatusBytes) {
     set_error("isx_bound_cells_noalloc: this network needs " + std::to_string(per_cta) +
@@ -1218,7 +1301,7 @@ extern "C" isx_status isx_bound_cells_noalloc(isx_inr inr, const float* d_lo, co
   set_kappas(a, w);
   TcMaps maps;
   std::memset(&maps, 0, sizeof(maps));
-  ISX_TRY(make_map(&maps.scratch, a.scratch, w, (uint64_t)grid * a.rows_per_cta, 64, 128));
+  ISX_TRY(make_scratch_map(&maps.scratch, a.scratch, w, a.rows_per_cta, grid));
   // the status word must start at zero on every call; the slices need no clearing (every row is
   // written before it is read)
   ISX_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), st));

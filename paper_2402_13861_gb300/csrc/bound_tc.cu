@@ -269,41 +269,31 @@ __device__ __forceinline__ bool ring_gemv(const Smem& s, int* status, uint32_t& 
   return true;
 }
 
-// B = D_j W_j^T in place: the 16-byte units of B (K-major, 128-byte swizzle) from index g on, with
-// stride kScaleThreads, scaled by alpha along K (the math warps run it with g = mt, mt + 128, ...;
-// four units in flight per thread).
-constexpr int kScaleThreads = 3 * kMathThreads;
+// B = D_j W_j^T in place, by the math warps: every thread owns one logical 8-column K chunk (its 8
+// alphas stay in registers) and walks W / 4 / (4 / KC) rows of it; the 8 lanes that share a row cover
+// its whole swizzled 128-byte row, so each warp access touches 4 rows x 128 contiguous bytes.
 template <int W>
-__device__ __forceinline__ void scale_b(const Smem& s, const float* al, int g) {
-  constexpr int UNITS = (W / 64) * W * 8;
-  for (int u0 = g; u0 < UNITS; u0 += 4 * kScaleThreads) {
-    uint4 val[4];
-    int k0[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int uidx = u0 + e * kScaleThreads;
-      if (uidx < UNITS) {
-        const int c = uidx / (W * 8), rem = uidx % (W * 8), nrow = rem >> 3, pu = rem & 7;
-        k0[e] = c * 64 + 8 * (pu ^ (nrow & 7));
-        val[e] = *reinterpret_cast<const uint4*>(s.B + (size_t)uidx * 16);
-      }
-    }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int uidx = u0 + e * kScaleThreads;
-      if (uidx < UNITS) {
-        const float4 a0 = *reinterpret_cast<const float4*>(al + k0[e]);
-        const float4 a1 = *reinterpret_cast<const float4*>(al + k0[e] + 4);
-        __nv_bfloat162* hv = reinterpret_cast<__nv_bfloat162*>(&val[e]);
-        float2 f0 = __bfloat1622float2(hv[0]), f1 = __bfloat1622float2(hv[1]);
-        float2 f2 = __bfloat1622float2(hv[2]), f3 = __bfloat1622float2(hv[3]);
-        hv[0] = __floats2bfloat162_rn(f0.x * a0.x, f0.y * a0.y);
-        hv[1] = __floats2bfloat162_rn(f1.x * a0.z, f1.y * a0.w);
-        hv[2] = __floats2bfloat162_rn(f2.x * a1.x, f2.y * a1.y);
-        hv[3] = __floats2bfloat162_rn(f3.x * a1.z, f3.y * a1.w);
-        *reinterpret_cast<uint4*>(s.B + (size_t)uidx * 16) = val[e];
-      }
-    }
+__device__ __forceinline__ void scale_b_rows(const Smem& s, const float* al, int mt) {
+  constexpr int KC = W / 64, WPC = 4 / KC, ROWS = W / WPC;   // warps per K chunk, rows per warp
+  const int mw = mt >> 5, l = mt & 31;
+  const int c = mw % KC, part = mw / KC, L = l & 7, roff = l >> 3;
+  const int k0 = c * 64 + 8 * L;
+  const float4 a0 = *reinterpret_cast<const float4*>(al + k0);
+  const float4 a1 = *reinterpret_cast<const float4*>(al + k0 + 4);
+  uint8_t* base = s.B + (size_t)c * W * 128;
+#pragma unroll 4
+  for (int i = 0; i < ROWS / 4; ++i) {
+    const int n = part * ROWS + roff + 4 * i;
+    uint4* pu = reinterpret_cast<uint4*>(base + (size_t)n * 128 + ((L ^ (n & 7)) << 4));
+    uint4 v = *pu;
+    __nv_bfloat162* hv = reinterpret_cast<__nv_bfloat162*>(&v);
+    const float2 f0 = __bfloat1622float2(hv[0]), f1 = __bfloat1622float2(hv[1]);
+    const float2 f2 = __bfloat1622float2(hv[2]), f3 = __bfloat1622float2(hv[3]);
+    hv[0] = __floats2bfloat162_rn(f0.x * a0.x, f0.y * a0.y);
+    hv[1] = __floats2bfloat162_rn(f1.x * a0.z, f1.y * a0.w);
+    hv[2] = __floats2bfloat162_rn(f2.x * a1.x, f2.y * a1.y);
+    hv[3] = __floats2bfloat162_rn(f3.x * a1.z, f3.y * a1.w);
+    *pu = v;
   }
 }
 
@@ -759,7 +749,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
           if (!group_wait(&s.bar[BAR_WLOADED], wl_n & 1)) { ok = false; break; }
           ++wl_n;
           if (mt == 0) trace(args, 0, cell / gridDim.x, 25 + 2 * (j - 1));
-          for (int g = mt; g < kScaleThreads; g += kMathThreads) scale_b<W>(s, al, g);
+          scale_b_rows<W>(s, al, mt);
           fence_async_shared();
           math_sync();
         } else {

@@ -20,6 +20,9 @@ Sec. IV-C:
 * read-off at the output: [x0 - r, x0 + r] (Eq. 2), or mu +- k sigma (Eq. 7, Algorithm 1), or the
   RA-UA variant: sound propagation with sigma^2 = (1/3) sum_i x_i^2 at the output only
   (Sec. IV-A).
+* RA-Fixed (Sec. V-A.4 baselines; App. A): the reduced form that keeps only the three input
+  symbols and condenses every other coefficient of a neuron into one non-negative radius of its
+  own (``propagate_rafixed``).
 
 Readings where the paper is silent (listed in the design notes):
 * The Chebyshev ReLU line is not printed.  For l < 0 < u it is the chord through (l, 0) and
@@ -35,7 +38,7 @@ from scipy.special import erf
 
 from .mlp import as_f64_layers
 
-SOUND, CLT, RAUA = "sound", "clt", "raua"
+SOUND, CLT, RAUA, RAFIXED = "sound", "clt", "raua", "rafixed"
 
 
 def relu_chebyshev(l, u):
@@ -109,13 +112,45 @@ def propagate(layers, lo, hi, mode):
     return c[:, 0], X[:, :, 0]
 
 
+def propagate_rafixed(layers, lo, hi):
+    """RA-Fixed: sound affine arithmetic that keeps the input symbols eps_1..3 and folds all other
+    symbols of a neuron into one radius r >= 0 that belongs to that neuron alone.
+
+    A neuron is c + sum_d A_d eps_d + r eta with eta in [-1, 1] private to the neuron, so
+      linear layer (Eq. 3 on the kept symbols; the private terms of the inputs combine as
+      sum_k |W_nk| r_k, the largest |sum_k W_nk r_k eta_k| can be):
+          c' = W c + b,  A' = A W^T,  r' = r |W|^T;
+      ReLU (Eq. 4, Chebyshev line on [c - s, c + s], s = sum_d |A_d| + r):
+          c' = alpha c + beta,  A' = alpha A,  r' = alpha r + gamma.
+    Returns the output centre (B,) and spread sum_d |A_d| + r (B,): the bound [c - s, c + s]."""
+    L = as_f64_layers(layers)
+    c, A = input_form(lo, hi, SOUND)
+    r = np.zeros(c.shape)
+    for l, (W, b) in enumerate(L):
+        c = c @ W.T + b
+        A = A @ W.T
+        r = r @ np.abs(W).T
+        if l == len(L) - 1:
+            break
+        s = np.sum(np.abs(A), axis=1) + r
+        alpha, beta, gamma = relu_chebyshev(c - s, c + s)
+        c = alpha * c + beta
+        A = A * alpha[:, None, :]
+        r = alpha * r + gamma
+    return c[:, 0], np.sum(np.abs(A[:, :, 0]), axis=1) + r[:, 0]
+
+
 def bound(layers, lo, hi, mode, batch=64):
-    """Centre and spread of every box: (x0, r) for SOUND, (mu, sigma) for CLT and RAUA."""
+    """Centre and spread of every box: (x0, r) for SOUND and RAFIXED, (mu, sigma) for CLT and RAUA."""
     lo = np.asarray(lo).reshape(-1, 3)
     hi = np.asarray(hi).reshape(-1, 3)
     n = lo.shape[0]
     centre = np.empty(n)
     spread = np.empty(n)
+    if mode == RAFIXED:
+        for s in range(0, n, batch):
+            centre[s:s + batch], spread[s:s + batch] = propagate_rafixed(layers, lo[s:s + batch], hi[s:s + batch])
+        return centre, spread
     prop_mode = CLT if mode == CLT else SOUND
     for s in range(0, n, batch):
         x0, coef = propagate(layers, lo[s:s + batch], hi[s:s + batch], prop_mode)
@@ -131,7 +166,7 @@ def bound(layers, lo, hi, mode, batch=64):
 
 def interval(centre, spread, mode, k):
     """[lower, upper] of the read-off: [x0 - r, x0 + r] or [mu - k sigma, mu + k sigma]."""
-    if mode == SOUND:
+    if mode in (SOUND, RAFIXED):
         return centre - spread, centre + spread
     return centre - k * spread, centre + k * spread
 

@@ -76,6 +76,50 @@ def extract_active(layers, max_level, isos, mode, k=3.0, batch=64, start_level=0
     return levels
 
 
+def kd_box(ijk, depth):
+    """Box of k-d cells at ``depth`` of Algorithm 1: the widest side is bisected at every depth (x, then
+    y, then z on ties, starting from the cube [-1, 1]^3), so axis a has been split
+    ``(depth + 2 - a) // 3`` times and the cell ``(i, j, k)`` spans ``-1 + 2 i_a / 2^splits_a`` onwards."""
+    ijk = np.asarray(ijk, dtype=np.float64).reshape(-1, 3)
+    splits = np.array([(depth + 2 - a) // 3 for a in range(3)])
+    size = 2.0 / (2.0 ** splits)
+    lo = -1.0 + ijk * size[None, :]
+    return lo, lo + size[None, :]
+
+
+def kd_extract_active(layers, max_level, isos, mode, k=3.0, batch=64):
+    """Algorithm 1 literally, breadth first: every node of depths 0 .. 3 max_level is bounded, a node
+    keeps the iso-values whose value lies inside its bound, and a surviving node below the maximum
+    depth is split in two along its widest side (``depth mod 3`` is that axis).  The leaves at depth
+    3 max_level are the cubes of the octree's finest level.  Returns one dict per depth as
+    extract_active does."""
+    isos = np.asarray(isos, dtype=np.float64)
+    full = (1 << isos.shape[0]) - 1
+    ijk = np.zeros((1, 3), dtype=np.int64)
+    masks = np.array([full], dtype=np.int64)
+    depths = []
+    D = 3 * max_level
+    for depth in range(D + 1):
+        lo, hi = kd_box(ijk, depth)
+        if ijk.shape[0]:
+            centre, spread = affine.bound(layers, lo, hi, mode, batch=batch)
+        else:
+            centre = spread = np.zeros(0)
+        lower, upper = affine.interval(centre, spread, mode, k)
+        new = masks & iso_bits(lower, upper, isos)
+        depths.append(dict(depth=depth, ijk=ijk, mask_in=masks, centre=centre, spread=spread,
+                           lower=lower, upper=upper, mask=new))
+        keep = new != 0
+        if depth < D:
+            axis = depth % 3
+            par = ijk[keep]
+            kids = np.repeat(par, 2, axis=0)
+            kids[:, axis] = 2 * kids[:, axis] + np.tile(np.array([0, 1]), par.shape[0])
+            ijk = kids
+            masks = np.repeat(new[keep], 2)
+    return depths
+
+
 def active_cells(levels):
     last = levels[-1]
     keep = last["mask"] != 0

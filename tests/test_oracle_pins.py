@@ -351,3 +351,81 @@ def test_mc_table_matches_golden():
         vals = list(map(int, r))
         assert vals[0] == c and vals[1] == ntri[c]
         assert vals[2:] == tab[c].ravel().tolist()
+
+
+def test_kd_tree_leaves_are_octree_cubes_and_nested():
+    """Algorithm 1's k-d tree bounds every octree cube and the two intermediate boxes between
+    consecutive cube depths, so its leaves at depth 3 L are a subset of the octree's active cells
+    (same mode and k), and sound bounds still never miss a dense crossing cell (brute force, 8^3)."""
+    layers = inr.random_inr([3, 16, 16, 1], 5)
+    L = 3
+    vals = mlp.mlp_forward(layers, octree.lattice_points(1 << L))
+    isos = np.quantile(vals, [0.3, 0.7])
+    for mode, k in (("sound", 0.0), ("clt", 2.0)):
+        kd = octree.kd_extract_active(layers, L, isos, mode, k=k, batch=64)
+        oc = octree.extract_active(layers, L, isos, mode, k=k, batch=64)
+        kd_cells, kd_masks = octree.active_cells(kd)
+        oc_cells, oc_masks = octree.active_cells(oc)
+        occ = {tuple(c): m for c, m in zip(oc_cells.tolist(), oc_masks.tolist())}
+        for c, m in zip(kd_cells.tolist(), kd_masks.tolist()):
+            assert tuple(c) in occ and (m & ~occ[tuple(c)]) == 0
+        # every third depth holds cubes: their boxes equal the octree's boxes of that level
+        for d in (0, 3, 6):
+            lo, hi = octree.kd_box(kd[d]["ijk"], d)
+            lo2, hi2 = octree.cell_box(kd[d]["ijk"], d // 3)
+            assert np.array_equal(lo, lo2) and np.array_equal(hi, hi2)
+        if mode == "sound":
+            got = {tuple(c): m for c, m in zip(kd_cells.tolist(), kd_masks.tolist())}
+            for q, iso in enumerate(isos):
+                for c in mc.crossing_cells(vals, 1 << L, iso).tolist():
+                    assert tuple(c) in got and (got[tuple(c)] >> q) & 1
+
+
+# ---- RA-Fixed: the reduced form against full affine arithmetic and brute force ----------------
+
+def test_rafixed_one_hidden_layer_equals_full_affine():
+    """With one hidden layer the only condensed symbols are the ReLU's own, whose output
+    coefficients w_m gamma_m add up in absolute value to |w| gamma either way: RA-Fixed and full
+    affine arithmetic give the same centre and radius."""
+    layers = inr.random_inr([3, 48, 1], 11)
+    lo, hi = boxes.random_boxes(200, 3, -6, -1)
+    c0, r0 = affine.bound(layers, lo, hi, affine.SOUND)
+    c1, r1 = affine.bound(layers, lo, hi, affine.RAFIXED)
+    assert np.allclose(c0, c1, rtol=1e-12, atol=1e-12) and np.allclose(r0, r1, rtol=1e-12, atol=1e-12)
+
+
+def test_rafixed_two_hidden_layers_is_full_affine_loosened():
+    """With two hidden layers the second layer's pre-activation radius is the same (sum_m |W_nm|
+    gamma_m either way), so the second ReLU's lines and the centre agree; at the output the
+    condensed radius sum_n |w_n| alpha_n |W_nm| gamma_m bounds the full form's |sum_n ...| term by
+    term: RA-Fixed radius >= full radius, with a strict gap for most boxes."""
+    layers = inr.random_inr([3, 32, 32, 1], 12)
+    lo, hi = boxes.random_boxes(300, 4, -5, -1)
+    c0, r0 = affine.bound(layers, lo, hi, affine.SOUND)
+    c1, r1 = affine.bound(layers, lo, hi, affine.RAFIXED)
+    assert np.allclose(c0, c1, rtol=1e-11, atol=1e-12)
+    assert np.all(r1 >= r0 - 1e-12 * np.abs(r0))
+    assert np.mean(r1 > r0 * (1 + 1e-9)) > 0.5
+
+
+def test_rafixed_bounds_contain_samples_and_linear_nets_are_exact(small):
+    layers, _, _ = small
+    rng = np.random.default_rng(6)
+    lo, hi = boxes.random_boxes(400, 10, -8, -1)
+    c, r = affine.bound(layers, lo, hi, affine.RAFIXED, batch=200)
+    lo64, hi64 = lo.astype(np.float64), hi.astype(np.float64)
+    u = rng.uniform(size=(400, 2000, 3))
+    corners = np.array([[(q >> d) & 1 for d in range(3)] for q in range(8)], dtype=np.float64)
+    u = np.concatenate([u, np.broadcast_to(corners, (400, 8, 3))], axis=1)
+    pts = lo64[:, None, :] + u * (hi64 - lo64)[:, None, :]
+    v = mlp.mlp_forward(layers, pts.reshape(-1, 3)).reshape(400, -1)
+    assert np.all(v.max(1) <= c + r + 1e-12) and np.all(v.min(1) >= c - r - 1e-12)
+    # a net whose ReLUs are all the identity on [-1, 1]^3 is affine: the radius is exact
+    lin = _linear_regime_net(7, [3, 8, 8, 8, 1], +1)
+    lo, hi = boxes.random_boxes(50, 8, -4, -1)
+    c, r = affine.bound(lin, lo, hi, affine.RAFIXED)
+    Weff = lin[0][0]
+    for W, _ in lin[1:]:
+        Weff = W @ Weff
+    h = (hi.astype(np.float64) - lo.astype(np.float64)) / 2
+    assert np.allclose(r, np.abs(Weff[0]) @ h.T, rtol=1e-10)

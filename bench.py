@@ -122,21 +122,25 @@ def extraction_forms(pkg, net, L, isos, plain, plain_ms, mode, k, prec):
     """End-to-end time of the other extraction forms on the same INR and isos, and the crossing
     (cell, iso) pairs of the dense extraction each form misses: bounding stopped at level 6 with
     tensor-core corner values, the proposer-assisted form (committed proposer), dense extraction
-    (FP32 and tensor-core evaluation).  Each form runs once after a warm-up of the same call."""
+    (FP32 and tensor-core evaluation), sound RA-Fixed bounds, and the k-d tree against the octree
+    one level lower.  Each form runs once after a warm-up of the same call."""
     import torch
     from paper_2402_13861_gb300 import proposer as gp
     from paper_2402_13861_gb300.train_proposer import missed
     st = torch.cuda.current_stream()
     bufs = {}
 
-    def timed(**kw):
+    def timed_level(level, **kw):
         for rep in range(2):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(st)
-            r = net.extract(L, isos, buffers=bufs, active_cap=1 << 27, tri_cap=1 << 25, **kw)
+            r = net.extract(level, isos, buffers=bufs, active_cap=1 << 27, tri_cap=1 << 25, **kw)
             b.record(st)
             torch.cuda.synchronize()
         return r, a.elapsed_time(b)
+
+    def timed(**kw):
+        return timed_level(L, **kw)
 
     dense32, ms_d32 = timed(prec="fp32", dense=True)
     cross = None
@@ -167,6 +171,15 @@ def extraction_forms(pkg, net, L, isos, plain, plain_ms, mode, k, prec):
     _, ms_dtc = timed(prec="fp32", dense=True, eval_prec="bf16")
     out["dense_fp32_eval"] = {"ms": ms_d32, "crossing_pairs": tot}
     out["dense_tc_eval"] = {"ms": ms_dtc}
+    # the reduced range-analysis baseline: sound RA-Fixed bounds (one fused float32 kernel)
+    r, ms = timed(mode="rafixed", prec="fp32")
+    m, _ = missed(r["codes"], r["masks"], cross)
+    out["rafixed_fp32"] = {"ms": ms, "cells_bounded": int(sum(r["cells_bounded"])), "n_active": r["n_active"],
+                           "missed_pairs": m, "missed_rate": m / max(tot, 1)}
+    # Algorithm 1's k-d tree (widest-side bisection) against the octree, one level lower (256^3)
+    for name, kd in (("octree_256", False), ("kd_tree_256", True)):
+        r, ms = timed_level(L - 1, mode=mode, k=k, prec=prec, kd_tree=kd)
+        out[name] = {"ms": ms, "cells_bounded": int(sum(r["cells_bounded"])), "n_active": r["n_active"]}
     return out
 
 

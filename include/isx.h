@@ -53,8 +53,13 @@ typedef enum {
  *         (Table VII), output N(mu, sigma^2) with sigma^2 = sum x_i^2 (Eq. 7), bound mu +- k sigma
  *         (Algorithm 1).
  *  RAUA:  SOUND propagation, then sigma^2 = (1/3) sum x_i^2 at the output only (Sec. IV-A),
- *         bound x0 +- k sigma. */
-typedef enum { ISX_BOUND_SOUND = 0, ISX_BOUND_CLT = 1, ISX_BOUND_RAUA = 2 } isx_bound_mode;
+ *         bound x0 +- k sigma.
+ *  RAFIXED: the reduced range-analysis baseline (Sec. V-A.4, App. A): sound affine arithmetic
+ *         that keeps the three input symbols and condenses every other coefficient of a neuron into
+ *         one private radius (linear layers carry it through |W|); bound x0 +- r, k unused.
+ *         Float32 only (prec = ISX_PREC_BF16 gives ISX_ERR_UNSUPPORTED); inflate applies as for
+ *         SOUND.  Hidden widths that are multiples of 16. */
+typedef enum { ISX_BOUND_SOUND = 0, ISX_BOUND_CLT = 1, ISX_BOUND_RAUA = 2, ISX_BOUND_RAFIXED = 3 } isx_bound_mode;
 
 /* Arithmetic of the coefficient propagation.  FP32: float32 storage and FMA.  BF16: coefficient
  * matrices stored in bfloat16 and multiplied on tcgen05 tensor cores with float32 accumulation;
@@ -138,6 +143,11 @@ typedef struct {
   /* corner / lattice evaluation: ISX_PREC_FP32 (CUDA cores, the default) or ISX_PREC_BF16
      (tensor cores with two-term BF16 operands, FP32-class accuracy; see isx_eval_points) */
   isx_precision eval_prec;
+  /* 0: octree (every level splits all three axes; the default). 1: the k-d tree of Algorithm 1: every
+     depth bisects the widest side (x, then y, then z on ties), depths 0 .. 3 max_level, so every third
+     depth and the leaves are cubes; bound_stop_level counts octree levels (depth 3 x level). Not
+     combined with the proposer. */
+  int kd_tree;
 } isx_extract_params;
 
 typedef struct {

@@ -18,9 +18,9 @@ ISX_MAX_ISO = 32
 ISX_MAX_LEVEL = 10
 ISX_MC_MAX_TRI = 5
 
-SOUND, CLT, RAUA = 0, 1, 2
+SOUND, CLT, RAUA, RAFIXED = 0, 1, 2, 3
 FP32, BF16 = 0, 1
-MODES = {"sound": SOUND, "clt": CLT, "raua": RAUA}
+MODES = {"sound": SOUND, "clt": CLT, "raua": RAUA, "rafixed": RAFIXED}
 PRECS = {"fp32": FP32, "bf16": BF16}
 
 STATUS = {0: "ISX_OK", 1: "ISX_ERR_ARG", 2: "ISX_ERR_CUDA", 3: "ISX_ERR_CAPACITY", 4: "ISX_ERR_TIMEOUT",
@@ -52,7 +52,7 @@ class ExtractParams(C.Structure):
     _fields_ = [("max_level", C.c_int), ("n_iso", C.c_int), ("iso", C.c_float * ISX_MAX_ISO),
                 ("mode", C.c_int), ("k", C.c_float), ("prec", C.c_int), ("inflate", C.c_int),
                 ("bound_stop_level", C.c_int), ("proposer", C.c_void_p), ("proposer_level", C.c_int),
-                ("tau_lo", C.c_float), ("tau_hi", C.c_float), ("eval_prec", C.c_int)]
+                ("tau_lo", C.c_float), ("tau_hi", C.c_float), ("eval_prec", C.c_int), ("kd_tree", C.c_int)]
 
 
 class Mesh(C.Structure):
@@ -230,7 +230,7 @@ class Inr:
 
     @staticmethod
     def params(max_level, isos, mode="sound", k=3.0, prec="fp32", inflate=False, bound_stop_level=-1,
-               proposer=None, proposer_level=1, tau_lo=0.0, tau_hi=1.0, eval_prec="fp32"):
+               proposer=None, proposer_level=1, tau_lo=0.0, tau_hi=1.0, eval_prec="fp32", kd_tree=False):
         p = ExtractParams()
         p.max_level = max_level
         isos = list(np.atleast_1d(np.asarray(isos, dtype=np.float32)))
@@ -247,16 +247,17 @@ class Inr:
         p.tau_lo = float(tau_lo)
         p.tau_hi = float(tau_hi)
         p.eval_prec = PRECS[eval_prec]
+        p.kd_tree = int(bool(kd_tree))
         return p
 
     def extract(self, max_level, isos, mode="sound", k=3.0, prec="fp32", inflate=False, bound_stop_level=-1,
                 active_cap=1 << 16, tri_cap=1 << 18, dense=False, stream=None, buffers=None, proposer=None,
-                proposer_level=1, tau_lo=0.0, tau_hi=1.0, eval_prec="fp32"):
+                proposer_level=1, tau_lo=0.0, tau_hi=1.0, eval_prec="fp32", kd_tree=False):
         """Hierarchical (or, with dense=True, dense) extraction.  Grows the output buffers and
         retries once if a capacity is exceeded.  Returns a dict of tensors and counters."""
         import torch
         p = self.params(max_level, isos, mode, k, prec, inflate, bound_stop_level, proposer, proposer_level,
-                        tau_lo, tau_hi, eval_prec)
+                        tau_lo, tau_hi, eval_prec, kd_tree)
         fn = load().isx_extract_dense if dense else load().isx_extract_isosurface
         dev = torch.device("cuda", torch.cuda.current_device())
         bufs = buffers if buffers is not None else {}

@@ -68,6 +68,13 @@ isx_status check_inr(isx_inr inr) {
 
 isx_status bound_dispatch(isx_inr inr, const CellSource& src, int64_t n, isx_bound_mode mode, isx_precision prec,
                           int inflate, float* center, float* spread, cudaStream_t st) {
+  if (mode == ISX_BOUND_RAFIXED) {
+    if (prec != ISX_PREC_FP32) {
+      set_error("RA-Fixed bounds are computed in float32 only");
+      return ISX_ERR_UNSUPPORTED;
+    }
+    return bound_rafixed(inr, src, n, inflate, center, spread, st);
+  }
   if (prec == ISX_PREC_BF16) return bound_bf16(inr, src, n, mode, inflate, center, spread, st);
   return bound_fp32(inr, src, n, mode, inflate, center, spread, st);
 }
@@ -86,17 +93,25 @@ isx_status validate_params(const isx_extract_params* p, const isx_mesh* m) {
     set_error("n_iso must be in [1, 32]");
     return ISX_ERR_ARG;
   }
-  if (p->mode < ISX_BOUND_SOUND || p->mode > ISX_BOUND_RAUA || p->prec < ISX_PREC_FP32 || p->prec > ISX_PREC_BF16) {
+  if (p->mode < ISX_BOUND_SOUND || p->mode > ISX_BOUND_RAFIXED || p->prec < ISX_PREC_FP32 || p->prec > ISX_PREC_BF16) {
     set_error("bad mode or precision");
     return ISX_ERR_ARG;
   }
-  if (!(p->k >= 0.0f) && p->mode != ISX_BOUND_SOUND) {
+  if (!(p->k >= 0.0f) && !sound_readout(p->mode)) {
     set_error("k must be >= 0");
     return ISX_ERR_ARG;
   }
   if (p->eval_prec < ISX_PREC_FP32 || p->eval_prec > ISX_PREC_BF16) {
     set_error("bad evaluation precision");
     return ISX_ERR_ARG;
+  }
+  if (p->mode == ISX_BOUND_RAFIXED && p->prec != ISX_PREC_FP32) {
+    set_error("RA-Fixed bounds are computed in float32 only");
+    return ISX_ERR_UNSUPPORTED;
+  }
+  if (p->kd_tree && p->proposer) {
+    set_error("the k-d mode does not take a proposer");
+    return ISX_ERR_UNSUPPORTED;
   }
   if (p->proposer && !(p->tau_lo >= 0.0f && p->tau_lo < p->tau_hi && p->tau_hi <= 1.0f)) {
     set_error("proposer thresholds must satisfy 0 <= tau_lo < tau_hi <= 1");
@@ -334,7 +349,7 @@ isx_status isx_bound_cells(isx_inr inr, const float* d_lo, const float* d_hi, in
     set_error("bad size or null pointer");
     return ISX_ERR_ARG;
   }
-  if (mode < ISX_BOUND_SOUND || mode > ISX_BOUND_RAUA || prec < ISX_PREC_FP32 || prec > ISX_PREC_BF16) {
+  if (mode < ISX_BOUND_SOUND || mode > ISX_BOUND_RAFIXED || prec < ISX_PREC_FP32 || prec > ISX_PREC_BF16) {
     set_error("bad mode or precision");
     return ISX_ERR_ARG;
   }
@@ -391,6 +406,46 @@ isx_status isx_extract_isosurface(isx_inr inr, const isx_extract_params* p, isx_
   int64_t* d_count = ws[WS_COUNT].as<int64_t>();
   int64_t n = 1;
   Slot ca = WS_CODES_A, cb = WS_CODES_B, ma = WS_MASK_A, mb = WS_MASK_B;
+  if (p->kd_tree) {
+    // Algorithm 1 literally: depth d bisects axis d mod 3 (the widest side, x before y before z);
+    // per-axis split counts at depth d are ceil(d/3), ceil((d-1)/3), floor(d/3)
+    const int D = 3 * L, stop_d = 3 * stop;
+    for (int depth = 0; depth <= D; ++depth) {
+      const bool bounded = depth <= stop_d;
+      const bool expand = depth < D;
+      const int lvl = (depth + 2) / 3;                // octree level the statistics are filed under
+      mesh->cells_visited[lvl] += n;
+      if (bounded) mesh->cells_bounded[lvl] += n;
+      if (n > 0) {
+        ISX_TRY(ws[WS_CENTER].ensure((size_t)n * 4, "center"));
+        ISX_TRY(ws[WS_SPREAD].ensure((size_t)n * 4, "spread"));
+        if (bounded) {
+          CellSource src;
+          src.codes = ws[ca].as<uint32_t>();
+          src.level = depth / 3;
+          src.lv[0] = (depth + 2) / 3;
+          src.lv[1] = (depth + 1) / 3;
+          src.lv[2] = depth / 3;
+          ISX_TRY(bound_dispatch(inr, src, n, p->mode, p->prec, p->inflate, ws[WS_CENTER].as<float>(),
+                                 ws[WS_SPREAD].as<float>(), st));
+        }
+        size_t need = (size_t)(expand ? 2 : 1) * n * 4;
+        ISX_TRY(ws[cb].ensure(need, "codes"));
+        ISX_TRY(ws[mb].ensure(need, "masks"));
+      }
+      ISX_TRY(level_step(inr, ws[ca].as<uint32_t>(), ws[ma].as<uint32_t>(), n, ws[WS_CENTER].as<float>(),
+                         ws[WS_SPREAD].as<float>(), bounded, iso, p->mode, p->k, p->inflate, expand,
+                         ws[cb].as<uint32_t>(), ws[mb].as<uint32_t>(), d_count, st, nullptr, depth % 3));
+      int64_t cnt = 0;
+      ISX_CUDA(cudaMemcpyAsync(&cnt, d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+      ISX_CUDA(cudaStreamSynchronize(st));
+      mesh->cells_kept[lvl] += expand ? cnt / 2 : cnt;
+      std::swap(ca, cb);
+      std::swap(ma, mb);
+      n = cnt;
+    }
+    return mesh_from_active(inr, p, ws[ca].as<uint32_t>(), ws[ma].as<uint32_t>(), n, mesh, tm, st);
+  }
   Slot aca = WS_ANC_C_A, acb = WS_ANC_C_B, asa = WS_ANC_S_A, asb = WS_ANC_S_B, aga = WS_ANC_G_A, agb = WS_ANC_G_B;
   for (int level = 0; level <= L; ++level) {
     const bool bounded = level <= stop;

@@ -387,8 +387,9 @@ isx_status isx_batch_create(const isx_inr* inrs, const isx_extract_params* param
       set_error("batch: every entry must use the same bound mode and inflation");
       return ISX_ERR_ARG;
     }
-    if (params[i].proposer || (params[i].bound_stop_level >= 0 && params[i].bound_stop_level < params[i].max_level)) {
-      set_error("batch: the proposer and bound_stop_level are not supported in a batch");
+    if (params[i].proposer || params[i].kd_tree ||
+        (params[i].bound_stop_level >= 0 && params[i].bound_stop_level < params[i].max_level)) {
+      set_error("batch: the proposer, the k-d mode and bound_stop_level are not supported in a batch");
       return ISX_ERR_UNSUPPORTED;
     }
   }

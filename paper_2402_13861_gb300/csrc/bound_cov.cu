@@ -255,9 +255,9 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_bound_cov(const __grid_constan
         float hh[3];
         if (src.codes) {
           uint32_t code = src.codes[cell];
-          float size = ldexpf(2.0f, -src.level);
           int ijk[3] = {int(code & 1023u), int((code >> 10) & 1023u), int((code >> 20) & 1023u)};
           for (int d = 0; d < 3; ++d) {
+            const float size = ldexpf(2.0f, -axis_level(src, d));
             hh[d] = 0.5f * size;
             xc[d] = -1.0f + size * float(ijk[d]) + hh[d];
           }

@@ -21,6 +21,7 @@
 
 #include <string>
 #include "linearise.cuh"
+#include "cell_box.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -33,33 +34,6 @@ constexpr float kSafe = 1.0000010f;         // (1 + 2^-20): slack for evaluating
 constexpr float kInvSqrt3 = 0.57735026918962576f;
 
 __host__ __device__ __forceinline__ float gamma_k(int k) { return (k * kU) / (1.0f - k * kU); }
-
-// Box of cell `i` of the source: centre and half-width per axis.
-__device__ __forceinline__ void cell_box(const CellSource& s, int64_t i, int inflate, float xc[3],
-                                         float h[3]) {
-  if (s.codes) {
-    uint32_t code = s.codes[i];
-    float size = ldexpf(2.0f, -s.level);           // exact dyadic
-    int ijk[3] = {int(code & 1023u), int((code >> 10) & 1023u), int((code >> 20) & 1023u)};
-    for (int d = 0; d < 3; ++d) {
-      float lo = -1.0f + size * float(ijk[d]);      // exact
-      h[d] = 0.5f * size;
-      xc[d] = lo + h[d];
-    }
-  } else {
-    for (int d = 0; d < 3; ++d) {
-      float lo = s.lo[3 * i + d], hi = s.hi[3 * i + d];
-      xc[d] = 0.5f * (lo + hi);
-      if (inflate) {
-        // cover [lo, hi] despite the rounding of xc
-        float hu = __fmul_ru(__fsub_ru(hi, lo), 0.5f);
-        h[d] = __fadd_ru(hu, fabsf(xc[d]) * 1.2e-7f);
-      } else {
-        h[d] = 0.5f * (hi - lo);
-      }
-    }
-  }
-}
 
 // z_1 = W_0 x + b_0 over the box: centre, 3 coefficient rows, per-neuron reduction, slack.
 __global__ void k_input_layer(CellSource src, int64_t first, int nc, const float* __restrict__ W0,

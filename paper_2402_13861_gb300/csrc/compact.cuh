@@ -16,7 +16,7 @@ constexpr int kTile = kThreads * kPer;        // elements per block
 __device__ __forceinline__ uint32_t keep_bits(float center, float spread, const IsoSet& iso, int mode,
                                               float k, int inflate) {
   float lo, hi;
-  if (mode == ISX_BOUND_SOUND) {
+  if (sound_readout(mode)) {
     lo = inflate ? __fsub_rd(center, spread) : center - spread;
     hi = inflate ? __fadd_ru(center, spread) : center + spread;
   } else {

@@ -86,7 +86,7 @@ namespace isx {
 enum KernelId {
   K_INPUT, K_RELU, K_GEMV, K_GEMM_FP32, K_FRESH, K_REDUCE, K_OUTPUT, K_CULL, K_SCAN, K_SCATTER, K_MARK,
   K_FLAGCOUNT, K_SCATTER_FLAGS, K_EVAL_FP32, K_MC_COUNT, K_MC_EMIT, K_IOTA, K_BOUND_TC, K_TC_PREP, K_TC_OUTPUT,
-  K_EVAL_TC, K_BOUND_COV, K_PROP_GATE, K_PROP_MERGE, K_PROP_FWD, K_PROP_GRAD, K_PROP_ADAM, K_COUNT
+  K_EVAL_TC, K_BOUND_COV, K_PROP_GATE, K_PROP_MERGE, K_PROP_FWD, K_PROP_GRAD, K_PROP_ADAM, K_BOUND_RAFIXED, K_COUNT
 };
 namespace prof {
 // RAII bracket around one kernel launch: counts it, adds its algorithmic work, and (when
@@ -109,12 +109,24 @@ struct CellSource {
   const float* lo = nullptr;
   const float* hi = nullptr;
   const uint32_t* codes = nullptr;
-  int level = 0;
+  int level = 0;                       // octree level of the codes: every axis split `level` times
+  int lv[3] = {-1, -1, -1};            // k-d cells: split count per axis (lv[0] < 0: `level` for all)
 };
+// Split count of axis d of the codes of `s` (cells of width 2 / 2^count along d).
+__host__ __device__ __forceinline__ int axis_level(const CellSource& s, int d) { return s.lv[0] < 0 ? s.level : s.lv[d]; }
 
 // Bounds n cells in float32 with the layer-by-layer path; chunked over the workspace.
 isx_status bound_fp32(isx_inr inr, const CellSource& src, int64_t n, isx_bound_mode mode,
                       int inflate, float* d_center, float* d_spread, cudaStream_t st);
+
+// RA-Fixed bounds (input symbols kept, all others condensed per neuron), one fused float32 kernel.
+isx_status bound_rafixed(isx_inr inr, const CellSource& src, int64_t n, int inflate, float* d_center,
+                         float* d_spread, cudaStream_t st);
+bool rafixed_supported(isx_inr inr);
+// Whether the read-off of `mode` is the sound interval centre +- spread (no k).
+__host__ __device__ __forceinline__ bool sound_readout(int mode) {
+  return mode == ISX_BOUND_SOUND || mode == ISX_BOUND_RAFIXED;
+}
 
 // Tensor-core (tcgen05, bfloat16) path; ISX_ERR_UNSUPPORTED for shapes it does not cover.
 isx_status bound_bf16(isx_inr inr, const CellSource& src, int64_t n, isx_bound_mode mode,
@@ -162,7 +174,8 @@ struct AncIO {
 isx_status level_step(isx_inr inr, const uint32_t* codes, const uint32_t* masks, int64_t n,
                       const float* center, const float* spread, bool bounded, const IsoSet& iso,
                       isx_bound_mode mode, float k, int inflate, bool expand, uint32_t* out_codes,
-                      uint32_t* out_masks, int64_t* d_count, cudaStream_t st, const AncIO* anc = nullptr);
+                      uint32_t* out_masks, int64_t* d_count, cudaStream_t st, const AncIO* anc = nullptr,
+                      int split_axis = -1);
 
 // Stable compaction of the indices i < n with flags[i] != 0 into out_idx; count to *d_count.
 isx_status compact_flags(isx_inr inr, const uint8_t* flags, int64_t n, uint32_t* out_idx,

@@ -26,7 +26,7 @@ const char* names[K_COUNT] = {"input_layer",   "relu",          "center_gemv",  
                               "mark_corners",  "flag_count",    "scatter_flags", "eval_fp32",    "mc_count",
                               "mc_emit",       "iota",          "bound_tc",      "tc_prep",      "tc_output",
                               "eval_tc",       "bound_cov",     "prop_gate",     "prop_merge",   "prop_forward",
-                              "prop_grad",     "prop_adam"};
+                              "prop_grad",     "prop_adam",     "bound_rafixed"};
 
 void drain_locked() {
   for (auto& r : pending) {

@@ -337,7 +337,7 @@ __global__ void k_prop_merge(const uint32_t* idx, int64_t nb, const uint32_t* ma
   const uint32_t i = idx[j];
   const float c = c_sub[j], s = s_sub[j];
   float lo, hi;
-  if (mode == ISX_BOUND_SOUND) {
+  if (sound_readout(mode)) {
     lo = inflate ? __fsub_rd(c, s) : c - s;
     hi = inflate ? __fadd_ru(c, s) : c + s;
   } else {

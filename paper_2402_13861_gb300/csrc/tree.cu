@@ -68,9 +68,12 @@ __global__ void __launch_bounds__(1024) k_scan_counts(const int* counts, int64_t
   scan_block_counts_dev(counts, nb, offsets, d_total, scale);
 }
 
+// expand: 0 writes the survivors; 1 writes their 8 octree children; with split_axis >= 0 and expand
+// set, their 2 k-d children along that axis.
 __global__ void __launch_bounds__(kThreads) k_scatter_cells(const uint32_t* codes, const uint32_t* newmask,
                                                             int64_t n, const int64_t* offsets, int expand,
-                                                            uint32_t* out_codes, uint32_t* out_masks, AncIO anc) {
+                                                            int split_axis, uint32_t* out_codes, uint32_t* out_masks,
+                                                            AncIO anc) {
   __shared__ int warp_sums[32];
   __shared__ int total;
   int64_t base = (int64_t)blockIdx.x * kTile;
@@ -83,7 +86,14 @@ __global__ void __launch_bounds__(kThreads) k_scatter_cells(const uint32_t* code
     if (f) {
       int64_t o = off + r;
       uint32_t code = codes[i];
-      if (expand) {
+      if (expand && split_axis >= 0) {
+        const uint32_t sh = 10u * (uint32_t)split_axis;
+        const uint32_t ca = ((code >> sh) & 1023u) << 1, rest = code & ~(1023u << sh);
+        out_codes[2 * o] = rest | (ca << sh);
+        out_codes[2 * o + 1] = rest | ((ca + 1u) << sh);
+        out_masks[2 * o] = m;
+        out_masks[2 * o + 1] = m;
+      } else if (expand) {
         uint32_t ci = (code & 1023u) << 1, cj = ((code >> 10) & 1023u) << 1, ck = ((code >> 20) & 1023u) << 1;
         for (int c = 0; c < 8; ++c) {
           uint32_t cc = (ci + (c & 1)) | ((cj + ((c >> 1) & 1)) << 10) | ((ck + ((c >> 2) & 1)) << 20);
@@ -162,7 +172,7 @@ isx_status iota_u32(uint32_t* out, int64_t n, cudaStream_t st) {
 isx_status level_step(isx_inr inr, const uint32_t* codes, const uint32_t* masks, int64_t n,
                       const float* center, const float* spread, bool bounded, const IsoSet& iso,
                       isx_bound_mode mode, float k, int inflate, bool expand, uint32_t* out_codes,
-                      uint32_t* out_masks, int64_t* d_count, cudaStream_t st, const AncIO* anc) {
+                      uint32_t* out_masks, int64_t* d_count, cudaStream_t st, const AncIO* anc, int split_axis) {
   if (n == 0) {
     ISX_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int64_t), st));
     return ISX_OK;
@@ -183,13 +193,13 @@ isx_status level_step(isx_inr inr, const uint32_t* codes, const uint32_t* masks,
   ISX_LAUNCH_CHECK("k_cull_count");
   {
     prof::Scope _ps(K_SCAN, st, 0, 0);
-    k_scan_counts<<<1, 1024, 0, st>>>(bc, nb, boff, d_count, expand ? 8 : 1);
+    k_scan_counts<<<1, 1024, 0, st>>>(bc, nb, boff, d_count, expand ? (split_axis >= 0 ? 2 : 8) : 1);
   }
   ISX_LAUNCH_CHECK("k_scan_counts");
   {
     prof::Scope _ps(K_SCATTER, st, 0, 0);
-    k_scatter_cells<<<(unsigned)nb, kThreads, 0, st>>>(codes, nm, n, boff, expand ? 1 : 0, out_codes, out_masks,
-                                                       anc ? *anc : AncIO());
+    k_scatter_cells<<<(unsigned)nb, kThreads, 0, st>>>(codes, nm, n, boff, expand ? 1 : 0, split_axis, out_codes,
+                                                       out_masks, anc ? *anc : AncIO());
   }
   ISX_LAUNCH_CHECK("k_scatter_cells");
   return ISX_OK;

@@ -36,6 +36,7 @@ from __future__ import annotations
 import numpy as np
 from scipy.special import erf
 
+from . import activations
 from .mlp import as_f64_layers
 
 SOUND, CLT, RAUA, RAFIXED = "sound", "clt", "raua", "rafixed"
@@ -88,8 +89,11 @@ def input_form(lo, hi, mode):
     return xc, X
 
 
-def propagate(layers, lo, hi, mode):
-    """Output centre (B,) and output coefficients (B, S) of every box, S = 3 + sum of hidden widths."""
+def propagate(layers, lo, hi, mode, act="relu"):
+    """Output centre (B,) and output coefficients (B, S) of every box, S = 3 + sum of hidden widths.
+    ELU and sine layers (``act``) take the least-squares rule of uncertainty propagation only."""
+    if act != "relu" and mode != CLT:
+        raise NotImplementedError("sound affine arithmetic is implemented for ReLU layers only")
     L = as_f64_layers(layers)
     c, X = input_form(lo, hi, mode)
     for l, (W, b) in enumerate(L):
@@ -99,7 +103,10 @@ def propagate(layers, lo, hi, mode):
             break
         if mode == CLT:
             sigma = np.sqrt(np.sum(X * X, axis=1))      # Eq. 7
-            alpha, beta, gamma = relu_least_squares(c, sigma)
+            if act == "relu":
+                alpha, beta, gamma = relu_least_squares(c, sigma)
+            else:
+                alpha, beta, gamma = activations.least_squares(act, c, sigma)
         else:
             r = np.sum(np.abs(X), axis=1)                # Eq. 2
             alpha, beta, gamma = relu_chebyshev(c - r, c + r)
@@ -140,7 +147,7 @@ def propagate_rafixed(layers, lo, hi):
     return c[:, 0], np.sum(np.abs(A[:, :, 0]), axis=1) + r[:, 0]
 
 
-def bound(layers, lo, hi, mode, batch=64):
+def bound(layers, lo, hi, mode, batch=64, act="relu"):
     """Centre and spread of every box: (x0, r) for SOUND and RAFIXED, (mu, sigma) for CLT and RAUA."""
     lo = np.asarray(lo).reshape(-1, 3)
     hi = np.asarray(hi).reshape(-1, 3)
@@ -153,7 +160,7 @@ def bound(layers, lo, hi, mode, batch=64):
         return centre, spread
     prop_mode = CLT if mode == CLT else SOUND
     for s in range(0, n, batch):
-        x0, coef = propagate(layers, lo[s:s + batch], hi[s:s + batch], prop_mode)
+        x0, coef = propagate(layers, lo[s:s + batch], hi[s:s + batch], prop_mode, act=act)
         centre[s:s + batch] = x0
         if mode == SOUND:
             spread[s:s + batch] = np.sum(np.abs(coef), axis=1)             # Eq. 2

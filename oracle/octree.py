@@ -44,7 +44,7 @@ def iso_bits(lower, upper, isos):
 
 
 def extract_active(layers, max_level, isos, mode, k=3.0, batch=64, start_level=0, start_cells=None,
-                   start_masks=None):
+                   start_masks=None, act="relu"):
     """Run the level loop.  Returns a list with one dict per level:
     ``ijk`` (n, 3) cells bounded at that level, ``mask_in`` their inherited iso sets, ``lower``,
     ``upper`` their bounds, ``mask`` the surviving sets.  The last level's surviving cells are the
@@ -62,7 +62,7 @@ def extract_active(layers, max_level, isos, mode, k=3.0, batch=64, start_level=0
     for level in range(start_level, max_level + 1):
         lo, hi = cell_box(ijk, level)
         if ijk.shape[0]:
-            centre, spread = affine.bound(layers, lo, hi, mode, batch=batch)
+            centre, spread = affine.bound(layers, lo, hi, mode, batch=batch, act=act)
         else:
             centre = spread = np.zeros(0)
         lower, upper = affine.interval(centre, spread, mode, k)

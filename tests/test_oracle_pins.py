@@ -429,3 +429,105 @@ def test_rafixed_bounds_contain_samples_and_linear_nets_are_exact(small):
         Weff = W @ Weff
     h = (hi.astype(np.float64) - lo.astype(np.float64)) / 2
     assert np.allclose(r, np.abs(Weff[0]) @ h.T, rtol=1e-10)
+
+
+# ---- ELU and sine activations: least-squares lines against Table VII and quadrature ------------
+
+from oracle import activations as acts  # noqa: E402
+from scipy.special import erf  # noqa: E402
+
+_GRID = [(mu, sg) for mu in (-4.0, -1.3, -0.2, 0.0, 0.4, 2.5) for sg in (0.05, 0.4, 1.0, 2.2)]
+
+
+def _table7_sine(mu, sg):
+    """Table VII, sine row, as printed."""
+    a = np.exp(-0.5 * sg ** 2)
+    alpha = a * np.cos(mu)
+    beta = a * (np.sin(mu) - mu * np.cos(mu))
+    g2 = -a ** 2 * (sg ** 2 * np.cos(mu) ** 2 + np.sin(mu) ** 2) + 0.5 * (1 - a ** 4 * np.cos(2 * mu))
+    return alpha, beta, g2
+
+
+def _table7_elu(mu, sg):
+    """Table VII, ELU row, as printed."""
+    a = erf(-mu / (np.sqrt(2) * sg))
+    b = (1 + erf((-mu - sg ** 2) / (np.sqrt(2) * sg))) * np.exp(mu + sg ** 2 / 2)
+    alpha = 0.5 * (1 - a + b)
+    c = np.exp(-mu ** 2 / (2 * sg ** 2)) / np.sqrt(2 * np.pi)
+    beta = 0.5 * b * (1 - mu) - 0.5 * (1 + a) + c * sg
+    g2 = (0.25 * (1 - a ** 2) * (mu ** 2 + sg ** 2) + (0.5 * a * b - c ** 2 - 0.25 * b ** 2 - 0.5 * b) * sg ** 2
+          + a * c * mu * sg + (a - b + 1) * c * sg + 0.5 * (a * b - b - a ** 2 + 1) * mu
+          + 0.25 * (1 + erf((-mu - 2 * sg ** 2) / (np.sqrt(2) * sg))) * np.exp(2 * mu + 2 * sg ** 2)
+          + 0.25 - 0.25 * (a - b) ** 2 - 0.5 * b)
+    return alpha, beta, g2
+
+
+@pytest.mark.parametrize("act", [acts.SINE, acts.ELU])
+def test_table7_sine_and_elu_rows(act):
+    """The moments-based fit equals Table VII's printed closed forms: alpha, beta and gamma^2 of the
+    sine row, alpha and beta of the ELU row.  The ELU row's gamma^2 as printed is negative over most
+    of the grid (e.g. -0.23 at mu = 0, sigma = 0.05), so it cannot be the residual variance; gamma^2
+    is taken from its definition and pinned by quadrature (test below)."""
+    table = _table7_sine if act == acts.SINE else _table7_elu
+    for mu, sg in _GRID:
+        al, be, ga = acts.least_squares(act, mu, sg)
+        ta, tb, tg2 = table(mu, sg)
+        scale = max(1.0, mu * mu + sg * sg)
+        assert abs(al - ta) <= 1e-12 * max(1, abs(ta)), (act, mu, sg)
+        assert abs(be - tb) <= 1e-12 * max(1, abs(tb)), (act, mu, sg)
+        if act == acts.SINE:
+            assert abs(ga ** 2 - max(tg2, 0.0)) <= 1e-12 * scale, (act, mu, sg, ga ** 2, tg2)
+    if act == acts.ELU:
+        assert _table7_elu(0.0, 0.05)[2] < -0.2 and acts.least_squares(acts.ELU, 0.0, 0.05)[2] > 0
+
+
+@pytest.mark.parametrize("act", [acts.RELU, acts.SINE, acts.ELU])
+def test_least_squares_fit_by_quadrature(act):
+    """Normal equations E[r] = E[r X] = 0 and gamma^2 = E[r^2] for the residual r = f(X) - alpha X - beta,
+    X ~ N(mu, sigma^2), by numerical integration; the ReLU row also equals affine.relu_least_squares."""
+    for mu, sg in _GRID:
+        al, be, ga = acts.least_squares(act, mu, sg)
+
+        def dens(x):
+            return np.exp(-0.5 * ((x - mu) / sg) ** 2) / (np.sqrt(2 * np.pi) * sg)
+
+        def r(x):
+            return float(acts.forward(act, x)) - al * x - be
+
+        lo, hi = mu - 12 * sg, mu + 12 * sg
+        pts = [0.0] if lo < 0 < hi else None
+        e0 = integrate.quad(lambda x: r(x) * dens(x), lo, hi, points=pts, limit=400, epsabs=1e-13)[0]
+        e1 = integrate.quad(lambda x: r(x) * (x - mu) * dens(x), lo, hi, points=pts, limit=400, epsabs=1e-13)[0]
+        e2 = integrate.quad(lambda x: r(x) ** 2 * dens(x), lo, hi, points=pts, limit=400, epsabs=1e-13)[0]
+        scale = max(1.0, abs(mu) + sg)
+        assert abs(e0) <= 1e-8 * scale and abs(e1) <= 1e-8 * scale * sg, (act, mu, sg, e0, e1)
+        assert abs(e2 - ga ** 2) <= 1e-8 * scale ** 2, (act, mu, sg, e2, ga ** 2)
+        if act == acts.RELU:
+            ra, rb, rg = affine.relu_least_squares(mu, sg)
+            assert abs(al - ra) <= 1e-12 and abs(be - rb) <= 1e-12 * scale
+            assert abs(ga ** 2 - rg ** 2) <= 1e-13 * scale ** 2
+
+
+@pytest.mark.parametrize("act", [acts.SINE, acts.ELU])
+def test_least_squares_small_sigma_is_the_tangent(act):
+    for mu in (-2.0, -0.5, 0.3, 1.7):
+        al, be, ga = acts.least_squares(act, mu, 1e-4)
+        t_al, t_be, t_ga = acts.least_squares(act, mu, 0.0)
+        assert abs(al - t_al) < 1e-7 and abs(be - t_be) < 1e-7 and t_ga == 0 and ga < 1e-7
+
+
+@pytest.mark.parametrize("act", [acts.SINE, acts.ELU])
+def test_up_mean_of_one_hidden_layer_equals_gaussian_input_expectation(act):
+    """With one hidden layer the propagated mean is b_out + sum_n w_n E f(z_n), z_n ~ N(mu_n,
+    sigma_n^2) from the Gaussian reading of the input box: it equals the Monte Carlo mean of the network
+    driven by x ~ N(x_c, diag(h^2 / 3)), whose pre-activations are exactly those Gaussians."""
+    layers = inr.random_inr([3, 24, 1], 19)
+    if act == acts.SINE:
+        layers = [(W * 6.0, b * 6.0) for W, b in layers[:1]] + layers[1:]
+    rng = np.random.default_rng(20)
+    lo, hi = np.array([[-0.4, 0.1, -0.3]]), np.array([[0.2, 0.5, 0.1]])
+    mu, _ = affine.bound(layers, lo, hi, affine.CLT, act=act)
+    xc, h = (lo + hi)[0] / 2, (hi - lo)[0] / 2
+    x = xc + rng.normal(size=(2_000_000, 3)) * h / np.sqrt(3)
+    v = mlp.mlp_forward(layers, x, act=act)
+    assert abs(mu[0] - v.mean()) <= 5 * v.std() / np.sqrt(x.shape[0])

@@ -66,15 +66,23 @@ typedef enum { ISX_BOUND_SOUND = 0, ISX_BOUND_CLT = 1, ISX_BOUND_RAUA = 2, ISX_B
  * centres, reductions and linearisations stay float32. */
 typedef enum { ISX_PREC_FP32 = 0, ISX_PREC_BF16 = 1 } isx_precision;
 
-/* A ReLU MLP: n_layers linear layers 3 -> w -> ... -> w -> 1 with ReLU after every layer but the
- * last (the ReLU INRs of App. E).  All hidden widths must be equal.  W[l] is row-major
- * [dims[l+1]][dims[l]] float32, b[l] has dims[l+1] entries; both are HOST pointers, copied by
- * isx_create_inr (the caller keeps ownership). */
+/* Activation applied after every linear layer but the last: ReLU (the ReLU INRs of App. E), ELU
+ * (x for x > 0, e^x - 1 otherwise; App. A, App. E) or sine (the SIREN INRs of Sec. V-A.2, with the
+ * frequency factor omega_0 folded into W and b by the caller, so the activation is sin z).
+ * ELU and sine networks are bounded by the uncertainty-propagation rule only (ISX_BOUND_CLT, with
+ * the ELU / sine rows of Table VII); the sound modes return ISX_ERR_UNSUPPORTED for them. */
+typedef enum { ISX_ACT_RELU = 0, ISX_ACT_ELU = 1, ISX_ACT_SINE = 2 } isx_activation;
+
+/* An MLP: n_layers linear layers 3 -> w -> ... -> w -> 1 with the activation after every layer but
+ * the last.  All hidden widths must be equal.  W[l] is row-major [dims[l+1]][dims[l]] float32, b[l]
+ * has dims[l+1] entries; both are HOST pointers, copied by isx_create_inr (the caller keeps
+ * ownership).  A zero-initialised `activation` is ReLU. */
 typedef struct {
   int n_layers;             /* 2 .. ISX_MAX_LAYERS                     */
   const int* dims;          /* n_layers + 1 entries, dims[0] = 3, dims[n_layers] = 1 */
   const float* const* W;
   const float* const* b;
+  int activation;           /* isx_activation                          */
 } isx_inr_desc;
 
 /* Copies the weights to the current device (float32, transposed and bfloat16 copies for the

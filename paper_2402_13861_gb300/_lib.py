@@ -20,6 +20,7 @@ ISX_MC_MAX_TRI = 5
 
 SOUND, CLT, RAUA, RAFIXED = 0, 1, 2, 3
 FP32, BF16 = 0, 1
+ACTS = {"relu": 0, "elu": 1, "sine": 2}
 MODES = {"sound": SOUND, "clt": CLT, "raua": RAUA, "rafixed": RAFIXED}
 PRECS = {"fp32": FP32, "bf16": BF16}
 
@@ -40,7 +41,8 @@ class KernelStats(C.Structure):
 
 class InrDesc(C.Structure):
     _fields_ = [("n_layers", C.c_int), ("dims", C.POINTER(C.c_int)),
-                ("W", C.POINTER(C.POINTER(C.c_float))), ("b", C.POINTER(C.POINTER(C.c_float)))]
+                ("W", C.POINTER(C.POINTER(C.c_float))), ("b", C.POINTER(C.POINTER(C.c_float))),
+                ("activation", C.c_int)]
 
 
 class TuneEntry(C.Structure):
@@ -177,8 +179,11 @@ def _ptr(t):
 class Inr:
     """An INR resident on the current CUDA device (wraps isx_inr)."""
 
-    def __init__(self, layers):
+    def __init__(self, layers, act="relu"):
+        """``layers``: (W, b) pairs, W of shape (out, in); ``act``: "relu", "elu" or "sine" (a SIREN's
+        omega_0 folded into W and b)."""
         lib = load()
+        self.act = act
         self.layers = [(np.ascontiguousarray(W, dtype=np.float32), np.ascontiguousarray(b, dtype=np.float32))
                        for W, b in layers]
         dims = [self.layers[0][0].shape[1]] + [W.shape[0] for W, _ in self.layers]
@@ -187,7 +192,7 @@ class Inr:
         c_dims = (C.c_int * (n + 1))(*dims)
         Wp = (C.POINTER(C.c_float) * n)(*[W.ctypes.data_as(C.POINTER(C.c_float)) for W, _ in self.layers])
         bp = (C.POINTER(C.c_float) * n)(*[b.ctypes.data_as(C.POINTER(C.c_float)) for _, b in self.layers])
-        desc = InrDesc(n, c_dims, Wp, bp)
+        desc = InrDesc(n, c_dims, Wp, bp, ACTS[act])
         h = C.c_void_p()
         _check(lib.isx_create_inr(C.byref(desc), C.byref(h)))
         self._h = h

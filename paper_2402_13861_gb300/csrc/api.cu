@@ -68,6 +68,10 @@ isx_status check_inr(isx_inr inr) {
 
 isx_status bound_dispatch(isx_inr inr, const CellSource& src, int64_t n, isx_bound_mode mode, isx_precision prec,
                           int inflate, float* center, float* spread, cudaStream_t st) {
+  if (inr->act != ISX_ACT_RELU && mode != ISX_BOUND_CLT) {
+    set_error("ELU and sine networks are bounded by uncertainty propagation (ISX_BOUND_CLT) only");
+    return ISX_ERR_UNSUPPORTED;
+  }
   if (mode == ISX_BOUND_RAFIXED) {
     if (prec != ISX_PREC_FP32) {
       set_error("RA-Fixed bounds are computed in float32 only");
@@ -243,6 +247,10 @@ isx_status isx_create_inr(const isx_inr_desc* d, isx_inr* out) {
     set_error("hidden width must be a multiple of 16 in [16, 512]");
     return ISX_ERR_UNSUPPORTED;
   }
+  if (d->activation < ISX_ACT_RELU || d->activation > ISX_ACT_SINE) {
+    set_error("unknown activation");
+    return ISX_ERR_ARG;
+  }
   for (int l = 0; l < L; ++l)
     if (!d->W[l] || !d->b[l]) {
       set_error("null weight pointer");
@@ -253,6 +261,7 @@ isx_status isx_create_inr(const isx_inr_desc* d, isx_inr* out) {
   inr->n_layers = L;
   inr->H = L - 1;
   inr->w = w;
+  inr->act = d->activation;
   inr->W.assign(L, nullptr);
   inr->Wt.assign(L, nullptr);
   inr->b.assign(L, nullptr);

@@ -57,6 +57,7 @@ struct CovArgs {
   float* center;
   float* spread;
   int* status;
+  int act;                             // isx_activation of the hidden layers
 };
 
 struct CovMaps {
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_bound_cov(const __grid_constan
         const float w0 = s.W0[3 * p], w1 = s.W0[3 * p + 1], w2 = s.W0[3 * p + 2];
         const float c1 = fmaf(w2, xc[2], fmaf(w1, xc[1], fmaf(w0, xc[0], args.b[0][p])));
         const float s2 = w0 * w0 * h23[0] + w1 * w1 * h23[1] + w2 * w2 * h23[2];
-        Lin L = relu_clt(c1, sqrtf(s2));
+        Lin L = act_clt(args.act, c1, sqrtf(s2));
         s.alpha[p] = L.alpha;
         s.beta[p] = L.beta;
         s.gamma[p] = L.gamma;
@@ -341,7 +342,7 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_bound_cov(const __grid_constan
         if (!gwait(&s.bar[CB_CENTER], center_n & 1)) { ok = false; break; }
         ++center_n;
         for (int p = ct; p < w; p += kCompThreads) {
-          Lin L = relu_clt(s.cn[p], sqrtf(s.sig2[p]));
+          Lin L = act_clt(args.act, s.cn[p], sqrtf(s.sig2[p]));
           s.alpha[p] = L.alpha;
           s.beta[p] = L.beta;
           s.gamma[p] = L.gamma;
@@ -494,6 +495,7 @@ isx_status bound_bf16_clt_cov(isx_inr inr, const CellSource& src, int64_t n, flo
   a.n = n;
   a.w = w;
   a.H = H;
+  a.act = inr->act;
   a.W0 = inr->W[0];
   for (int l = 0; l < inr->n_layers; ++l) {
     a.b[l] = inr->b[l];

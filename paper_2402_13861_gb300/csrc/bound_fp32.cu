@@ -67,12 +67,12 @@ __global__ void k_input_layer(CellSource src, int64_t first, int nc, const float
   }
 }
 
-// ReLU linearisation per (cell, neuron); updates the centre in place, writes alpha and gamma.
-__global__ void k_relu(int64_t total, int mode, int inflate, float* C, const float* RAD,
+// Activation linearisation per (cell, neuron); updates the centre in place, writes alpha and gamma.
+__global__ void k_relu(int64_t total, int mode, int inflate, int act, float* C, const float* RAD,
                        const float* DELTA, float* ALPHA, float* GAMMA) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= total) return;
-  Lin r = (mode == ISX_BOUND_CLT) ? relu_clt(C[i], RAD[i])
+  Lin r = (mode == ISX_BOUND_CLT) ? act_clt(act, C[i], RAD[i])
                                   : relu_sound(C[i], RAD[i], inflate ? DELTA[i] : 0.0f, inflate != 0);
   C[i] = r.center;
   ALPHA[i] = r.alpha;
@@ -333,7 +333,7 @@ isx_status bound_fp32(isx_inr inr, const CellSource& src, int64_t n, isx_bound_m
     for (int j = 1; j <= H - 1; ++j) {
       {
         prof::Scope _ps(K_RELU, st, 0, 0);
-        k_relu<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(tot, (int)mode, inflate, C, RAD, DE, AL, GA);
+        k_relu<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(tot, (int)mode, inflate, inr->act, C, RAD, DE, AL, GA);
       }
       ISX_LAUNCH_CHECK("k_relu");
       float kappa = 3.0f * kU + gamma_k(w);
@@ -376,7 +376,7 @@ isx_status bound_fp32(isx_inr inr, const CellSource& src, int64_t n, isx_bound_m
     }
     {
       prof::Scope _ps(K_RELU, st, 0, 0);
-      k_relu<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(tot, (int)mode, inflate, C, RAD, DE, AL, GA);
+      k_relu<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(tot, (int)mode, inflate, inr->act, C, RAD, DE, AL, GA);
     }
     ISX_LAUNCH_CHECK("k_relu");
     const int L = inr->n_layers - 1;

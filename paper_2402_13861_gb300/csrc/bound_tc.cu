@@ -81,6 +81,7 @@ struct TcNet {
   float bout;
   int H;
   int w;                               // cells of networks of another width are skipped
+  int act;                             // isx_activation of the hidden layers (CLT rule)
 };
 
 struct TcArgs {
@@ -726,7 +727,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
         float* ga = s.gamma + (j % 3) * W;
         // ---- ReLU j (Eq. 4 / Eq. 9) ----
         for (int nn = mt; nn < W; nn += kMathThreads) {
-          Lin L = clt ? relu_clt(s.c[nn], s.r[nn]) : relu_sound(s.c[nn], s.r[nn], s.delta[nn], infl);
+          Lin L = clt ? act_clt(N.act, s.c[nn], s.r[nn]) : relu_sound(s.c[nn], s.r[nn], s.delta[nn], infl);
           al[nn] = L.alpha;
           ga[nn] = L.gamma;
           s.a[nn] = L.center;
@@ -814,7 +815,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
       float* ga = s.gamma + (H % 3) * W;
       const float* wout = N.W[H];
       for (int nn = mt; nn < W; nn += kMathThreads) {
-        Lin L = clt ? relu_clt(s.c[nn], s.r[nn]) : relu_sound(s.c[nn], s.r[nn], s.delta[nn], infl);
+        Lin L = clt ? act_clt(N.act, s.c[nn], s.r[nn]) : relu_sound(s.c[nn], s.r[nn], s.delta[nn], infl);
         al[nn] = L.alpha;
         ga[nn] = L.gamma;
         s.a[nn] = L.center;
@@ -1032,6 +1033,7 @@ isx_status build_net(isx_inr inr, TcNet* h) {
   h->bout = inr->hb[inr->n_layers - 1][0];
   h->H = inr->H;
   h->w = inr->w;
+  h->act = inr->act;
   return ISX_OK;
 }
 

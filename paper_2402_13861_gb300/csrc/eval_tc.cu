@@ -9,14 +9,15 @@
 //
 // Layout: one CTA (one warpgroup, 128 threads) per 128-point tile, persistent over tiles.  Thread
 // t owns point t of the tile = TMEM lane t.  Layer 0 (3 -> w) runs in FP32 on the CUDA cores; its
-// ReLU output is split into A_hi, A_lo in shared memory (K-major, 128-byte swizzle).  Each hidden
-// layer W_l (w x w) streams through two 32 KB stages (X: W_hi chunk, Y: W_lo chunk; one 64-wide K
-// chunk each) loaded by TMA; thread 0 issues the MMAs into one w-column FP32 accumulator.  The
-// epilogue reads TMEM, adds the bias, applies ReLU and writes the next A_hi, A_lo; after the last
-// hidden layer it contracts with w_out in FP32 instead.  Every wait is bounded (2 s): on timeout
+// activation output is split into A_hi, A_lo in shared memory (K-major, 128-byte swizzle).  Each
+// hidden layer W_l (w x w) streams through two 32 KB stages (X: W_hi chunk, Y: W_lo chunk; one
+// 64-wide K chunk each) loaded by TMA; thread 0 issues the MMAs into one w-column FP32 accumulator.
+// The epilogue reads TMEM, adds the bias, applies the activation (ReLU, ELU or sine) and writes the
+// next A_hi, A_lo; after the last hidden layer it contracts with w_out in FP32 instead.  Every wait is bounded (2 s): on timeout
 // the kernel records ISX_ERR_TIMEOUT, lets copies land, frees TMEM and returns.
 #include "internal.cuh"
 #include "tc_ptx.cuh"
+#include "linearise.cuh"
 
 #include <algorithm>
 #include <cstring>
@@ -41,6 +42,7 @@ struct EvArgs {
   const float* b[ISX_MAX_LAYERS];              // biases of layers 0 .. H-1
   const float* wout;                           // [w]
   float bout;
+  int act;                             // isx_activation of the hidden layers
   int* status;
 };
 struct EvMaps {
@@ -78,7 +80,7 @@ __device__ __forceinline__ bool ewait(uint64_t* b, uint32_t parity, volatile int
   }
 }
 
-// relu(v) split into two BF16 terms, 8 consecutive columns, stored at A_hi / A_lo.
+// v (after the activation) split into two BF16 terms, 8 consecutive columns, stored at A_hi / A_lo.
 __device__ __forceinline__ void store_split8(uint8_t* Ahi, uint8_t* Alo, int row, int k, const float* v) {
   uint32_t ph[4], pl[4];
 #pragma unroll
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(kT, 1) k_eval_tc(const __grid_constant__ EvArg
       for (int i = 0; i < 8; ++i) {
         const int nn = k + i;
         const float z = fmaf(sW0[3 * nn + 2], x[2], fmaf(sW0[3 * nn + 1], x[1], fmaf(sW0[3 * nn], x[0], sb[nn])));
-        v[i] = fmaxf(z, 0.f);
+        v[i] = act_fwd(args.act, z);
       }
       store_split8(Ahi, Alo, t, k, v);
     }
@@ -234,7 +236,7 @@ __global__ void __launch_bounds__(kT, 1) k_eval_tc(const __grid_constant__ EvArg
           float v[32];
           tmem_ld32(trow + c0, v);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i] + bl[c0 + i], 0.f);
+          for (int i = 0; i < 32; ++i) v[i] = act_fwd(args.act, v[i] + bl[c0 + i]);
 #pragma unroll
           for (int u = 0; u < 4; ++u) store_split8(Ahi, Alo, t, c0 + 8 * u, v + 8 * u);
         }
@@ -245,7 +247,7 @@ __global__ void __launch_bounds__(kT, 1) k_eval_tc(const __grid_constant__ EvArg
           float v[32];
           tmem_ld32(trow + c0, v);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) y = fmaf(swo[c0 + i], fmaxf(v[i] + bl[c0 + i], 0.f), y);
+          for (int i = 0; i < 32; ++i) y = fmaf(swo[c0 + i], act_fwd(args.act, v[i] + bl[c0 + i]), y);
         }
         if (p < args.n) args.out[p] = y + args.bout;
       }
@@ -302,6 +304,7 @@ isx_status eval_points_tc(isx_inr inr, const float* xyz, const uint32_t* lattice
   for (int l = 0; l < H; ++l) a.b[l] = inr->b[l];
   a.wout = inr->W[H];
   a.bout = inr->hb[H][0];
+  a.act = inr->act;
   auto& ws = inr->ws;
   ISX_TRY(ws[WS_TC_STATUS].ensure(64, "tc status"));
   a.status = ws[WS_TC_STATUS].as<int>();

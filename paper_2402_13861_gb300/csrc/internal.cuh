@@ -65,6 +65,7 @@ struct isx_inr_s {
   int n_layers = 0;           // linear layers = H + 1
   int H = 0;                  // hidden (activation) layers
   int w = 0;                  // hidden width
+  int act = 0;                // isx_activation of the hidden layers
   // device copies, per linear layer l: W[l] row-major [out][in], Wt[l] = W[l]^T row-major [in][out]
   std::vector<float*> W, Wt, b;
   std::vector<__nv_bfloat16*> Wt_bf16;   // W[l]^T in bfloat16, for the tensor-core path

@@ -1,6 +1,7 @@
 // Corner queries and marching cubes in the predicted active cells (Sec. IV-D, last paragraph), the
 // float32 point evaluation of the MLP, and the library's own marching-cubes case table.
 #include "internal.cuh"
+#include "linearise.cuh"
 
 #include <algorithm>
 #include <cstring>
@@ -183,6 +184,7 @@ __device__ __forceinline__ void point_xyz(const float* xyz, const uint32_t* ids,
 struct MlpView {
   int n_layers;
   int w;
+  int act;                             // isx_activation of the hidden layers
   const float* W0;
   const float* b0;
   const float* Wt[ISX_MAX_LAYERS];
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(256) k_eval_fp32(MlpView m, const float* xyz, 
   for (int idx = threadIdx.x; idx < kEvalPts * w; idx += blockDim.x) {
     int p = idx / w, nn = idx % w;
     float z = fmaf(m.W0[3 * nn + 2], pts[p][2], fmaf(m.W0[3 * nn + 1], pts[p][1], fmaf(m.W0[3 * nn], pts[p][0], m.b0[nn])));
-    A[p * w + nn] = fmaxf(z, 0.0f);
+    A[p * w + nn] = act_fwd(m.act, z);
   }
   __syncthreads();
   for (int l = 1; l < m.n_layers - 1; ++l) {
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(256) k_eval_fp32(MlpView m, const float* xyz, 
         for (int p = 0; p < kEvalPts; ++p) acc[p] = fmaf(wk, A[p * w + k], acc[p]);
       }
 #pragma unroll
-      for (int p = 0; p < kEvalPts; ++p) B[p * w + nn] = fmaxf(acc[p], 0.0f);
+      for (int p = 0; p < kEvalPts; ++p) B[p * w + nn] = act_fwd(m.act, acc[p]);
     }
     __syncthreads();
     float* t = A; A = B; B = t;
@@ -252,6 +254,7 @@ isx_status eval_points_fp32(isx_inr inr, const float* xyz, const uint32_t* latti
   MlpView m{};
   m.n_layers = inr->n_layers;
   m.w = inr->w;
+  m.act = inr->act;
   m.W0 = inr->W[0];
   m.b0 = inr->b[0];
   for (int l = 1; l < inr->n_layers - 1; ++l) {

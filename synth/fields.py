@@ -110,3 +110,35 @@ def sphere_sdf(radius: float = 0.5):
         x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
         return np.linalg.norm(x, axis=1) - radius
     return f
+
+
+@dataclass
+class SdfField:
+    """Signed distance (negative inside) to the union of a torus in the z = 0 plane (major radius
+    ``R``, minor ``r``) and spheres ``(centre, radius)``: the min of the parts' distances, which is
+    an exact distance outside the union and a lower bound on the depth inside."""
+    R: float
+    r: float
+    spheres: list
+
+    def __call__(self, x: np.ndarray) -> np.ndarray:
+        x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+        q = np.sqrt(x[:, 0] ** 2 + x[:, 1] ** 2) - self.R
+        d = np.sqrt(q * q + x[:, 2] ** 2) - self.r
+        for c, rad in self.spheres:
+            d = np.minimum(d, np.linalg.norm(x - np.asarray(c), axis=1) - rad)
+        return d
+
+    def torch_eval(self, x):
+        import torch
+        q = torch.sqrt(x[:, 0] ** 2 + x[:, 1] ** 2) - self.R
+        d = torch.sqrt(q * q + x[:, 2] ** 2) - self.r
+        for c, rad in self.spheres:
+            d = torch.minimum(d, torch.linalg.norm(x - torch.tensor(c, dtype=x.dtype, device=x.device), dim=1) - rad)
+        return d
+
+
+def torus_and_spheres():
+    """The synthetic SDF of the mesh-extraction workload: a torus (R = 0.5, r = 0.18) with three
+    spheres (radii 0.22, 0.15, 0.12) placed on and off its ring."""
+    return SdfField(0.5, 0.18, [((0.5, 0.0, 0.0), 0.22), ((-0.25, 0.43, 0.1), 0.15), ((0.0, 0.0, 0.45), 0.12)])

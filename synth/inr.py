@@ -36,24 +36,46 @@ def he_init(dims, seed):
     return layers
 
 
-def _torch_forward(params, x):
+def siren_init(dims, seed, omega0=30.0):
+    """SIREN initialisation with the frequency factor folded in: a hidden layer computes sin(W x + b)
+    with W = omega0 W', W' uniform on +-1/fan_in (first layer) or +-sqrt(6/fan_in)/omega0 (others),
+    b = omega0 b', b' uniform on +-1/sqrt(fan_in); the output layer is linear (W' unscaled)."""
+    rng = np.random.default_rng(seed)
+    layers = []
+    n = len(dims) - 1
+    for l, (fan_in, fan_out) in enumerate(zip(dims[:-1], dims[1:])):
+        lim = 1.0 / fan_in if l == 0 else np.sqrt(6.0 / fan_in) / omega0
+        W = rng.uniform(-lim, lim, size=(fan_out, fan_in))
+        b = rng.uniform(-1.0, 1.0, size=fan_out) / np.sqrt(fan_in)
+        scale = omega0 if l < n - 1 else 1.0
+        layers.append(((W * scale).astype(np.float32), (b * scale).astype(np.float32)))
+    return layers
+
+
+def _torch_act(act):
     import torch
+    return {"relu": torch.relu, "elu": torch.nn.functional.elu, "sine": torch.sin}[act]
+
+
+def _torch_forward(params, x, act="relu"):
+    f = _torch_act(act)
     n = len(params) // 2
     a = x
     for l in range(n):
         a = a @ params[2 * l].T + params[2 * l + 1]
         if l < n - 1:
-            a = torch.relu(a)
+            a = f(a)
     return a[:, 0]
 
 
 def fit(dims, target, steps, lr=1e-3, batch=65536, init_seed=0, sample_seed=1, device=None,
-        log_every=0):
-    """Adam fit of a He-initialised ReLU MLP to ``target`` (a GaussianField) on uniform samples."""
+        log_every=0, act="relu"):
+    """Adam fit of an MLP to ``target`` (a field with ``torch_eval``) on uniform samples: He
+    initialisation for ReLU / ELU, SIREN initialisation (omega0 = 30, folded) for sine."""
     import torch
     if device is None:
         device = "cuda" if torch.cuda.is_available() else "cpu"
-    layers = he_init(dims, init_seed)
+    layers = siren_init(dims, init_seed) if act == "sine" else he_init(dims, init_seed)
     params = []
     for W, b in layers:
         params.append(torch.tensor(W, device=device, requires_grad=True))
@@ -65,7 +87,7 @@ def fit(dims, target, steps, lr=1e-3, batch=65536, init_seed=0, sample_seed=1, d
         x = torch.rand(batch, 3, generator=gen, device=device) * 2 - 1
         with torch.no_grad():
             y = target.torch_eval(x)
-        loss = torch.mean((_torch_forward(params, x) - y) ** 2)
+        loss = torch.mean((_torch_forward(params, x, act) - y) ** 2)
         opt.zero_grad(set_to_none=True)
         loss.backward()
         opt.step()
@@ -85,7 +107,7 @@ def lattice_centers(n):
     return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
 
 
-def quantile_isos(layers, n_iso, lo_q=0.10, hi_q=0.90, grid=128, device=None):
+def quantile_isos(layers, n_iso, lo_q=0.10, hi_q=0.90, grid=128, device=None, act="relu"):
     """``n_iso`` iso-values evenly spaced between the ``lo_q`` and ``hi_q`` quantiles of the fitted
     INR over the centres of a ``grid^3`` lattice (iso_q = q_lo + q (q_hi - q_lo) / (n_iso - 1))."""
     import torch
@@ -99,7 +121,7 @@ def quantile_isos(layers, n_iso, lo_q=0.10, hi_q=0.90, grid=128, device=None):
     with torch.no_grad():
         for s in range(0, x.shape[0], 1 << 18):
             xs = torch.tensor(x[s:s + (1 << 18)], dtype=torch.float32, device=device)
-            vals.append(_torch_forward(params, xs).cpu().numpy())
+            vals.append(_torch_forward(params, xs, act).cpu().numpy())
     v = np.concatenate(vals)
     ql, qh = np.quantile(v, [lo_q, hi_q])
     if n_iso == 1:
@@ -122,6 +144,7 @@ class Workload:
     k: float = 3.0
     lr: float = 1e-3
     batch: int = 65536
+    act: str = "relu"
 
 
 WORKLOADS = {
@@ -132,6 +155,13 @@ WORKLOADS = {
     # octree to 512^3, 8 iso-values over the 10-90 % quantiles.
     "scientific": Workload("scientific", [3] + [256] * 5 + [1], lambda: fields.anisotropic_blobs(2, 256),
                            5000, 2, 3, max_level=9, n_iso=8),
+    # SIREN 3->256 (3 hidden)->1 (sine, omega0 = 30 folded in) on the scientific field (seed 2),
+    # 3000 steps at lr 1e-4, octree to 512^3, 8 iso-values over the 10-90 % quantiles.
+    "siren": Workload("siren", [3] + [256] * 3 + [1], lambda: fields.anisotropic_blobs(2, 256), 3000, 12, 13,
+                      max_level=9, n_iso=8, lr=1e-4, act="sine"),
+    # ELU SDF 3->128 (4 hidden)->1 of a torus with three spheres, 3000 steps, octree to 512^3, iso 0.
+    "sdf_elu": Workload("sdf_elu", [3] + [128] * 4 + [1], fields.torus_and_spheres, 3000, 14, 15,
+                        max_level=9, fixed_isos=[0.0], act="elu"),
     # 3->512 (8 hidden)->1, 1024 anisotropic blobs (seed 5), octree to 1024^3.
     "large": Workload("large", [3] + [512] * 8 + [1], lambda: fields.anisotropic_blobs(5, 1024),
                       5000, 5, 6, max_level=10, n_iso=1),
@@ -153,11 +183,11 @@ def load_inr(name: str, device=None, verbose=False):
             return layers, z["isos"].astype(np.float32), wl
     t0 = time.time()
     layers, loss = fit(wl.dims, wl.field_fn(), wl.fit_steps, wl.lr, wl.batch, wl.init_seed,
-                       wl.sample_seed, device=device)
+                       wl.sample_seed, device=device, act=wl.act)
     if wl.fixed_isos:
         isos = np.array(wl.fixed_isos, dtype=np.float32)
     else:
-        isos = quantile_isos(layers, wl.n_iso, device=device)
+        isos = quantile_isos(layers, wl.n_iso, device=device, act=wl.act)
     if verbose:
         print(f"fitted {name} in {time.time() - t0:.1f}s, final loss {loss:.3e}", flush=True)
     save_inr(_cache_dir() / f"{name}.npz", layers, isos, loss)
@@ -176,6 +206,7 @@ def save_inr(path: Path, layers, isos, loss=float("nan")):
     os.replace(tmp, path)
 
 
-def random_inr(dims, seed):
-    """He-initialised (unfitted) ReLU MLP: a cheap network for shape and edge-case tests."""
-    return he_init(dims, seed)
+def random_inr(dims, seed, act="relu"):
+    """Unfitted MLP for shape and edge-case tests: He initialisation (ReLU, ELU) or the folded
+    SIREN initialisation (sine)."""
+    return siren_init(dims, seed) if act == "sine" else he_init(dims, seed)

@@ -56,11 +56,16 @@ def test_argument_errors_without_gpu(lib):
     dims = (C.c_int * 3)(3, 20, 1)
     desc = _lib.InrDesc(2, dims, W, W)
     assert lib.isx_create_inr(C.byref(desc), C.byref(h)) == 5
+    dims = (C.c_int * 3)(3, 64, 1)
+    desc = _lib.InrDesc(2, dims, W, W, 7)                  # no such activation
+    assert lib.isx_create_inr(C.byref(desc), C.byref(h)) == 1
+    assert b"activation" in lib.isx_last_error()
     assert lib.isx_version() == 100
 
 
 def test_struct_layouts_match_the_c_compiler(tmp_path):
-    """The ctypes mirrors of isx_extract_params and isx_mesh have the C compiler's sizes and offsets."""
+    """The ctypes mirrors of isx_extract_params, isx_mesh and isx_inr_desc have the C compiler's sizes
+    and offsets."""
     import shutil
     import subprocess
     if shutil.which("gcc") is None:
@@ -69,9 +74,12 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
     src = tmp_path / "layout.c"
     fields_p = [f for f, _ in _lib.ExtractParams._fields_]
     fields_m = [f for f, _ in _lib.Mesh._fields_]
+    fields_d = [f for f, _ in _lib.InrDesc._fields_]
     body = "\n".join([f'printf("P {f} %zu\\n", offsetof(isx_extract_params, {f}));' for f in fields_p] +
                      [f'printf("M {f} %zu\\n", offsetof(isx_mesh, {f}));' for f in fields_m] +
-                     ['printf("SP %zu\\nSM %zu\\n", sizeof(isx_extract_params), sizeof(isx_mesh));'])
+                     [f'printf("D {f} %zu\\n", offsetof(isx_inr_desc, {f}));' for f in fields_d] +
+                     ['printf("SP %zu\\nSM %zu\\nSD %zu\\n", sizeof(isx_extract_params), sizeof(isx_mesh), '
+                      'sizeof(isx_inr_desc));'])
     src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "isx.h"\nint main(void){' + body + 'return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
@@ -81,7 +89,10 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
         assert int(out[f"P {f}"]) == getattr(_lib.ExtractParams, f).offset, f
     for f in fields_m:
         assert int(out[f"M {f}"]) == getattr(_lib.Mesh, f).offset, f
+    for f in fields_d:
+        assert int(out[f"D {f}"]) == getattr(_lib.InrDesc, f).offset, f
     assert int(out["SP"]) == C.sizeof(_lib.ExtractParams) and int(out["SM"]) == C.sizeof(_lib.Mesh)
+    assert int(out["SD"]) == C.sizeof(_lib.InrDesc)
 
 
 def test_proposer_argument_errors_without_gpu(lib):

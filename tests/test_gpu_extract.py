@@ -67,9 +67,9 @@ def _corner_clean(vals, code, c, R):
     return np.all(np.abs(cv - c) > BAND)
 
 
-def _check_extraction(layers, isos, L, vals, res, mode, k):
+def _check_extraction(layers, isos, L, vals, res, mode, k, act="relu"):
     R = 1 << L
-    levels = octree.extract_active(layers, L, isos, mode, k=k, batch=512)
+    levels = octree.extract_active(layers, L, isos, mode, k=k, batch=512, act=act)
     o_cells, o_masks = octree.active_cells(levels)
     bands = band_codes(levels, isos, BAND, L)
     g_codes = to_np(res["codes"]).astype(np.int64) & 0xFFFFFFFF

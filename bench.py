@@ -227,6 +227,51 @@ def batched_form(pkg, mode, k):
             "cells_bounded_sequential": int(sum(sum(s["cells_bounded"]) for s in singles))}
 
 
+def activation_forms(pkg, k):
+    """The SIREN (sine, Table VII's sine row) and ELU-SDF workloads at 512^3: hierarchical CLT
+    extraction on the tensor cores against dense extraction (FP32 evaluation), the crossing
+    (cell, iso) pairs the hierarchy misses, and the fit that made each network."""
+    import torch
+    from synth import inr
+    from paper_2402_13861_gb300.train_proposer import missed
+    st = torch.cuda.current_stream()
+    out = {}
+    for name in ("siren", "sdf_elu"):
+        t0 = time.time()
+        layers, isos, wl = inr.load_inr(name, device="cuda")
+        fit_s = time.time() - t0
+        net = pkg.Inr(layers, act=wl.act)
+        L = wl.max_level
+        bufs = {}
+
+        def timed(**kw):
+            for rep in range(2):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(st)
+                r = net.extract(L, isos, buffers=bufs, active_cap=1 << 27, tri_cap=1 << 25, **kw)
+                b.record(st)
+                torch.cuda.synchronize()
+            return r, a.elapsed_time(b)
+
+        dense, ms_d = timed(prec="fp32", dense=True)
+        cell = dense["tri_cell"].to(torch.int64) & 0xFFFFFFFF
+        tiso = dense["tri_iso"].to(torch.int64)
+        key = torch.unique(cell)
+        masks = torch.zeros_like(key)
+        for q in range(len(isos)):
+            kq = torch.unique(cell[tiso == q])
+            if kq.numel():
+                masks[torch.searchsorted(key, kq)] |= 1 << q
+        h, ms_h = timed(mode="clt", k=k, prec="bf16")
+        m, tot = missed(h["codes"], h["masks"], (key, masks))
+        out[name] = {"activation": wl.act, "dims": wl.dims, "n_iso": int(len(isos)), "max_level": L,
+                     "fit_s": fit_s, "hier_clt_bf16_ms": ms_h, "cells_bounded": int(sum(h["cells_bounded"])),
+                     "n_active": h["n_active"], "n_tris": h["n_tris"], "dense_fp32_ms": ms_d,
+                     "dense_tris": dense["n_tris"], "missed_pairs": m, "missed_rate": m / max(tot, 1)}
+        net.close()
+    return out
+
+
 def cpu_baseline(layers, mode, k, budget_s=12.0):
     """Float64 oracle bounding random cells of levels 6-9 of the same workload for ~budget_s."""
     import numpy as np
@@ -408,6 +453,7 @@ def main():
         line["forms"] = extraction_forms(pkg, net, L, isos, res, ms_per_step, args.mode, args.k, prec)
         if prec == "bf16":
             line["forms"]["batched"] = batched_form(pkg, args.mode, args.k)
+            line["forms"]["activations"] = activation_forms(pkg, args.k)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(layers, args.mode, args.k)
     if rank == 0:

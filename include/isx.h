@@ -1,6 +1,6 @@
 /*
  * isx.h -- C interface of the GB300 (sm_103a) library for hierarchical iso-surface extraction on
- * ReLU-MLP implicit neural representations (Li & Shen, "Improving Efficiency of Iso-Surface
+ * MLP implicit neural representations (Li & Shen, "Improving Efficiency of Iso-Surface
  * Extraction on Implicit Neural Representations Using Uncertainty Propagation").
  *
  * Conventions for every entry point
@@ -153,8 +153,9 @@ typedef struct {
   isx_precision eval_prec;
   /* 0: octree (every level splits all three axes; the default). 1: the k-d tree of Algorithm 1: every
      depth bisects the widest side (x, then y, then z on ties), depths 0 .. 3 max_level, so every third
-     depth and the leaves are cubes; bound_stop_level counts octree levels (depth 3 x level). Not
-     combined with the proposer. */
+     depth and the leaves are cubes; bound_stop_level counts octree levels (depth 3 x level).
+     cells_visited / bounded / kept of depth d are added to octree level (d + 2) / 3.  With a
+     proposer: ISX_ERR_UNSUPPORTED. */
   int kd_tree;
 } isx_extract_params;
 

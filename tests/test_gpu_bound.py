@@ -142,3 +142,23 @@ def test_fp32_gemm_autotuner_picks_a_shape_and_keeps_results(pkg):
     s = s2.cpu().numpy()[:50].astype(np.float64)
     assert np.all(np.abs(s - os_) <= 1e-4 * os_ + 1e-7)
     net.close()
+
+
+@pytest.mark.parametrize("mode", ["sound", "clt"])
+def test_fp32_bounds_large_network_shape(pkg, mode):
+    """The large configuration's network shape (3 -> 512 x 8 -> 1: up to 4099 noise symbols per
+    neuron) on the float32 path against the oracle, a few boxes from level 2 to level 10 size."""
+    dims = [3] + [512] * 8 + [1]
+    layers = inr.random_inr(dims, 77)
+    rng = np.random.default_rng(78)
+    layers = [(W, rng.normal(0, 0.05, size=b.shape).astype(np.float32)) for W, b in layers]
+    net = pkg.Inr(layers)
+    lo, hi = boxes.random_boxes(9, 79, -10, -2)
+    c, s = _gpu_bounds(net, lo, hi, mode)
+    oc, os_ = affine.bound(layers, lo, hi, mode, batch=3)
+    H, w = len(dims) - 2, dims[1]
+    tol = 8 * H * w * 2.0 ** -24 * (np.abs(oc) + os_) + 1e-7
+    print(f"large {mode}: max |dc| / tol {np.max(np.abs(c - oc) / tol):.3f}, max |ds| / tol "
+          f"{np.max(np.abs(s - os_) / tol):.3f}")
+    assert np.all(np.abs(c - oc) <= tol) and np.all(np.abs(s - os_) <= tol)
+    net.close()

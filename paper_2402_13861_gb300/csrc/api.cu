@@ -2,6 +2,8 @@
 // loop of Algorithm 1 followed by corner queries and marching cubes.
 #include "internal.cuh"
 
+#include <cstdlib>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -79,7 +81,13 @@ isx_status bound_dispatch(isx_inr inr, const CellSource& src, int64_t n, isx_bou
     }
     return bound_rafixed(inr, src, n, inflate, center, spread, st);
   }
-  if (prec == ISX_PREC_BF16) return bound_bf16(inr, src, n, mode, inflate, center, spread, st);
+  if (prec == ISX_PREC_BF16) {
+    // the row-batched tensor-core path where it applies (ISX_BF16_ROWS=0 selects the per-cell kernel)
+    const char* e = std::getenv("ISX_BF16_ROWS");
+    if (rows_supported(inr, mode, inflate) && !(e && e[0] == '0'))
+      return bound_bf16_rows(inr, src, n, mode, center, spread, st);
+    return bound_bf16(inr, src, n, mode, inflate, center, spread, st);
+  }
   return bound_fp32(inr, src, n, mode, inflate, center, spread, st);
 }
 

@@ -1,0 +1,792 @@
+// Row-batched tensor-core bounds: the layer loop of Sec. III-B / IV-C run layer-synchronously over a
+// chunk of cells, with the noise-symbol rows of all cells of the chunk in one matrix per layer.
+//
+// Per cell the pre-activation z_j carries a centre c (w floats), the three input-symbol rows I
+// (3 x w, float32) and the rows of the symbols created by earlier activations
+// (bfloat16, "G rows").  Through activation j and linear layer j (Eq. 4 / 9, then Eq. 3 / 8):
+//   a = alpha c + beta,  c' = W_j a + b_j,  I' = (I diag(alpha)) W_j^T   (tensor cores, two-term bf16)
+//   G' = (G diag(alpha)) W_j^T                                          (one tcgen05 GEMM, all cells)
+//   new rows gamma_n W_j[:, n] for every neuron with gamma_n != 0       (appended after the cell's G')
+// A symbol whose coefficient gamma_n is exactly 0 (a neuron whose interval or Gaussian lies on
+// one side of the kink) has an all-zero row in every later layer, so it is never created: the
+// result is the full propagation's up to the order of the reductions.  At the finest levels of the
+// scientific workload only 6-20 % of the neurons per layer create a symbol.
+//
+// alpha is applied to the A operand (the rows) while it is staged into shared memory, so the B
+// operand is W_j itself, loaded once per CTA and shared by the rows of every cell: rows of many
+// cells fill each 128-row MMA tile.  After the GEMM a reduction pass forms r = sum |x| (sound) or
+// sigma^2 = sum x^2 (UP) per (cell, neuron) from the stored rows and the input rows, and the
+// activation pass linearises.  The output layer is a per-cell dot product of every row with
+// alpha_H * w_out.
+#include "internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <cuda_bf16.h>
+
+#include "cell_box.cuh"
+#include "compact.cuh"
+#include "linearise.cuh"
+#include "tc_ptx.cuh"
+
+namespace isx {
+namespace {
+
+using namespace tc;
+
+constexpr int kRT = 128;                        // rows per MMA tile
+constexpr int kGT = 256;                        // threads of the row GEMM: two per row
+constexpr int kMaxW = 512;                      // largest hidden width of an INR
+constexpr uint64_t kRowsWaitNs = 2000000000ull;
+enum { RB_WFULL, RB_MMA, RB_COUNT };
+
+struct RowsGemmArgs {
+  const __nv_bfloat16* xin;                     // [R][W] rows of z_j
+  const int* rowcell;                           // [R] cell of every row
+  const int64_t* off_in;                        // [nc] first row of each cell in xin
+  const int64_t* off_out;                       // [nc] first row of each cell in xout
+  const float* alpha;                           // [nc][W]
+  int64_t R;
+  __nv_bfloat16* xout;                          // [R'][W] rows of z_{j+1}
+  int* status;
+};
+
+template <int W>
+struct RowsSmem {
+  static constexpr int KC = W / 64;
+  static constexpr size_t kWB = (size_t)W * W * 2;         // W_j, KC chunks of [W rows][128 B]
+  static constexpr size_t kAB = (size_t)kRT * W * 2;       // one A tile, KC chunks of [128 rows][128 B]
+  static constexpr size_t bytes() { return 1024 + kWB + kAB + RB_COUNT * 8 + 16; }
+};
+
+__device__ __forceinline__ uint32_t roff(int row, int k) {  // byte offset of (row, k..k+7) in an A tile
+  return (uint32_t)((k >> 6) * kRT * 128 + row * 128 + ((((k & 63) >> 3) ^ (row & 7)) << 4));
+}
+
+__device__ __forceinline__ bool rwait(uint64_t* b, uint32_t parity, volatile int* abort, int* status) {
+  if (mbar_try(b, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try(b, parity)) return true;
+    if ((it & 3) == 0) {
+      if (*abort) return false;
+      if (global_ns() - t0 > kRowsWaitNs) {
+        *abort = 1;
+        atomicExch(status, (int)ISX_ERR_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+// G' = (G diag(alpha_cell)) W^T for all rows: persistent CTAs over 128-row tiles.  W (bf16,
+// [out][in] = N x K, K-major) is loaded once by TMA; two threads stage each row of the A tile (one
+// K half each), scaled by its cell's alpha, into the 128-byte-swizzled K-major layout.  The
+// epilogue splits the columns the same way (warp w reads TMEM lanes 32 (w mod 4) onwards, column
+// half w / 4).  The accumulators are
+// double-buffered in TMEM so that the epilogue of tile k-1 (TMEM -> bf16 rows in global memory)
+// overlaps the MMAs of tile k.  Every wait is bounded (2 s): on timeout the kernel records
+// ISX_ERR_TIMEOUT, lets the MMAs in flight finish, frees TMEM and returns.
+template <int W>
+__global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ RowsGemmArgs args,
+                                                       const __grid_constant__ CUtensorMap wmap) {
+  using S = RowsSmem<W>;
+  constexpr int KC = S::KC;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* Wsm = base;
+  uint8_t* Asm = Wsm + S::kWB;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Asm + S::kAB);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + RB_COUNT);
+  volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
+  const int t = threadIdx.x, warp = t >> 5;
+  const int64_t ntiles = (args.R + kRT - 1) / kRT;
+
+  if (t == 0) {
+    for (int i = 0; i < RB_COUNT; ++i) mbar_init(&bar[i], 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                 "n"(2 * W)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t id = idesc(W);
+  if (t == 0) {
+    mbar_expect_tx(&bar[RB_WFULL], (uint32_t)S::kWB);
+    for (int c = 0; c < KC; ++c) tma_load_2d(Wsm + (size_t)c * W * 128, &wmap, &bar[RB_WFULL], c * 64, 0);
+  }
+  bool ok = true;
+  int64_t prev = -1;
+  uint32_t k = 0;
+
+  const int row = t & (kRT - 1), half = t >> 7;
+  // every thread of a warp runs the (warp-collective) TMEM loads; rows past R are not stored
+  auto epilogue = [&](int64_t tile, uint32_t buf) {
+    const int64_t r = tile * kRT + row;
+    const uint32_t trow = tmem + buf * W + ((uint32_t)(32 * (warp & 3)) << 16);
+    const bool valid = r < args.R;
+    __nv_bfloat16* dst = nullptr;
+    if (valid) {
+      const int cell = args.rowcell[r];
+      dst = args.xout + (args.off_out[cell] + (r - args.off_in[cell])) * W;
+    }
+#pragma unroll 1
+    for (int c0 = half * (W / 2); c0 < (half + 1) * (W / 2); c0 += 32) {
+      float v[32];
+      tmem_ld32(trow + c0, v);
+      if (valid) {
+        uint32_t pk[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+          pk[i] = *reinterpret_cast<const uint32_t*>(&h);
+        }
+        uint4* d4 = reinterpret_cast<uint4*>(dst + c0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) d4[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+      }
+    }
+  };
+
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+    // the MMAs of the previous tile have read the A tile (and filled TMEM buffer (k-1) & 1)
+    if (k > 0) {
+      if (!rwait(&bar[RB_MMA], (k - 1) & 1, abort, args.status)) ok = false;
+    }
+    if (__syncthreads_or(!ok || *abort)) {
+      ok = false;
+      break;
+    }
+    tc_fence_after();
+    // ---- stage row r of the tile (this thread's K half), scaled by alpha of its cell ----
+    {
+      const int64_t r = tile * kRT + row;
+      if (r < args.R) {
+        const int cell = args.rowcell[r];
+        const uint4* src = reinterpret_cast<const uint4*>(args.xin + r * W);
+        const float4* al = reinterpret_cast<const float4*>(args.alpha + (size_t)cell * W);
+#pragma unroll 4
+        for (int g = half * (W / 16); g < (half + 1) * (W / 16); ++g) {
+          const uint4 x = src[g];
+          const float4 a0 = al[2 * g], a1 = al[2 * g + 1];
+          const __nv_bfloat162* xb = reinterpret_cast<const __nv_bfloat162*>(&x);
+          const float2 x0 = __bfloat1622float2(xb[0]), x1 = __bfloat1622float2(xb[1]);
+          const float2 x2 = __bfloat1622float2(xb[2]), x3 = __bfloat1622float2(xb[3]);
+          const __nv_bfloat162 p0 = __floats2bfloat162_rn(x0.x * a0.x, x0.y * a0.y);
+          const __nv_bfloat162 p1 = __floats2bfloat162_rn(x1.x * a0.z, x1.y * a0.w);
+          const __nv_bfloat162 p2 = __floats2bfloat162_rn(x2.x * a1.x, x2.y * a1.y);
+          const __nv_bfloat162 p3 = __floats2bfloat162_rn(x3.x * a1.z, x3.y * a1.w);
+          *reinterpret_cast<uint4*>(Asm + roff(row, 8 * g)) =
+              make_uint4(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1),
+                         *reinterpret_cast<const uint32_t*>(&p2), *reinterpret_cast<const uint32_t*>(&p3));
+        }
+      } else {
+        for (int g = half * (W / 16); g < (half + 1) * (W / 16); ++g)
+          *reinterpret_cast<uint4*>(Asm + roff(row, 8 * g)) = make_uint4(0, 0, 0, 0);
+      }
+    }
+    fence_async_shared();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    // ---- thread 0: the MMAs of this tile into TMEM buffer k & 1 ----
+    if (t == 0) {
+      bool wready = true;
+      if (k == 0) wready = rwait(&bar[RB_WFULL], 0, abort, args.status);
+      if (wready) {
+        const uint32_t dt = tmem + (k & 1) * W;
+        const uint32_t a0 = su32(Asm), w0 = su32(Wsm);
+#pragma unroll
+        for (int c = 0; c < KC; ++c)
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            mma_bf16(dt, sdesc(a0 + c * kRT * 128 + kk * 32), sdesc(w0 + c * W * 128 + kk * 32), id,
+                     (c > 0 || kk > 0) ? 1u : 0u);
+        mma_commit(&bar[RB_MMA]);
+      }
+    }
+    // ---- epilogue of the previous tile (its MMAs completed before this tile's A was staged) ----
+    if (prev >= 0) epilogue(prev, (k - 1) & 1);
+    tc_fence_before();
+    prev = tile;
+  }
+  if (ok && prev >= 0) {
+    if (!rwait(&bar[RB_MMA], (k - 1) & 1, abort, args.status)) ok = false;
+    if (!__syncthreads_or(!ok || *abort)) {
+      tc_fence_after();
+      epilogue(prev, (k - 1) & 1);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (*abort)
+    for (int i = 0; i < 1000; ++i) __nanosleep(1000);
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(2 * W) : "memory");
+  }
+}
+
+// ---- layer 0: centre c_1, the three input rows I_1 = diag(h) W_0^T, and their reduction ----
+__global__ void k_rows_input(CellSource src, int64_t first, int w, int clt, const float* __restrict__ W0,
+                             const float* __restrict__ b0, float* C, float* I, float* RAD) {
+  const int cell = blockIdx.x;
+  float xc[3], h[3];
+  cell_box(src, first + cell, 0, xc, h);
+  if (clt)
+    for (int d = 0; d < 3; ++d) h[d] *= 0.57735026918962576f;   // uniform on [-h, h] has std h / sqrt 3
+  for (int n = threadIdx.x; n < w; n += blockDim.x) {
+    const float w0 = W0[3 * n], w1 = W0[3 * n + 1], w2 = W0[3 * n + 2];
+    const float c = fmaf(w2, xc[2], fmaf(w1, xc[1], fmaf(w0, xc[0], b0[n])));
+    const float i0 = h[0] * w0, i1 = h[1] * w1, i2 = h[2] * w2;
+    const size_t o = (size_t)cell * w + n;
+    C[o] = c;
+    I[(size_t)cell * 3 * w + n] = i0;
+    I[(size_t)cell * 3 * w + w + n] = i1;
+    I[(size_t)cell * 3 * w + 2 * w + n] = i2;
+    RAD[o] = clt ? sqrtf(i0 * i0 + i1 * i1 + i2 * i2) : fabsf(i0) + fabsf(i1) + fabsf(i2);
+  }
+}
+
+// ---- activation j: alpha, gamma, post-activation centre a; new-symbol count per cell ----
+__global__ void k_rows_act(int w, int mode, int act, const float* C, const float* RAD, float* A, float* AL,
+                           float* GA, const int* cnt_in, int* cnt_out) {
+  __shared__ int wsum[32];
+  const int cell = blockIdx.x;
+  int m = 0;
+  for (int n = threadIdx.x; n < w; n += blockDim.x) {
+    const size_t o = (size_t)cell * w + n;
+    const Lin L = (mode == ISX_BOUND_CLT) ? act_clt(act, C[o], RAD[o]) : relu_sound(C[o], RAD[o], 0.0f, false);
+    A[o] = L.center;
+    AL[o] = L.alpha;
+    GA[o] = L.gamma;
+    m += (L.gamma != 0.0f);
+  }
+  if (!cnt_out) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+  if (lane == 0) wsum[warp] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tot = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += wsum[i];
+    cnt_out[cell] = cnt_in[cell] + tot;
+  }
+}
+
+// Exclusive scan of the per-cell row counts into int64 row offsets; total to *d_total.
+__global__ void k_rows_scan(const int* cnt, int64_t nc, int64_t* off, int64_t* d_total) {
+  compact::scan_block_counts_dev(cnt, nc, off, d_total, 1);
+}
+
+// ---- new rows gamma_n W_j[:, n] (row n of W_j^T) after each cell's transformed rows, in
+//      increasing n; the row -> cell map of the whole output ----
+__global__ void k_rows_new(int w, const float* __restrict__ GA, const float* __restrict__ Wt, const int* cnt_in,
+                           const int64_t* off_out, const int* cnt_out, __nv_bfloat16* xout, int* rowcell_out) {
+  __shared__ int list[kMaxW];
+  __shared__ int wcount[32];
+  __shared__ int nlist;
+  const int cell = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+  const int64_t o0 = off_out[cell];
+  for (int64_t r = o0 + t; r < o0 + cnt_out[cell]; r += blockDim.x) rowcell_out[r] = cell;
+  if (t == 0) nlist = 0;
+  __syncthreads();
+  for (int n0 = 0; n0 < w; n0 += blockDim.x) {
+    const int n = n0 + t;
+    const bool f = n < w && GA[(size_t)cell * w + n] != 0.0f;
+    const unsigned b = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) wcount[warp] = __popc(b);
+    __syncthreads();
+    int before = nlist;
+    for (int i = 0; i < warp; ++i) before += wcount[i];
+    if (f) list[before + __popc(b & ((1u << lane) - 1u))] = n;
+    __syncthreads();
+    if (t == 0)
+      for (int i = 0; i < nw; ++i) nlist += wcount[i];
+    __syncthreads();
+  }
+  // 8 columns (one 16-byte store) per thread: w / 8 threads per row, blockDim / (w / 8) rows per pass
+  const int64_t base = o0 + cnt_in[cell];
+  const int tpr = w / 8, rpp = blockDim.x / tpr;
+  const int sub = t / tpr, m8 = (t - sub * tpr) * 8;
+  if (sub < rpp)
+    for (int i = sub; i < nlist; i += rpp) {
+      const int n = list[i];
+      const float g = GA[(size_t)cell * w + n];
+      const float4* src = reinterpret_cast<const float4*>(Wt + (size_t)n * w + m8);
+      const float4 a = src[0], b = src[1];
+      const __nv_bfloat162 p0 = __floats2bfloat162_rn(g * a.x, g * a.y), p1 = __floats2bfloat162_rn(g * a.z, g * a.w);
+      const __nv_bfloat162 p2 = __floats2bfloat162_rn(g * b.x, g * b.y), p3 = __floats2bfloat162_rn(g * b.z, g * b.w);
+      *reinterpret_cast<uint4*>(xout + (base + i) * w + m8) =
+          make_uint4(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1),
+                     *reinterpret_cast<const uint32_t*>(&p2), *reinterpret_cast<const uint32_t*>(&p3));
+    }
+}
+
+// ---- centre and input rows of z_{j+1}: c' = W a + b, I'_d = (I_d diag(alpha)) W^T, at float32-class
+//      accuracy on the tensor cores: every operand x is carried as x_hi + x_lo (two bf16 terms) and
+//      the product as a_hi w_hi + a_lo w_hi + a_hi w_lo (the dropped a_lo w_lo is below 2^-16 of
+//      it), accumulated in float32 in TMEM.  Row r of a 128-row tile is quantity r & 3 (0: a,
+//      1-3: alpha I_d) of cell r >> 2.  W_hi and W_lo stream through two 64-wide K-chunk stages. ----
+enum { SB_XFULL, SB_XEMPTY, SB_YFULL, SB_YEMPTY, SB_DONE, SB_COUNT };
+
+struct RowsSplitArgs {
+  int64_t nc;
+  const float* A;                               // [nc][W] post-activation centre
+  const float* AL;                              // [nc][W]
+  const float* Iin;                             // [nc][3][W]
+  const float* bias;                            // [W]
+  float* Cout;                                  // [nc][W]
+  float* Iout;                                  // [nc][3][W]
+  int* status;
+};
+
+template <int W>
+struct SplitSmem {
+  static constexpr int KC = W / 64;
+  static constexpr size_t kA = (size_t)kRT * W * 2;        // one bf16 term of the A tile
+  static constexpr size_t kS = (size_t)W * 128;            // one weight stage (64-wide K chunk)
+  static constexpr size_t bytes() { return 1024 + 2 * kA + 2 * kS + SB_COUNT * 8 + 16; }
+};
+
+// 8 consecutive columns of row `row`, split into bf16 high and low terms
+__device__ __forceinline__ void split_store8(uint8_t* Ahi, uint8_t* Alo, int row, int k, const float* v) {
+  uint32_t ph[4], pl[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
+    ph[i] = *reinterpret_cast<const uint32_t*>(&h);
+    pl[i] = *reinterpret_cast<const uint32_t*>(&l);
+  }
+  const uint32_t o = roff(row, k);
+  *reinterpret_cast<uint4*>(Ahi + o) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+  *reinterpret_cast<uint4*>(Alo + o) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kRT, 1) k_rows_split(const __grid_constant__ RowsSplitArgs args,
+                                                        const __grid_constant__ CUtensorMap whi,
+                                                        const __grid_constant__ CUtensorMap wlo) {
+  using S = SplitSmem<W>;
+  constexpr int KC = S::KC;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* Ahi = base;
+  uint8_t* Alo = Ahi + S::kA;
+  uint8_t* X = Alo + S::kA;
+  uint8_t* Y = X + S::kS;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Y + S::kS);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + SB_COUNT);
+  volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
+  const int t = threadIdx.x, warp = t >> 5;
+  const int64_t ntiles = (4 * args.nc + kRT - 1) / kRT;
+  if (t == 0) {
+    for (int i = 0; i < SB_COUNT; ++i) mbar_init(&bar[i], 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "n"(W)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t id = idesc(W);
+  uint32_t xf = 0, xe = 0, yf = 0, ye = 0, dn = 0;
+  auto load_x = [&](int c) {
+    mbar_expect_tx(&bar[SB_XFULL], (uint32_t)S::kS);
+    tma_load_2d(X, &whi, &bar[SB_XFULL], c * 64, 0);
+  };
+  auto load_y = [&](int c) {
+    mbar_expect_tx(&bar[SB_YFULL], (uint32_t)S::kS);
+    tma_load_2d(Y, &wlo, &bar[SB_YFULL], c * 64, 0);
+  };
+  if (t == 0 && blockIdx.x < ntiles) {
+    load_x(0);
+    load_y(0);
+  }
+  bool ok = true;
+  for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const int64_t r = tile * kRT + t;
+    const int64_t cell = r >> 2;
+    const int q = (int)(r & 3);
+    const bool valid = cell < args.nc;
+    for (int k = 0; k < W; k += 8) {
+      float v[8];
+      if (valid) {
+        if (q == 0) {
+          const float4* s4 = reinterpret_cast<const float4*>(args.A + cell * W + k);
+          const float4 a0 = s4[0], a1 = s4[1];
+          v[0] = a0.x; v[1] = a0.y; v[2] = a0.z; v[3] = a0.w; v[4] = a1.x; v[5] = a1.y; v[6] = a1.z; v[7] = a1.w;
+        } else {
+          const float4* s4 = reinterpret_cast<const float4*>(args.Iin + (cell * 3 + q - 1) * W + k);
+          const float4* l4 = reinterpret_cast<const float4*>(args.AL + cell * W + k);
+          const float4 a0 = s4[0], a1 = s4[1], l0 = l4[0], l1 = l4[1];
+          v[0] = a0.x * l0.x; v[1] = a0.y * l0.y; v[2] = a0.z * l0.z; v[3] = a0.w * l0.w;
+          v[4] = a1.x * l1.x; v[5] = a1.y * l1.y; v[6] = a1.z * l1.z; v[7] = a1.w * l1.w;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = 0.0f;
+      }
+      split_store8(Ahi, Alo, t, k, v);
+    }
+    fence_async_shared();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (t == 0) {
+      for (int c = 0; c < KC && ok; ++c) {
+        if (!rwait(&bar[SB_XFULL], xf & 1, abort, args.status)) { ok = false; break; }
+        ++xf;
+        tc_fence_after();
+        const uint32_t ah = su32(Ahi + (size_t)c * kRT * 128), al = su32(Alo + (size_t)c * kRT * 128);
+        const uint32_t bx = su32(X), by = su32(Y);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          mma_bf16(tmem, sdesc(ah + kk * 32), sdesc(bx + kk * 32), id, (c > 0 || kk > 0) ? 1u : 0u);
+          mma_bf16(tmem, sdesc(al + kk * 32), sdesc(bx + kk * 32), id, 1u);
+        }
+        mma_commit(&bar[SB_XEMPTY]);
+        if (!rwait(&bar[SB_YFULL], yf & 1, abort, args.status)) { ok = false; break; }
+        ++yf;
+        tc_fence_after();
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) mma_bf16(tmem, sdesc(ah + kk * 32), sdesc(by + kk * 32), id, 1u);
+        mma_commit(&bar[SB_YEMPTY]);
+        // refill: the next chunk of this tile, else chunk 0 of this CTA's next tile
+        const int nxt = (c + 1 < KC) ? c + 1 : ((tile + gridDim.x < ntiles) ? 0 : -1);
+        if (!rwait(&bar[SB_XEMPTY], xe & 1, abort, args.status)) { ok = false; break; }
+        ++xe;
+        if (nxt >= 0) load_x(nxt);
+        if (!rwait(&bar[SB_YEMPTY], ye & 1, abort, args.status)) { ok = false; break; }
+        ++ye;
+        if (nxt >= 0) load_y(nxt);
+      }
+      if (ok) mma_commit(&bar[SB_DONE]);
+    }
+    if (!rwait(&bar[SB_DONE], dn & 1, abort, args.status)) ok = false;
+    ++dn;
+    if (__syncthreads_or(!ok || *abort)) {
+      ok = false;
+      break;
+    }
+    tc_fence_after();
+    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+    float* dst = nullptr;
+    if (valid) dst = (q == 0) ? args.Cout + cell * W : args.Iout + (cell * 3 + q - 1) * W;
+    for (int c0 = 0; c0 < W; c0 += 32) {
+      float v[32];
+      tmem_ld32(trow + c0, v);
+      if (valid) {
+        if (q == 0)
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] += args.bias[c0 + i];
+        float4* d4 = reinterpret_cast<float4*>(dst + c0);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
+  __syncthreads();
+  if (*abort)
+    for (int i = 0; i < 1000; ++i) __nanosleep(1000);
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(W) : "memory");
+  }
+}
+
+// ---- reductions of z_{j+1} per (cell, neuron): r = sum |x| or sigma = sqrt(sum x^2) over the
+//      cell's G rows and its three input rows (compensated); two neurons per thread ----
+__global__ void k_rows_reduce(int w, int sq, const __nv_bfloat16* X, const int64_t* off, const int* cnt,
+                              const float* I, float* RAD) {
+  const int cell = blockIdx.x;
+  const int64_t o0 = off[cell];
+  const int rows = cnt[cell];
+  for (int n2 = threadIdx.x; n2 < w / 2; n2 += blockDim.x) {
+    float s0 = 0.0f, s1 = 0.0f, e0 = 0.0f, e1 = 0.0f;
+    auto add = [&](float& s, float& e, float x) {
+      const float v = sq ? x * x : fabsf(x);
+      const float y = v - e, tt = s + y;
+      e = (tt - s) - y;
+      s = tt;
+    };
+    for (int d = 0; d < 3; ++d) {
+      add(s0, e0, I[(size_t)cell * 3 * w + d * w + 2 * n2]);
+      add(s1, e1, I[(size_t)cell * 3 * w + d * w + 2 * n2 + 1]);
+    }
+    const __nv_bfloat162* src = reinterpret_cast<const __nv_bfloat162*>(X + o0 * w) + n2;
+    for (int r = 0; r < rows; ++r) {
+      const float2 x = __bfloat1622float2(src[(size_t)r * (w / 2)]);
+      add(s0, e0, x.x);
+      add(s1, e1, x.y);
+    }
+    RAD[(size_t)cell * w + 2 * n2] = sq ? sqrtf(s0) : s0;
+    RAD[(size_t)cell * w + 2 * n2 + 1] = sq ? sqrtf(s1) : s1;
+  }
+}
+
+// ---- output layer and read-off: x0 = w_out . a + b_out; every symbol's output coefficient is its
+//      row . (alpha_H * w_out), or gamma_n w_out,n for the last activation's symbols ----
+__global__ void __launch_bounds__(256) k_rows_output(int w, int mode, const __nv_bfloat16* X, const int64_t* off,
+                                                     const int* cnt, const float* I, const float* A,
+                                                     const float* AL, const float* GA,
+                                                     const float* __restrict__ wout, float bout, int64_t first,
+                                                     float* center, float* spread) {
+  __shared__ float v[kMaxW];
+  __shared__ float red[2][8];
+  const int cell = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const bool sq = mode != ISX_BOUND_SOUND;
+  float x0 = 0.0f, s = 0.0f;
+  for (int n = t; n < w; n += blockDim.x) {
+    const size_t o = (size_t)cell * w + n;
+    v[n] = AL[o] * wout[n];
+    x0 = fmaf(wout[n], A[o], x0);
+    const float y = GA[o] * wout[n];
+    s += sq ? y * y : fabsf(y);
+  }
+  __syncthreads();
+  // three input rows and the G rows: one warp per row
+  const int rows = cnt[cell];
+  const int64_t o0 = off[cell];
+  for (int r = warp; r < rows + 3; r += 8) {
+    float y = 0.0f;
+    if (r < 3) {
+      const float* src = I + (size_t)cell * 3 * w + (size_t)r * w;
+      for (int n = lane; n < w; n += 32) y = fmaf(src[n], v[n], y);
+    } else {
+      const __nv_bfloat16* src = X + (o0 + r - 3) * w;
+      for (int n = lane; n < w; n += 32) y = fmaf(__bfloat162float(src[n]), v[n], y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+    if (lane == 0) s += sq ? y * y : fabsf(y);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    x0 += __shfl_xor_sync(0xffffffffu, x0, o);
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  if (lane == 0) {
+    red[0][warp] = x0;
+    red[1][warp] = s;
+  }
+  __syncthreads();
+  if (t == 0) {
+    float a = 0.0f, b = 0.0f;
+    for (int i = 0; i < 8; ++i) {
+      a += red[0][i];
+      b += red[1][i];
+    }
+    center[first + cell] = a + bout;
+    spread[first + cell] = (mode == ISX_BOUND_SOUND) ? b : sqrtf(mode == ISX_BOUND_RAUA ? b / 3.0f : b);
+  }
+}
+
+template <int W>
+isx_status launch_rows_gemm(isx_inr inr, const RowsGemmArgs& a, const CUtensorMap& map, cudaStream_t st) {
+  const size_t smem = RowsSmem<W>::bytes();
+  ISX_CUDA(cudaFuncSetAttribute(k_rows_gemm<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int sms = 148;
+  ISX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, inr->device));
+  int per_sm = 1;
+  ISX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_gemm<W>, kGT, smem));
+  per_sm = std::max(1, std::min(per_sm, 512 / (2 * W)));   // TMEM: 2 W columns per CTA
+  const int64_t ntiles = (a.R + kRT - 1) / kRT;
+  const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
+  k_rows_gemm<W><<<grid, kGT, smem, st>>>(a, map);
+  ISX_LAUNCH_CHECK("k_rows_gemm");
+  return ISX_OK;
+}
+
+template <int W>
+isx_status launch_rows_split(isx_inr inr, const RowsSplitArgs& a, const CUtensorMap& hi, const CUtensorMap& lo,
+                             cudaStream_t st) {
+  const size_t smem = SplitSmem<W>::bytes();
+  ISX_CUDA(cudaFuncSetAttribute(k_rows_split<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int sms = 148;
+  ISX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, inr->device));
+  int per_sm = 1;
+  ISX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_split<W>, kRT, smem));
+  per_sm = std::max(1, std::min(per_sm, 512 / W));
+  const int64_t ntiles = (4 * a.nc + kRT - 1) / kRT;
+  const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
+  k_rows_split<W><<<grid, kRT, smem, st>>>(a, hi, lo);
+  ISX_LAUNCH_CHECK("k_rows_split");
+  return ISX_OK;
+}
+
+}  // namespace
+
+bool rows_supported(isx_inr inr, isx_bound_mode mode, int inflate) {
+  if (!(inr->w == 128 || inr->w == 256) || inr->H < 1) return false;
+  if (mode == ISX_BOUND_SOUND && inflate) return false;
+  return mode == ISX_BOUND_SOUND || mode == ISX_BOUND_CLT || mode == ISX_BOUND_RAUA;
+}
+
+isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bound_mode mode, float* d_center,
+                           float* d_spread, cudaStream_t st) {
+  if (n <= 0) return ISX_OK;
+  if (!rows_supported(inr, mode, 0)) {
+    set_error("row-batched tensor-core bounds need hidden width 128 or 256 and no inflation");
+    return ISX_ERR_UNSUPPORTED;
+  }
+  const int w = inr->w, H = inr->H;
+  const int clt = mode == ISX_BOUND_CLT;
+  auto& ws = inr->ws;
+  ISX_TRY(ws[WS_TC_STATUS].ensure(64, "tc status"));
+  ISX_TRY(ws[WS_R_TOT].ensure(64, "row total"));
+  int* status = ws[WS_TC_STATUS].as<int>();
+  int64_t* d_tot = ws[WS_R_TOT].as<int64_t>();
+  ISX_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+  std::vector<CUtensorMap> maps(inr->n_layers), lomaps(inr->n_layers);
+  for (int l = 1; l <= H - 1; ++l) {
+    ISX_TRY(tensor_map_bf16(&maps[l], inr->W_bf16[l], w, w, 64, w));
+    ISX_TRY(tensor_map_bf16(&lomaps[l], inr->Wlo_bf16[l], w, w, 64, w));
+  }
+  // chunk size: about kRowBudget G rows per chunk, from the rows per cell the previous chunk needed
+  const int64_t kRowBudget = 1 << 24;
+  const int64_t kMaxCells = 1 << 19;
+  double rows_per_cell = (double)w * (H - 1);
+  int64_t first = 0;
+  while (first < n) {
+    const int64_t want = (int64_t)((double)kRowBudget / std::max(1.0, 1.25 * rows_per_cell));
+    const int nc = (int)std::min<int64_t>(n - first, std::max<int64_t>(1024, std::min(kMaxCells, want)));
+    const size_t cw = (size_t)nc * w * sizeof(float);
+    ISX_TRY(ws[WS_C].ensure(cw, "rows centre"));
+    ISX_TRY(ws[WS_R_A].ensure(cw, "rows post-activation centre"));
+    ISX_TRY(ws[WS_RAD].ensure(cw, "rows radius"));
+    ISX_TRY(ws[WS_ALPHA].ensure(cw, "rows alpha"));
+    ISX_TRY(ws[WS_GAMMA].ensure(cw, "rows gamma"));
+    ISX_TRY(ws[WS_R_I0].ensure(3 * cw, "rows input rows"));
+    ISX_TRY(ws[WS_R_I1].ensure(3 * cw, "rows input rows"));
+    for (Slot s : {WS_R_CNT0, WS_R_CNT1}) ISX_TRY(ws[s].ensure((size_t)nc * sizeof(int), "rows counts"));
+    for (Slot s : {WS_R_OFF0, WS_R_OFF1}) ISX_TRY(ws[s].ensure((size_t)nc * sizeof(int64_t), "rows offsets"));
+    float* C = ws[WS_C].as<float>();
+    float* A = ws[WS_R_A].as<float>();
+    float* RAD = ws[WS_RAD].as<float>();
+    float* AL = ws[WS_ALPHA].as<float>();
+    float* GA = ws[WS_GAMMA].as<float>();
+    float* I0 = ws[WS_R_I0].as<float>();
+    float* I1 = ws[WS_R_I1].as<float>();
+    Slot xs[2] = {WS_X0, WS_X1}, cs[2] = {WS_R_CNT0, WS_R_CNT1}, os[2] = {WS_R_OFF0, WS_R_OFF1},
+         rs[2] = {WS_R_RC0, WS_R_RC1};
+    int cur = 0;
+    int64_t R = 0;
+    {
+      prof::Scope ps(K_ROWS_AUX, st, 2.0 * nc * 3 * w, 0);
+      k_rows_input<<<nc, std::min(w, 256), 0, st>>>(src, first, w, clt, inr->W[0], inr->b[0], C, I0, RAD);
+    }
+    ISX_LAUNCH_CHECK("k_rows_input");
+    ISX_CUDA(cudaMemsetAsync(ws[cs[0]].ptr, 0, (size_t)nc * sizeof(int), st));
+    ISX_CUDA(cudaMemsetAsync(ws[os[0]].ptr, 0, (size_t)nc * sizeof(int64_t), st));
+    for (int j = 1; j <= H - 1; ++j) {
+      const int nxt = cur ^ 1;
+      int* cnt_in = ws[cs[cur]].as<int>();
+      int* cnt_out = ws[cs[nxt]].as<int>();
+      int64_t* off_in = ws[os[cur]].as<int64_t>();
+      int64_t* off_out = ws[os[nxt]].as<int64_t>();
+      {
+        prof::Scope ps(K_ROWS_ACT, st, 0, 0);
+        k_rows_act<<<nc, 256, 0, st>>>(w, (int)mode, inr->act, C, RAD, A, AL, GA, cnt_in, cnt_out);
+        ISX_LAUNCH_CHECK("k_rows_act");
+        k_rows_scan<<<1, 1024, 0, st>>>(cnt_out, nc, off_out, d_tot);
+        ISX_LAUNCH_CHECK("k_rows_scan");
+      }
+      int64_t Rn = 0;
+      ISX_CUDA(cudaMemcpyAsync(&Rn, d_tot, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+      ISX_CUDA(cudaStreamSynchronize(st));
+      ISX_TRY(ws[xs[nxt]].ensure((size_t)std::max<int64_t>(Rn, 1) * w * 2, "rows"));
+      ISX_TRY(ws[rs[nxt]].ensure((size_t)std::max<int64_t>(Rn, 1) * sizeof(int), "row cells"));
+      __nv_bfloat16* Xin = ws[xs[cur]].as<__nv_bfloat16>();
+      __nv_bfloat16* Xout = ws[xs[nxt]].as<__nv_bfloat16>();
+      if (R > 0) {
+        RowsGemmArgs ga{};
+        ga.xin = Xin;
+        ga.rowcell = ws[rs[cur]].as<int>();
+        ga.off_in = off_in;
+        ga.off_out = off_out;
+        ga.alpha = AL;
+        ga.R = R;
+        ga.xout = Xout;
+        ga.status = status;
+        prof::Scope ps(K_ROWS_GEMM, st, 2.0 * (double)R * w * w, 4.0 * (double)R * w);
+        if (w == 256) {
+          ISX_TRY(launch_rows_gemm<256>(inr, ga, maps[j], st));
+        } else {
+          ISX_TRY(launch_rows_gemm<128>(inr, ga, maps[j], st));
+        }
+      }
+      {
+        prof::Scope ps(K_ROWS_NEW, st, 0, 0);
+        k_rows_new<<<nc, 256, 0, st>>>(w, GA, inr->Wt[j], cnt_in, off_out, cnt_out, Xout, ws[rs[nxt]].as<int>());
+        ISX_LAUNCH_CHECK("k_rows_new");
+      }
+      {
+        RowsSplitArgs sa{};
+        sa.nc = nc;
+        sa.A = A;
+        sa.AL = AL;
+        sa.Iin = I0;
+        sa.bias = inr->b[j];
+        sa.Cout = C;
+        sa.Iout = I1;
+        sa.status = status;
+        prof::Scope ps(K_ROWS_SPLIT, st, 2.0 * nc * 4.0 * w * w, 0);
+        if (w == 256) {
+          ISX_TRY(launch_rows_split<256>(inr, sa, maps[j], lomaps[j], st));
+        } else {
+          ISX_TRY(launch_rows_split<128>(inr, sa, maps[j], lomaps[j], st));
+        }
+      }
+      {
+        prof::Scope ps(K_ROWS_REDUCE, st, 0, 2.0 * (double)Rn * w);
+        k_rows_reduce<<<nc, std::min(w / 2, 128), 0, st>>>(w, clt, Xout, off_out, cnt_out, I1, RAD);
+        ISX_LAUNCH_CHECK("k_rows_reduce");
+      }
+      std::swap(I0, I1);
+      cur = nxt;
+      R = Rn;
+    }
+    {
+      prof::Scope ps(K_ROWS_OUT, st, 2.0 * (double)(R + 3.0 * nc) * w, 0);
+      k_rows_act<<<nc, 256, 0, st>>>(w, (int)mode, inr->act, C, RAD, A, AL, GA, nullptr, nullptr);
+      ISX_LAUNCH_CHECK("k_rows_act");
+      const int L = inr->n_layers - 1;
+      k_rows_output<<<nc, 256, 0, st>>>(w, (int)mode, ws[xs[cur]].as<__nv_bfloat16>(), ws[os[cur]].as<int64_t>(),
+                                        ws[cs[cur]].as<int>(), I0, A, AL, GA, inr->W[L], inr->hb[L][0], first,
+                                        d_center, d_spread);
+      ISX_LAUNCH_CHECK("k_rows_output");
+    }
+    rows_per_cell = std::max(1.0, (double)R / nc);
+    first += nc;
+  }
+  int stat = 0;
+  ISX_CUDA(cudaMemcpyAsync(&stat, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  ISX_CUDA(cudaStreamSynchronize(st));
+  if (stat != 0) {
+    set_error("row-batched tensor-core kernel gave up waiting (bounded wait expired)");
+    return (isx_status)stat;
+  }
+  return ISX_OK;
+}
+
+}  // namespace isx

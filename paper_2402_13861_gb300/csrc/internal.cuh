@@ -54,6 +54,7 @@ enum Slot {
   WS_TC_SCRATCH, WS_TC_STATE, WS_TC_STATUS,
   WS_ANC_C_A, WS_ANC_C_B, WS_ANC_S_A, WS_ANC_S_B, WS_ANC_G_A, WS_ANC_G_B, WS_PROP_KEEP, WS_PROP_NEED,
   WS_PROP_IDX, WS_PROP_CODES,
+  WS_R_I0, WS_R_I1, WS_R_A, WS_R_CNT0, WS_R_CNT1, WS_R_OFF0, WS_R_OFF1, WS_R_RC0, WS_R_RC1, WS_R_TOT,
   WS_N_SLOTS
 };
 
@@ -87,7 +88,8 @@ namespace isx {
 enum KernelId {
   K_INPUT, K_RELU, K_GEMV, K_GEMM_FP32, K_FRESH, K_REDUCE, K_OUTPUT, K_CULL, K_SCAN, K_SCATTER, K_MARK,
   K_FLAGCOUNT, K_SCATTER_FLAGS, K_EVAL_FP32, K_MC_COUNT, K_MC_EMIT, K_IOTA, K_BOUND_TC, K_TC_PREP, K_TC_OUTPUT,
-  K_EVAL_TC, K_BOUND_COV, K_PROP_GATE, K_PROP_MERGE, K_PROP_FWD, K_PROP_GRAD, K_PROP_ADAM, K_BOUND_RAFIXED, K_COUNT
+  K_EVAL_TC, K_BOUND_COV, K_PROP_GATE, K_PROP_MERGE, K_PROP_FWD, K_PROP_GRAD, K_PROP_ADAM, K_BOUND_RAFIXED, K_ROWS_GEMM, K_ROWS_AUX,
+  K_ROWS_ACT, K_ROWS_NEW, K_ROWS_SPLIT, K_ROWS_REDUCE, K_ROWS_OUT, K_COUNT
 };
 namespace prof {
 // RAII bracket around one kernel launch: counts it, adds its algorithmic work, and (when
@@ -128,6 +130,13 @@ bool rafixed_supported(isx_inr inr);
 __host__ __device__ __forceinline__ bool sound_readout(int mode) {
   return mode == ISX_BOUND_SOUND || mode == ISX_BOUND_RAFIXED;
 }
+
+// Row-batched tensor-core path: layer-synchronous over a chunk of cells, noise-symbol rows with a
+// zero coefficient dropped, alpha applied on the A side so that one weight operand serves all
+// cells (bound_rows.cu).  Hidden widths 128 and 256, no inflation.
+isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bound_mode mode, float* d_center,
+                           float* d_spread, cudaStream_t st);
+bool rows_supported(isx_inr inr, isx_bound_mode mode, int inflate);
 
 // Tensor-core (tcgen05, bfloat16) path; ISX_ERR_UNSUPPORTED for shapes it does not cover.
 isx_status bound_bf16(isx_inr inr, const CellSource& src, int64_t n, isx_bound_mode mode,

@@ -1,6 +1,7 @@
 """Batched extraction (isx_batch_*): every entry of a level-synchronous batch gives exactly the
-active cells and triangles of its own single extraction (the same bound kernel and cull test, the
-same stable order), with and without CUDA-graph replay; unsupported batches are rejected."""
+active cells and triangles of its own single extraction with the per-cell tensor-core bound
+kernel (the same bound kernel and cull test, the same stable order), with and without CUDA-graph
+replay; unsupported batches are rejected."""
 import numpy as np
 import pytest
 import torch
@@ -39,10 +40,13 @@ def _same(a, b):
 
 
 @pytest.mark.parametrize("use_graph", [False, True])
-def test_batch_equals_single_extractions(pkg, use_graph):
+def test_batch_equals_single_extractions(pkg, use_graph, monkeypatch):
     ents = _entries()
     nets = [pkg.Inr(layers) for layers, _ in ents]
+    # the batch runs the per-cell tensor-core bound kernel; single extractions take it too
+    monkeypatch.setenv("ISX_BF16_ROWS", "0")
     singles = [net.extract(**p) for net, (_, p) in zip(nets, ents)]
+    monkeypatch.delenv("ISX_BF16_ROWS")
     batch = pkg.Batch(nets, [p for _, p in ents], use_graph=use_graph)
     for rep in range(3):                       # sized run, then (graph) capture + replay, then replay
         res = batch.run()

@@ -1,0 +1,73 @@
+"""The row-batched tensor-core bound path (bound_rows.cu): bounds of many cells, over several
+chunks of the layer-synchronous loop, agree with the per-cell tensor-core kernel and with the
+float32 path within the bfloat16 band 3 H u_b (|x0| + spread) (u_b = 2^-8, three bf16 roundings per
+coefficient per layer on either path), and the path really runs (its GEMM kernel is counted by the
+launch accounting).  Parity against the float64 oracle is in test_gpu_bf16.py, which takes this
+path for every mode it supports."""
+import numpy as np
+import pytest
+import torch
+
+from synth import boxes, inr
+
+from _helpers import to_np
+
+pytestmark = pytest.mark.gpu
+UB = 2.0 ** -8
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2402_13861_gb300 as p
+    torch.cuda.set_device(0)
+    return p
+
+
+def _cubes(n, seed, lmin, lmax):
+    ijk, level, lo, hi = boxes.random_cubes(n, seed, lmin, lmax)
+    return torch.tensor(lo, device="cuda"), torch.tensor(hi, device="cuda")
+
+
+@pytest.mark.parametrize("dims", [[3, 128, 128, 128, 1], "scientific"])
+@pytest.mark.parametrize("mode", ["clt", "sound", "raua"])
+def test_rows_path_matches_per_cell_kernel(pkg, dims, mode, monkeypatch):
+    layers = inr.load_inr(dims)[0] if isinstance(dims, str) else inr.random_inr(dims, 5)
+    H = len(layers) - 1
+    net = pkg.Inr(layers)
+    n = 60000 if isinstance(dims, str) else 20000          # several chunks of the row loop at w = 256
+    lo, hi = _cubes(n, 12, 3, 9)
+    c, s = net.bound_cells(lo, hi, mode=mode, prec="bf16")
+    c, s = to_np(c).astype(np.float64), to_np(s).astype(np.float64)
+    monkeypatch.setenv("ISX_BF16_ROWS", "0")
+    c1, s1 = net.bound_cells(lo, hi, mode=mode, prec="bf16")
+    monkeypatch.delenv("ISX_BF16_ROWS")
+    c1, s1 = to_np(c1).astype(np.float64), to_np(s1).astype(np.float64)
+    m = 4000
+    c32, s32 = net.bound_cells(lo[:m], hi[:m], mode=mode, prec="fp32")
+    c32, s32 = to_np(c32).astype(np.float64), to_np(s32).astype(np.float64)
+    tol = 3 * H * UB * (np.abs(c1) + s1) + 1e-6
+    print(f"{dims if isinstance(dims, str) else dims[1:-1]} {mode}: rows vs per-cell max |dc|/tol "
+          f"{np.max(np.abs(c - c1) / tol):.3f}, |ds|/tol {np.max(np.abs(s - s1) / tol):.3f}; rows vs fp32 "
+          f"|ds|/s {np.max(np.abs(s[:m] - s32) / np.maximum(s32, 1e-30)):.2e}")
+    assert np.all(np.isfinite(c)) and np.all(np.isfinite(s))
+    assert np.all(np.abs(c - c1) <= 2 * tol) and np.all(np.abs(s - s1) <= 2 * tol)
+    tol32 = 3 * H * UB * (np.abs(c32) + s32) + 1e-6
+    assert np.all(np.abs(c[:m] - c32) <= tol32) and np.all(np.abs(s[:m] - s32) <= tol32)
+    net.close()
+
+
+def test_rows_path_runs_its_kernels(pkg):
+    from paper_2402_13861_gb300 import _lib
+    net = pkg.Inr(inr.random_inr([3, 256, 256, 256, 1], 6))
+    lo, hi = _cubes(3000, 13, 2, 8)
+    _lib.profile_enable(True)
+    _lib.profile_reset()
+    net.bound_cells(lo, hi, mode="clt", prec="bf16")
+    torch.cuda.synchronize()
+    prof = _lib.profile_read()
+    _lib.profile_enable(False)
+    assert prof["rows_gemm"]["launches"] >= 1 and prof.get("bound_tc", {"launches": 0})["launches"] == 0
+    print("rows_gemm launches", prof["rows_gemm"]["launches"], "GFLOP", prof["rows_gemm"]["flops"] / 1e9)
+    net.close()

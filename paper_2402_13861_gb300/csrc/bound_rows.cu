@@ -256,9 +256,18 @@ __global__ void k_rows_input(CellSource src, int64_t first, int w, int clt, cons
   }
 }
 
-// ---- activation j: alpha, gamma, post-activation centre a; new-symbol count per cell ----
+// ---- activation j: alpha, gamma, post-activation centre a; new-symbol count per cell; and (when
+//      AH is given) the A operand of the centre / input-row GEMM, rows 4 cell + q = a, alpha I_q,
+//      each split into bf16 high and low terms ----
+__device__ __forceinline__ void split_put(__nv_bfloat16* hi, __nv_bfloat16* lo, size_t i, float v) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  hi[i] = h;
+  lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
 __global__ void k_rows_act(int w, int mode, int act, const float* C, const float* RAD, float* A, float* AL,
-                           float* GA, const int* cnt_in, int* cnt_out) {
+                           float* GA, const int* cnt_in, int* cnt_out, const float* I, __nv_bfloat16* AH,
+                           __nv_bfloat16* ALO) {
   __shared__ int wsum[32];
   const int cell = blockIdx.x;
   int m = 0;
@@ -269,6 +278,11 @@ __global__ void k_rows_act(int w, int mode, int act, const float* C, const float
     AL[o] = L.alpha;
     GA[o] = L.gamma;
     m += (L.gamma != 0.0f);
+    if (AH) {
+      const size_t r0 = (size_t)cell * 4 * w + n;
+      split_put(AH, ALO, r0, L.center);
+      for (int d = 0; d < 3; ++d) split_put(AH, ALO, r0 + (size_t)(d + 1) * w, L.alpha * I[((size_t)cell * 3 + d) * w + n]);
+    }
   }
   if (!cnt_out) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -335,69 +349,60 @@ __global__ void k_rows_new(int w, const float* __restrict__ GA, const float* __r
 // ---- centre and input rows of z_{j+1}: c' = W a + b, I'_d = (I_d diag(alpha)) W^T, at float32-class
 //      accuracy on the tensor cores: every operand x is carried as x_hi + x_lo (two bf16 terms) and
 //      the product as a_hi w_hi + a_lo w_hi + a_hi w_lo (the dropped a_lo w_lo is below 2^-16 of
-//      it), accumulated in float32 in TMEM.  Row r of a 128-row tile is quantity r & 3 (0: a,
-//      1-3: alpha I_d) of cell r >> 2.  W_hi and W_lo stream through two 64-wide K-chunk stages. ----
-enum { SB_XFULL, SB_XEMPTY, SB_YFULL, SB_YEMPTY, SB_DONE, SB_COUNT };
+//      it), accumulated in float32 in TMEM.  Row r of the A operand is quantity r & 3 (0: a,
+//      1-3: alpha I_d) of cell r >> 2; the activation pass writes it, split, to global memory.
+//      Warp-specialised and TMA-fed: warp 0 loads A_hi, A_lo, W_hi, W_lo chunk by chunk (64-wide K)
+//      into a two-stage ring, warp 1 issues the MMAs into one of two TMEM accumulators, warps 2-5
+//      drain the other accumulator to float32 rows (TMEM lane group = warp mod 4). ----
+enum { SB_FULL, SB_EMPTY = SB_FULL + 2, SB_TFULL = SB_EMPTY + 2, SB_TEMPTY = SB_TFULL + 2, SB_COUNT = SB_TEMPTY + 2 };
+constexpr int kST = 192;                        // threads of the split GEMM: producer, MMA, 4 epilogue warps
 
 struct RowsSplitArgs {
   int64_t nc;
-  const float* A;                               // [nc][W] post-activation centre
-  const float* AL;                              // [nc][W]
-  const float* Iin;                             // [nc][3][W]
   const float* bias;                            // [W]
   float* Cout;                                  // [nc][W]
   float* Iout;                                  // [nc][3][W]
   int* status;
 };
+struct RowsSplitMaps {
+  CUtensorMap ahi, alo;                         // A terms [4 nc][W] bf16, box {64, 128}
+  CUtensorMap whi, wlo;                         // W_j terms [W][W] bf16, box {64, W}
+};
 
 template <int W>
 struct SplitSmem {
   static constexpr int KC = W / 64;
-  static constexpr size_t kA = (size_t)kRT * W * 2;        // one bf16 term of the A tile
-  static constexpr size_t kS = (size_t)W * 128;            // one weight stage (64-wide K chunk)
-  static constexpr size_t bytes() { return 1024 + 2 * kA + 2 * kS + SB_COUNT * 8 + 16; }
+  static constexpr size_t kA = (size_t)kRT * 128;          // one A term of one K chunk
+  static constexpr size_t kB = (size_t)W * 128;            // one W term of one K chunk
+  static constexpr size_t kStage = 2 * kA + 2 * kB;
+  static constexpr size_t bytes() { return 1024 + 2 * kStage + SB_COUNT * 8 + 16; }
 };
 
-// 8 consecutive columns of row `row`, split into bf16 high and low terms
-__device__ __forceinline__ void split_store8(uint8_t* Ahi, uint8_t* Alo, int row, int k, const float* v) {
-  uint32_t ph[4], pl[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-    const float2 hf = __bfloat1622float2(h);
-    const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
-    ph[i] = *reinterpret_cast<const uint32_t*>(&h);
-    pl[i] = *reinterpret_cast<const uint32_t*>(&l);
-  }
-  const uint32_t o = roff(row, k);
-  *reinterpret_cast<uint4*>(Ahi + o) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-  *reinterpret_cast<uint4*>(Alo + o) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
-}
-
 template <int W>
-__global__ void __launch_bounds__(kRT, 1) k_rows_split(const __grid_constant__ RowsSplitArgs args,
-                                                        const __grid_constant__ CUtensorMap whi,
-                                                        const __grid_constant__ CUtensorMap wlo) {
+__global__ void __launch_bounds__(kST, 1) k_rows_split(const __grid_constant__ RowsSplitArgs args,
+                                                        const __grid_constant__ RowsSplitMaps maps) {
   using S = SplitSmem<W>;
   constexpr int KC = S::KC;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* Ahi = base;
-  uint8_t* Alo = Ahi + S::kA;
-  uint8_t* X = Alo + S::kA;
-  uint8_t* Y = X + S::kS;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(Y + S::kS);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + 2 * S::kStage);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + SB_COUNT);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
-  const int t = threadIdx.x, warp = t >> 5;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int64_t ntiles = (4 * args.nc + kRT - 1) / kRT;
   if (t == 0) {
-    for (int i = 0; i < SB_COUNT; ++i) mbar_init(&bar[i], 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bar[SB_FULL + i], 1);
+      mbar_init(&bar[SB_EMPTY + i], 1);
+      mbar_init(&bar[SB_TFULL + i], 1);
+      mbar_init(&bar[SB_TEMPTY + i], 4);
+    }
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "n"(W)
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                 "n"(2 * W)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -405,112 +410,94 @@ __global__ void __launch_bounds__(kRT, 1) k_rows_split(const __grid_constant__ R
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t id = idesc(W);
-  uint32_t xf = 0, xe = 0, yf = 0, ye = 0, dn = 0;
-  auto load_x = [&](int c) {
-    mbar_expect_tx(&bar[SB_XFULL], (uint32_t)S::kS);
-    tma_load_2d(X, &whi, &bar[SB_XFULL], c * 64, 0);
-  };
-  auto load_y = [&](int c) {
-    mbar_expect_tx(&bar[SB_YFULL], (uint32_t)S::kS);
-    tma_load_2d(Y, &wlo, &bar[SB_YFULL], c * 64, 0);
-  };
-  if (t == 0 && blockIdx.x < ntiles) {
-    load_x(0);
-    load_y(0);
-  }
-  bool ok = true;
-  for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    const int64_t r = tile * kRT + t;
-    const int64_t cell = r >> 2;
-    const int q = (int)(r & 3);
-    const bool valid = cell < args.nc;
-    for (int k = 0; k < W; k += 8) {
-      float v[8];
-      if (valid) {
-        if (q == 0) {
-          const float4* s4 = reinterpret_cast<const float4*>(args.A + cell * W + k);
-          const float4 a0 = s4[0], a1 = s4[1];
-          v[0] = a0.x; v[1] = a0.y; v[2] = a0.z; v[3] = a0.w; v[4] = a1.x; v[5] = a1.y; v[6] = a1.z; v[7] = a1.w;
-        } else {
-          const float4* s4 = reinterpret_cast<const float4*>(args.Iin + (cell * 3 + q - 1) * W + k);
-          const float4* l4 = reinterpret_cast<const float4*>(args.AL + cell * W + k);
-          const float4 a0 = s4[0], a1 = s4[1], l0 = l4[0], l1 = l4[1];
-          v[0] = a0.x * l0.x; v[1] = a0.y * l0.y; v[2] = a0.z * l0.z; v[3] = a0.w * l0.w;
-          v[4] = a1.x * l1.x; v[5] = a1.y * l1.y; v[6] = a1.z * l1.z; v[7] = a1.w * l1.w;
+  auto stage = [&](int s) { return base + (size_t)s * S::kStage; };
+
+  if (warp == 0) {
+    // ---- producer ----
+    if (lane == 0) {
+      uint32_t it = 0;
+      for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        for (int c = 0; c < KC; ++c, ++it) {
+          const int sidx = it & 1;
+          if (!rwait(&bar[SB_EMPTY + sidx], ((it >> 1) & 1) ^ 1, abort, args.status)) break;
+          uint8_t* sp = stage(sidx);
+          mbar_expect_tx(&bar[SB_FULL + sidx], (uint32_t)S::kStage);
+          tma_load_2d(sp, &maps.ahi, &bar[SB_FULL + sidx], c * 64, (int)(tile * kRT));
+          tma_load_2d(sp + S::kA, &maps.alo, &bar[SB_FULL + sidx], c * 64, (int)(tile * kRT));
+          tma_load_2d(sp + 2 * S::kA, &maps.whi, &bar[SB_FULL + sidx], c * 64, 0);
+          tma_load_2d(sp + 2 * S::kA + S::kB, &maps.wlo, &bar[SB_FULL + sidx], c * 64, 0);
         }
-      } else {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = 0.0f;
+        if (*abort) break;
       }
-      split_store8(Ahi, Alo, t, k, v);
     }
-    fence_async_shared();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (t == 0) {
-      for (int c = 0; c < KC && ok; ++c) {
-        if (!rwait(&bar[SB_XFULL], xf & 1, abort, args.status)) { ok = false; break; }
-        ++xf;
+  } else if (warp == 1) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      const uint32_t id = idesc(W);
+      uint32_t it = 0, tt = 0;
+      for (int64_t tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x, ++tt) {
+        const uint32_t b = tt & 1;
+        if (!rwait(&bar[SB_TEMPTY + b], ((tt >> 1) & 1) ^ 1, abort, args.status)) break;
         tc_fence_after();
-        const uint32_t ah = su32(Ahi + (size_t)c * kRT * 128), al = su32(Alo + (size_t)c * kRT * 128);
-        const uint32_t bx = su32(X), by = su32(Y);
+        const uint32_t dt = tmem + b * W;
+        for (int c = 0; c < KC; ++c, ++it) {
+          const int sidx = it & 1;
+          if (!rwait(&bar[SB_FULL + sidx], (it >> 1) & 1, abort, args.status)) break;
+          tc_fence_after();
+          const uint32_t ah = su32(stage(sidx)), al = ah + (uint32_t)S::kA;
+          const uint32_t bh = ah + 2 * (uint32_t)S::kA, bl = bh + (uint32_t)S::kB;
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          mma_bf16(tmem, sdesc(ah + kk * 32), sdesc(bx + kk * 32), id, (c > 0 || kk > 0) ? 1u : 0u);
-          mma_bf16(tmem, sdesc(al + kk * 32), sdesc(bx + kk * 32), id, 1u);
+          for (int kk = 0; kk < 4; ++kk) {
+            mma_bf16(dt, sdesc(ah + kk * 32), sdesc(bh + kk * 32), id, (c > 0 || kk > 0) ? 1u : 0u);
+            mma_bf16(dt, sdesc(al + kk * 32), sdesc(bh + kk * 32), id, 1u);
+            mma_bf16(dt, sdesc(ah + kk * 32), sdesc(bl + kk * 32), id, 1u);
+          }
+          mma_commit(&bar[SB_EMPTY + sidx]);
         }
-        mma_commit(&bar[SB_XEMPTY]);
-        if (!rwait(&bar[SB_YFULL], yf & 1, abort, args.status)) { ok = false; break; }
-        ++yf;
-        tc_fence_after();
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) mma_bf16(tmem, sdesc(ah + kk * 32), sdesc(by + kk * 32), id, 1u);
-        mma_commit(&bar[SB_YEMPTY]);
-        // refill: the next chunk of this tile, else chunk 0 of this CTA's next tile
-        const int nxt = (c + 1 < KC) ? c + 1 : ((tile + gridDim.x < ntiles) ? 0 : -1);
-        if (!rwait(&bar[SB_XEMPTY], xe & 1, abort, args.status)) { ok = false; break; }
-        ++xe;
-        if (nxt >= 0) load_x(nxt);
-        if (!rwait(&bar[SB_YEMPTY], ye & 1, abort, args.status)) { ok = false; break; }
-        ++ye;
-        if (nxt >= 0) load_y(nxt);
-      }
-      if (ok) mma_commit(&bar[SB_DONE]);
-    }
-    if (!rwait(&bar[SB_DONE], dn & 1, abort, args.status)) ok = false;
-    ++dn;
-    if (__syncthreads_or(!ok || *abort)) {
-      ok = false;
-      break;
-    }
-    tc_fence_after();
-    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
-    float* dst = nullptr;
-    if (valid) dst = (q == 0) ? args.Cout + cell * W : args.Iout + (cell * 3 + q - 1) * W;
-    for (int c0 = 0; c0 < W; c0 += 32) {
-      float v[32];
-      tmem_ld32(trow + c0, v);
-      if (valid) {
-        if (q == 0)
-#pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] += args.bias[c0 + i];
-        float4* d4 = reinterpret_cast<float4*>(dst + c0);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        mma_commit(&bar[SB_TFULL + b]);
       }
     }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
+  } else {
+    // ---- epilogue: TMEM lane group warp % 4, one row per thread ----
+    const int row = 32 * (warp & 3) + lane;
+    uint32_t tt = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tt) {
+      const uint32_t b = tt & 1;
+      const bool got = rwait(&bar[SB_TFULL + b], (tt >> 1) & 1, abort, args.status);
+      if (!__all_sync(0xffffffffu, got)) break;
+      tc_fence_after();
+      const int64_t r = tile * kRT + row;
+      const int64_t cell = r >> 2;
+      const int q = (int)(r & 3);
+      const bool valid = cell < args.nc;
+      float* dst = nullptr;
+      if (valid) dst = (q == 0) ? args.Cout + cell * W : args.Iout + (cell * 3 + q - 1) * W;
+      const uint32_t trow = tmem + b * W + ((uint32_t)(32 * (warp & 3)) << 16);
+#pragma unroll 1
+      for (int c0 = 0; c0 < W; c0 += 32) {
+        float v[32];
+        tmem_ld32(trow + c0, v);
+        if (valid) {
+          if (q == 0)
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] += args.bias[c0 + i];
+          float4* d4 = reinterpret_cast<float4*>(dst + c0);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar[SB_TEMPTY + b]);
+    }
   }
+  tc_fence_before();
   __syncthreads();
   if (*abort)
     for (int i = 0; i < 1000; ++i) __nanosleep(1000);
-  if (warp == 0) {
+  if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(W) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(2 * W) : "memory");
   }
 }
 
@@ -618,18 +605,17 @@ isx_status launch_rows_gemm(isx_inr inr, const RowsGemmArgs& a, const CUtensorMa
 }
 
 template <int W>
-isx_status launch_rows_split(isx_inr inr, const RowsSplitArgs& a, const CUtensorMap& hi, const CUtensorMap& lo,
-                             cudaStream_t st) {
+isx_status launch_rows_split(isx_inr inr, const RowsSplitArgs& a, const RowsSplitMaps& maps, cudaStream_t st) {
   const size_t smem = SplitSmem<W>::bytes();
   ISX_CUDA(cudaFuncSetAttribute(k_rows_split<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int sms = 148;
   ISX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, inr->device));
   int per_sm = 1;
-  ISX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_split<W>, kRT, smem));
-  per_sm = std::max(1, std::min(per_sm, 512 / W));
+  ISX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_split<W>, kST, smem));
+  per_sm = std::max(1, std::min(per_sm, 512 / (2 * W)));
   const int64_t ntiles = (4 * a.nc + kRT - 1) / kRT;
   const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
-  k_rows_split<W><<<grid, kRT, smem, st>>>(a, hi, lo);
+  k_rows_split<W><<<grid, kST, smem, st>>>(a, maps);
   ISX_LAUNCH_CHECK("k_rows_split");
   return ISX_OK;
 }
@@ -678,6 +664,8 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
     ISX_TRY(ws[WS_GAMMA].ensure(cw, "rows gamma"));
     ISX_TRY(ws[WS_R_I0].ensure(3 * cw, "rows input rows"));
     ISX_TRY(ws[WS_R_I1].ensure(3 * cw, "rows input rows"));
+    ISX_TRY(ws[WS_R_AH].ensure(4 * cw / 2, "split A, high terms"));
+    ISX_TRY(ws[WS_R_ALO].ensure(4 * cw / 2, "split A, low terms"));
     for (Slot s : {WS_R_CNT0, WS_R_CNT1}) ISX_TRY(ws[s].ensure((size_t)nc * sizeof(int), "rows counts"));
     for (Slot s : {WS_R_OFF0, WS_R_OFF1}) ISX_TRY(ws[s].ensure((size_t)nc * sizeof(int64_t), "rows offsets"));
     float* C = ws[WS_C].as<float>();
@@ -687,6 +675,8 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
     float* GA = ws[WS_GAMMA].as<float>();
     float* I0 = ws[WS_R_I0].as<float>();
     float* I1 = ws[WS_R_I1].as<float>();
+    __nv_bfloat16* AH = ws[WS_R_AH].as<__nv_bfloat16>();
+    __nv_bfloat16* ALO = ws[WS_R_ALO].as<__nv_bfloat16>();
     Slot xs[2] = {WS_X0, WS_X1}, cs[2] = {WS_R_CNT0, WS_R_CNT1}, os[2] = {WS_R_OFF0, WS_R_OFF1},
          rs[2] = {WS_R_RC0, WS_R_RC1};
     int cur = 0;
@@ -706,7 +696,7 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
       int64_t* off_out = ws[os[nxt]].as<int64_t>();
       {
         prof::Scope ps(K_ROWS_ACT, st, 0, 0);
-        k_rows_act<<<nc, 256, 0, st>>>(w, (int)mode, inr->act, C, RAD, A, AL, GA, cnt_in, cnt_out);
+        k_rows_act<<<nc, 256, 0, st>>>(w, (int)mode, inr->act, C, RAD, A, AL, GA, cnt_in, cnt_out, I0, AH, ALO);
         ISX_LAUNCH_CHECK("k_rows_act");
         k_rows_scan<<<1, 1024, 0, st>>>(cnt_out, nc, off_out, d_tot);
         ISX_LAUNCH_CHECK("k_rows_scan");
@@ -743,18 +733,21 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
       {
         RowsSplitArgs sa{};
         sa.nc = nc;
-        sa.A = A;
-        sa.AL = AL;
-        sa.Iin = I0;
         sa.bias = inr->b[j];
         sa.Cout = C;
         sa.Iout = I1;
         sa.status = status;
+        RowsSplitMaps sm;
+        std::memset(&sm, 0, sizeof(sm));
+        ISX_TRY(tensor_map_bf16(&sm.ahi, AH, w, 4 * (uint64_t)nc, 64, kRT));
+        ISX_TRY(tensor_map_bf16(&sm.alo, ALO, w, 4 * (uint64_t)nc, 64, kRT));
+        sm.whi = maps[j];
+        sm.wlo = lomaps[j];
         prof::Scope ps(K_ROWS_SPLIT, st, 2.0 * nc * 4.0 * w * w, 0);
         if (w == 256) {
-          ISX_TRY(launch_rows_split<256>(inr, sa, maps[j], lomaps[j], st));
+          ISX_TRY(launch_rows_split<256>(inr, sa, sm, st));
         } else {
-          ISX_TRY(launch_rows_split<128>(inr, sa, maps[j], lomaps[j], st));
+          ISX_TRY(launch_rows_split<128>(inr, sa, sm, st));
         }
       }
       {
@@ -768,7 +761,8 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
     }
     {
       prof::Scope ps(K_ROWS_OUT, st, 2.0 * (double)(R + 3.0 * nc) * w, 0);
-      k_rows_act<<<nc, 256, 0, st>>>(w, (int)mode, inr->act, C, RAD, A, AL, GA, nullptr, nullptr);
+      k_rows_act<<<nc, 256, 0, st>>>(w, (int)mode, inr->act, C, RAD, A, AL, GA, nullptr, nullptr, nullptr, nullptr,
+                                     nullptr);
       ISX_LAUNCH_CHECK("k_rows_act");
       const int L = inr->n_layers - 1;
       k_rows_output<<<nc, 256, 0, st>>>(w, (int)mode, ws[xs[cur]].as<__nv_bfloat16>(), ws[os[cur]].as<int64_t>(),

@@ -54,7 +54,7 @@ enum Slot {
   WS_TC_SCRATCH, WS_TC_STATE, WS_TC_STATUS,
   WS_ANC_C_A, WS_ANC_C_B, WS_ANC_S_A, WS_ANC_S_B, WS_ANC_G_A, WS_ANC_G_B, WS_PROP_KEEP, WS_PROP_NEED,
   WS_PROP_IDX, WS_PROP_CODES,
-  WS_R_I0, WS_R_I1, WS_R_A, WS_R_CNT0, WS_R_CNT1, WS_R_OFF0, WS_R_OFF1, WS_R_RC0, WS_R_RC1, WS_R_TOT,
+  WS_R_I0, WS_R_I1, WS_R_A, WS_R_CNT0, WS_R_CNT1, WS_R_OFF0, WS_R_OFF1, WS_R_RC0, WS_R_RC1, WS_R_TOT, WS_R_AH, WS_R_ALO,
   WS_N_SLOTS
 };
 

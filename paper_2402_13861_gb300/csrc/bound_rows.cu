@@ -36,10 +36,8 @@ namespace {
 using namespace tc;
 
 constexpr int kRT = 128;                        // rows per MMA tile
-constexpr int kGT = 256;                        // threads of the row GEMM: two per row
 constexpr int kMaxW = 512;                      // largest hidden width of an INR
 constexpr uint64_t kRowsWaitNs = 2000000000ull;
-enum { RB_WFULL, RB_MMA, RB_COUNT };
 
 struct RowsGemmArgs {
   const __nv_bfloat16* xin;                     // [R][W] rows of z_j
@@ -55,9 +53,10 @@ struct RowsGemmArgs {
 template <int W>
 struct RowsSmem {
   static constexpr int KC = W / 64;
+  static constexpr int NS = (W == 256) ? 5 : 4;            // A ring: one 64-wide K chunk of a tile each
   static constexpr size_t kWB = (size_t)W * W * 2;         // W_j, KC chunks of [W rows][128 B]
-  static constexpr size_t kAB = (size_t)kRT * W * 2;       // one A tile, KC chunks of [128 rows][128 B]
-  static constexpr size_t bytes() { return 1024 + kWB + kAB + RB_COUNT * 8 + 16; }
+  static constexpr size_t kAC = (size_t)kRT * 128;         // one A chunk: [128 rows][128 B]
+  static constexpr size_t bytes() { return 1024 + kWB + NS * kAC + (3 * NS + 5) * 8 + 16; }
 };
 
 __device__ __forceinline__ uint32_t roff(int row, int k) {  // byte offset of (row, k..k+7) in an A tile
@@ -80,35 +79,54 @@ __device__ __forceinline__ bool rwait(uint64_t* b, uint32_t parity, volatile int
   }
 }
 
-// G' = (G diag(alpha_cell)) W^T for all rows: persistent CTAs over 128-row tiles.  W (bf16,
-// [out][in] = N x K, K-major) is loaded once by TMA; two threads stage each row of the A tile (one
-// K half each), scaled by its cell's alpha, into the 128-byte-swizzled K-major layout.  The
-// epilogue splits the columns the same way (warp w reads TMEM lanes 32 (w mod 4) onwards, column
-// half w / 4).  The accumulators are
-// double-buffered in TMEM so that the epilogue of tile k-1 (TMEM -> bf16 rows in global memory)
-// overlaps the MMAs of tile k.  Every wait is bounded (2 s): on timeout the kernel records
-// ISX_ERR_TIMEOUT, lets the MMAs in flight finish, frees TMEM and returns.
+// G' = (G diag(alpha_cell)) W^T for all rows: persistent, warp-specialised CTAs over 128-row tiles.
+//  - warp 5 streams the rows of G by TMA, one 64-wide K chunk of a tile per stage of an NS-stage
+//    ring, already in the 128-byte-swizzled K-major layout of the MMA's A operand;
+//  - warps 0-3 scale each staged chunk in place: thread t multiplies row t by its cell's alpha
+//    (rows past R stay the TMA's zero fill);
+//  - warp 4 loads W_j (bf16, [out][in] = N x K, K-major) once by TMA, owns TMEM and issues the MMAs;
+//  - warps 6-13 drain the two TMEM accumulators to bf16 rows of G' (lane group = warp mod 4,
+//    column half = (warp - 6) / 4).
+// Loads of tile k + 1 and the epilogue of tile k - 1 overlap the MMAs of tile k.  Every wait is
+// bounded (2 s): on timeout the kernel records ISX_ERR_TIMEOUT, lets the work in flight finish,
+// frees TMEM and returns.
+constexpr int kGT = 448;
 template <int W>
 __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ RowsGemmArgs args,
-                                                       const __grid_constant__ CUtensorMap wmap) {
+                                                       const __grid_constant__ CUtensorMap wmap,
+                                                       const __grid_constant__ CUtensorMap xmap) {
   using S = RowsSmem<W>;
-  constexpr int KC = S::KC;
+  constexpr int KC = S::KC, NS = S::NS;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* Wsm = base;
   uint8_t* Asm = Wsm + S::kWB;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(Asm + S::kAB);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + RB_COUNT);
+  uint64_t* araw = reinterpret_cast<uint64_t*>(Asm + NS * S::kAC);
+  uint64_t* afull = araw + NS;
+  uint64_t* aempty = afull + NS;
+  uint64_t* tfull = aempty + NS;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* wfull = tempty + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(wfull + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
-  const int t = threadIdx.x, warp = t >> 5;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int64_t ntiles = (args.R + kRT - 1) / kRT;
 
   if (t == 0) {
-    for (int i = 0; i < RB_COUNT; ++i) mbar_init(&bar[i], 1);
+    for (int i = 0; i < NS; ++i) {
+      mbar_init(&araw[i], 1);
+      mbar_init(&afull[i], kRT);
+      mbar_init(&aempty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 8);
+    }
+    mbar_init(wfull, 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 4) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
                  "n"(2 * W)
                  : "memory");
@@ -118,118 +136,134 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t id = idesc(W);
-  if (t == 0) {
-    mbar_expect_tx(&bar[RB_WFULL], (uint32_t)S::kWB);
-    for (int c = 0; c < KC; ++c) tma_load_2d(Wsm + (size_t)c * W * 128, &wmap, &bar[RB_WFULL], c * 64, 0);
-  }
-  bool ok = true;
-  int64_t prev = -1;
-  uint32_t k = 0;
 
-  const int row = t & (kRT - 1), half = t >> 7;
-  // every thread of a warp runs the (warp-collective) TMEM loads; rows past R are not stored
-  auto epilogue = [&](int64_t tile, uint32_t buf) {
-    const int64_t r = tile * kRT + row;
-    const uint32_t trow = tmem + buf * W + ((uint32_t)(32 * (warp & 3)) << 16);
-    const bool valid = r < args.R;
-    __nv_bfloat16* dst = nullptr;
-    if (valid) {
-      const int cell = args.rowcell[r];
-      dst = args.xout + (args.off_out[cell] + (r - args.off_in[cell])) * W;
-    }
-#pragma unroll 1
-    for (int c0 = half * (W / 2); c0 < (half + 1) * (W / 2); c0 += 32) {
-      float v[32];
-      tmem_ld32(trow + c0, v);
-      if (valid) {
-        uint32_t pk[16];
+  if (warp < 4) {
+    // ---- scale row t of every staged chunk by alpha of its cell, in place ----
+    uint32_t it = 0;
+    bool ok = true;
+    int64_t r_next = (int64_t)blockIdx.x * kRT + t;
+    int cell_next = (r_next < args.R) ? args.rowcell[r_next] : 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      const int64_t r = tile * kRT + t;
+      const bool valid = r < args.R;
+      const float4* al = reinterpret_cast<const float4*>(args.alpha + (size_t)cell_next * W);
+      // the next tile's row -> cell lookup is in flight while this tile is scaled
+      r_next = (tile + gridDim.x) * kRT + t;
+      cell_next = (tile + gridDim.x < ntiles && r_next < args.R) ? args.rowcell[r_next] : 0;
+      for (int c = 0; c < KC; ++c, ++it) {
+        const int sidx = it % NS;
+        // alpha of this chunk is loaded before the wait for the chunk's rows
+        float4 av[16];
+        if (valid) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-          pk[i] = *reinterpret_cast<const uint32_t*>(&h);
+          for (int g = 0; g < 16; ++g) av[g] = al[16 * c + g];
         }
-        uint4* d4 = reinterpret_cast<uint4*>(dst + c0);
+        if (!rwait(&araw[sidx], (it / NS) & 1, abort, args.status)) { ok = false; break; }
+        uint8_t* Ac = Asm + (size_t)sidx * S::kAC;
+        if (valid) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) d4[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+          for (int g = 0; g < 8; ++g) {
+            uint4* p = reinterpret_cast<uint4*>(Ac + roff(t, 8 * g));
+            const uint4 x = *p;
+            const float4 a0 = av[2 * g], a1 = av[2 * g + 1];
+            const __nv_bfloat162* xb = reinterpret_cast<const __nv_bfloat162*>(&x);
+            const float2 x0 = __bfloat1622float2(xb[0]), x1 = __bfloat1622float2(xb[1]);
+            const float2 x2 = __bfloat1622float2(xb[2]), x3 = __bfloat1622float2(xb[3]);
+            const __nv_bfloat162 p0 = __floats2bfloat162_rn(x0.x * a0.x, x0.y * a0.y);
+            const __nv_bfloat162 p1 = __floats2bfloat162_rn(x1.x * a0.z, x1.y * a0.w);
+            const __nv_bfloat162 p2 = __floats2bfloat162_rn(x2.x * a1.x, x2.y * a1.y);
+            const __nv_bfloat162 p3 = __floats2bfloat162_rn(x3.x * a1.z, x3.y * a1.w);
+            *p = make_uint4(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1),
+                            *reinterpret_cast<const uint32_t*>(&p2), *reinterpret_cast<const uint32_t*>(&p3));
+          }
+        }
+        fence_async_shared();
+        mbar_arrive(&afull[sidx]);
       }
     }
-  };
-
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
-    // the MMAs of the previous tile have read the A tile (and filled TMEM buffer (k-1) & 1)
-    if (k > 0) {
-      if (!rwait(&bar[RB_MMA], (k - 1) & 1, abort, args.status)) ok = false;
-    }
-    if (__syncthreads_or(!ok || *abort)) {
-      ok = false;
-      break;
-    }
-    tc_fence_after();
-    // ---- stage row r of the tile (this thread's K half), scaled by alpha of its cell ----
-    {
-      const int64_t r = tile * kRT + row;
-      if (r < args.R) {
-        const int cell = args.rowcell[r];
-        const uint4* src = reinterpret_cast<const uint4*>(args.xin + r * W);
-        const float4* al = reinterpret_cast<const float4*>(args.alpha + (size_t)cell * W);
-#pragma unroll 4
-        for (int g = half * (W / 16); g < (half + 1) * (W / 16); ++g) {
-          const uint4 x = src[g];
-          const float4 a0 = al[2 * g], a1 = al[2 * g + 1];
-          const __nv_bfloat162* xb = reinterpret_cast<const __nv_bfloat162*>(&x);
-          const float2 x0 = __bfloat1622float2(xb[0]), x1 = __bfloat1622float2(xb[1]);
-          const float2 x2 = __bfloat1622float2(xb[2]), x3 = __bfloat1622float2(xb[3]);
-          const __nv_bfloat162 p0 = __floats2bfloat162_rn(x0.x * a0.x, x0.y * a0.y);
-          const __nv_bfloat162 p1 = __floats2bfloat162_rn(x1.x * a0.z, x1.y * a0.w);
-          const __nv_bfloat162 p2 = __floats2bfloat162_rn(x2.x * a1.x, x2.y * a1.y);
-          const __nv_bfloat162 p3 = __floats2bfloat162_rn(x3.x * a1.z, x3.y * a1.w);
-          *reinterpret_cast<uint4*>(Asm + roff(row, 8 * g)) =
-              make_uint4(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1),
-                         *reinterpret_cast<const uint32_t*>(&p2), *reinterpret_cast<const uint32_t*>(&p3));
+  } else if (warp == 5) {
+    // ---- TMA producer of the row chunks ----
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        for (int c = 0; c < KC; ++c, ++it) {
+          const int sidx = it % NS;
+          if (!rwait(&aempty[sidx], ((it / NS) & 1) ^ 1, abort, args.status)) { ok = false; break; }
+          mbar_expect_tx(&araw[sidx], (uint32_t)S::kAC);
+          tma_load_2d(Asm + (size_t)sidx * S::kAC, &xmap, &araw[sidx], c * 64, (int)(tile * kRT));
         }
-      } else {
-        for (int g = half * (W / 16); g < (half + 1) * (W / 16); ++g)
-          *reinterpret_cast<uint4*>(Asm + roff(row, 8 * g)) = make_uint4(0, 0, 0, 0);
       }
     }
-    fence_async_shared();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    // ---- thread 0: the MMAs of this tile into TMEM buffer k & 1 ----
-    if (t == 0) {
-      bool wready = true;
-      if (k == 0) wready = rwait(&bar[RB_WFULL], 0, abort, args.status);
-      if (wready) {
-        const uint32_t dt = tmem + (k & 1) * W;
-        const uint32_t a0 = su32(Asm), w0 = su32(Wsm);
-#pragma unroll
-        for (int c = 0; c < KC; ++c)
+  } else if (warp == 4) {
+    // ---- W_j once, then the MMAs ----
+    if (lane == 0) {
+      mbar_expect_tx(wfull, (uint32_t)S::kWB);
+      for (int c = 0; c < KC; ++c) tma_load_2d(Wsm + (size_t)c * W * 128, &wmap, wfull, c * 64, 0);
+      const uint32_t id = idesc(W);
+      uint32_t it = 0, tt = 0;
+      bool ok = rwait(wfull, 0, abort, args.status);
+      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tt) {
+        const uint32_t b = tt & 1;
+        if (!rwait(&tempty[b], ((tt >> 1) & 1) ^ 1, abort, args.status)) break;
+        tc_fence_after();
+        const uint32_t dt = tmem + b * W;
+        for (int c = 0; c < KC; ++c, ++it) {
+          const int sidx = it % NS;
+          if (!rwait(&afull[sidx], (it / NS) & 1, abort, args.status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t a0 = su32(Asm + (size_t)sidx * S::kAC), w0 = su32(Wsm + (size_t)c * W * 128);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
-            mma_bf16(dt, sdesc(a0 + c * kRT * 128 + kk * 32), sdesc(w0 + c * W * 128 + kk * 32), id,
-                     (c > 0 || kk > 0) ? 1u : 0u);
-        mma_commit(&bar[RB_MMA]);
+            mma_bf16(dt, sdesc(a0 + kk * 32), sdesc(w0 + kk * 32), id, (c > 0 || kk > 0) ? 1u : 0u);
+          mma_commit(&aempty[sidx]);
+        }
+        if (ok) mma_commit(&tfull[b]);
       }
     }
-    // ---- epilogue of the previous tile (its MMAs completed before this tile's A was staged) ----
-    if (prev >= 0) epilogue(prev, (k - 1) & 1);
-    tc_fence_before();
-    prev = tile;
-  }
-  if (ok && prev >= 0) {
-    if (!rwait(&bar[RB_MMA], (k - 1) & 1, abort, args.status)) ok = false;
-    if (!__syncthreads_or(!ok || *abort)) {
+  } else {
+    // ---- epilogue: TMEM -> bf16 rows of G' ----
+    const int row = 32 * (warp & 3) + lane, half = (warp - 6) >> 2;
+    uint32_t tt = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tt) {
+      const uint32_t b = tt & 1;
+      const bool got = rwait(&tfull[b], (tt >> 1) & 1, abort, args.status);
+      if (!__all_sync(0xffffffffu, got)) break;
       tc_fence_after();
-      epilogue(prev, (k - 1) & 1);
+      const int64_t r = tile * kRT + row;
+      const bool valid = r < args.R;
+      __nv_bfloat16* dst = nullptr;
+      if (valid) {
+        const int cell = args.rowcell[r];
+        dst = args.xout + (args.off_out[cell] + (r - args.off_in[cell])) * W;
+      }
+      const uint32_t trow = tmem + b * W + ((uint32_t)(32 * (warp & 3)) << 16);
+#pragma unroll 1
+      for (int c0 = half * (W / 2); c0 < (half + 1) * (W / 2); c0 += 32) {
+        float v[32];
+        tmem_ld32(trow + c0, v);
+        if (valid) {
+          uint32_t pk[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+            pk[i] = *reinterpret_cast<const uint32_t*>(&h);
+          }
+          uint4* d4 = reinterpret_cast<uint4*>(dst + c0);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) d4[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
     }
   }
   tc_fence_before();
   __syncthreads();
   if (*abort)
     for (int i = 0; i < 1000; ++i) __nanosleep(1000);
-  if (warp == 0) {
+  if (warp == 4) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(2 * W) : "memory");
   }
@@ -259,42 +293,53 @@ __global__ void k_rows_input(CellSource src, int64_t first, int w, int clt, cons
 // ---- activation j: alpha, gamma, post-activation centre a; new-symbol count per cell; and (when
 //      AH is given) the A operand of the centre / input-row GEMM, rows 4 cell + q = a, alpha I_q,
 //      each split into bf16 high and low terms ----
-__device__ __forceinline__ void split_put(__nv_bfloat16* hi, __nv_bfloat16* lo, size_t i, float v) {
-  const __nv_bfloat16 h = __float2bfloat16_rn(v);
-  hi[i] = h;
-  lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
-}
-
-__global__ void k_rows_act(int w, int mode, int act, const float* C, const float* RAD, float* A, float* AL,
-                           float* GA, const int* cnt_in, int* cnt_out, const float* I, __nv_bfloat16* AH,
-                           __nv_bfloat16* ALO) {
-  __shared__ int wsum[32];
-  const int cell = blockIdx.x;
+// Several cells per block (w / 2 threads per cell, two adjacent neurons per thread, so the split
+// A operand goes out as bf16 pairs).
+__global__ void __launch_bounds__(256) k_rows_act(int w, int nc, int mode, int act, const float* C, const float* RAD,
+                                                  float* A, float* AL, float* GA, const int* cnt_in, int* cnt_out,
+                                                  const float* I, __nv_bfloat16* AH, __nv_bfloat16* ALO) {
+  __shared__ int mcount[8];
+  const int tpc = w / 2, cpb = blockDim.x / tpc;
+  const int sub = threadIdx.x / tpc, n = 2 * (threadIdx.x - sub * tpc);
+  const int64_t cell = (int64_t)blockIdx.x * cpb + sub;
+  if (threadIdx.x < 8) mcount[threadIdx.x] = 0;
+  __syncthreads();
+  const bool valid = sub < cpb && cell < nc;
   int m = 0;
-  for (int n = threadIdx.x; n < w; n += blockDim.x) {
+  if (valid) {
     const size_t o = (size_t)cell * w + n;
-    const Lin L = (mode == ISX_BOUND_CLT) ? act_clt(act, C[o], RAD[o]) : relu_sound(C[o], RAD[o], 0.0f, false);
-    A[o] = L.center;
-    AL[o] = L.alpha;
-    GA[o] = L.gamma;
-    m += (L.gamma != 0.0f);
+    const float2 c2 = *reinterpret_cast<const float2*>(C + o);
+    const float2 r2 = *reinterpret_cast<const float2*>(RAD + o);
+    Lin L[2];
+    L[0] = (mode == ISX_BOUND_CLT) ? act_clt(act, c2.x, r2.x) : relu_sound(c2.x, r2.x, 0.0f, false);
+    L[1] = (mode == ISX_BOUND_CLT) ? act_clt(act, c2.y, r2.y) : relu_sound(c2.y, r2.y, 0.0f, false);
+    *reinterpret_cast<float2*>(A + o) = make_float2(L[0].center, L[1].center);
+    *reinterpret_cast<float2*>(AL + o) = make_float2(L[0].alpha, L[1].alpha);
+    *reinterpret_cast<float2*>(GA + o) = make_float2(L[0].gamma, L[1].gamma);
+    m = (L[0].gamma != 0.0f) + (L[1].gamma != 0.0f);
     if (AH) {
+      auto put = [&](size_t i, float v0, float v1) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+        *reinterpret_cast<__nv_bfloat162*>(AH + i) = h;
+        *reinterpret_cast<__nv_bfloat162*>(ALO + i) = l;
+      };
       const size_t r0 = (size_t)cell * 4 * w + n;
-      split_put(AH, ALO, r0, L.center);
-      for (int d = 0; d < 3; ++d) split_put(AH, ALO, r0 + (size_t)(d + 1) * w, L.alpha * I[((size_t)cell * 3 + d) * w + n]);
+      put(r0, L[0].center, L[1].center);
+      for (int d = 0; d < 3; ++d) {
+        const float2 i2 = *reinterpret_cast<const float2*>(I + ((size_t)cell * 3 + d) * w + n);
+        put(r0 + (size_t)(d + 1) * w, L[0].alpha * i2.x, L[1].alpha * i2.y);
+      }
     }
   }
   if (!cnt_out) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
-  if (lane == 0) wsum[warp] = m;
+  // a warp never spans two cells (w / 2 >= 64 threads per cell)
+  if ((threadIdx.x & 31) == 0 && valid) atomicAdd(&mcount[sub], m);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int tot = 0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += wsum[i];
-    cnt_out[cell] = cnt_in[cell] + tot;
-  }
+  if (valid && threadIdx.x - sub * tpc == 0) cnt_out[cell] = cnt_in[cell] + mcount[sub];
 }
 
 // Exclusive scan of the per-cell row counts into int64 row offsets; total to *d_total.
@@ -590,6 +635,8 @@ __global__ void __launch_bounds__(256) k_rows_output(int w, int mode, const __nv
 
 template <int W>
 isx_status launch_rows_gemm(isx_inr inr, const RowsGemmArgs& a, const CUtensorMap& map, cudaStream_t st) {
+  CUtensorMap xmap;
+  ISX_TRY(tensor_map_bf16(&xmap, a.xin, W, (uint64_t)a.R, 64, kRT));
   const size_t smem = RowsSmem<W>::bytes();
   ISX_CUDA(cudaFuncSetAttribute(k_rows_gemm<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int sms = 148;
@@ -599,7 +646,7 @@ isx_status launch_rows_gemm(isx_inr inr, const RowsGemmArgs& a, const CUtensorMa
   per_sm = std::max(1, std::min(per_sm, 512 / (2 * W)));   // TMEM: 2 W columns per CTA
   const int64_t ntiles = (a.R + kRT - 1) / kRT;
   const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
-  k_rows_gemm<W><<<grid, kGT, smem, st>>>(a, map);
+  k_rows_gemm<W><<<grid, kGT, smem, st>>>(a, map, xmap);
   ISX_LAUNCH_CHECK("k_rows_gemm");
   return ISX_OK;
 }
@@ -681,6 +728,7 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
          rs[2] = {WS_R_RC0, WS_R_RC1};
     int cur = 0;
     int64_t R = 0;
+    const int act_blocks = (int)((nc + (512 / w) - 1) / (512 / w));   // 512 / w cells per block
     {
       prof::Scope ps(K_ROWS_AUX, st, 2.0 * nc * 3 * w, 0);
       k_rows_input<<<nc, std::min(w, 256), 0, st>>>(src, first, w, clt, inr->W[0], inr->b[0], C, I0, RAD);
@@ -696,7 +744,8 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
       int64_t* off_out = ws[os[nxt]].as<int64_t>();
       {
         prof::Scope ps(K_ROWS_ACT, st, 0, 0);
-        k_rows_act<<<nc, 256, 0, st>>>(w, (int)mode, inr->act, C, RAD, A, AL, GA, cnt_in, cnt_out, I0, AH, ALO);
+        k_rows_act<<<act_blocks, 256, 0, st>>>(w, nc, (int)mode, inr->act, C, RAD, A, AL, GA, cnt_in, cnt_out, I0,
+                                               AH, ALO);
         ISX_LAUNCH_CHECK("k_rows_act");
         k_rows_scan<<<1, 1024, 0, st>>>(cnt_out, nc, off_out, d_tot);
         ISX_LAUNCH_CHECK("k_rows_scan");
@@ -761,8 +810,8 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
     }
     {
       prof::Scope ps(K_ROWS_OUT, st, 2.0 * (double)(R + 3.0 * nc) * w, 0);
-      k_rows_act<<<nc, 256, 0, st>>>(w, (int)mode, inr->act, C, RAD, A, AL, GA, nullptr, nullptr, nullptr, nullptr,
-                                     nullptr);
+      k_rows_act<<<act_blocks, 256, 0, st>>>(w, nc, (int)mode, inr->act, C, RAD, A, AL, GA, nullptr, nullptr, nullptr,
+                                             nullptr, nullptr);
       ISX_LAUNCH_CHECK("k_rows_act");
       const int L = inr->n_layers - 1;
       k_rows_output<<<nc, 256, 0, st>>>(w, (int)mode, ws[xs[cur]].as<__nv_bfloat16>(), ws[os[cur]].as<int64_t>(),

@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--mode", default="clt", choices=["sound", "clt", "raua"])
     ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "bf16"])
     ap.add_argument("--k", type=float, default=3.0)
+    ap.add_argument("--eval-prec", default="auto", choices=["auto", "fp32", "bf16"],
+                    help="corner evaluation: bf16 = tensor cores with two-term bf16 operands (float32-class)")
     ap.add_argument("--max-level", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -107,13 +109,13 @@ def load_peaks():
         return {}
 
 
-def traffic_per_cell(kernel, src_file):
-    """ncu DRAM bytes per bounded cell recorded in profiles/traffic.json (from a capture of a smaller
-    launch of the same kernel), if the kernel source is unchanged since the capture."""
+def traffic_record(kernel, src_file):
+    """The ncu DRAM record of `kernel` in profiles/traffic.json (from a capture of a smaller launch of
+    the same kernel), if the kernel source is unchanged since the capture."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
         sha = hashlib.sha256(open(src_file, "rb").read()).hexdigest()[:16]
-        return rec["dram_bytes_per_cell"] if rec.get("src_sha") == sha else None
+        return rec if rec.get("src_sha") == sha else None
     except Exception:
         return None
 
@@ -343,7 +345,8 @@ def main():
     net = pkg.Inr(layers)
     if prec == "auto":
         prec = "bf16" if pkg._lib.load() and _bf16_ok(net, pkg) else "fp32"
-    kw = dict(mode=args.mode, k=args.k, prec=prec, inflate=(args.mode == "sound"))
+    eval_prec = args.eval_prec if args.eval_prec != "auto" else ("bf16" if prec == "bf16" else "fp32")
+    kw = dict(mode=args.mode, k=args.k, prec=prec, inflate=(args.mode == "sound"), eval_prec=eval_prec)
     bufs = {}
     res = net.extract(L, isos, buffers=bufs, active_cap=1 << 22, tri_cap=1 << 24, **kw)   # sizes the buffers
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
@@ -415,22 +418,39 @@ def main():
                "ms_per_step": e2e_ms / steps_e2e, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     peaks = load_peaks()
-    bound_kernels = ["bound_tc", "gemm_fp32"]
+    # the roofline of the dominant bound kernel: the row-batched tcgen05 GEMM (BF16, default), the
+    # per-cell tcgen05 kernel (BF16 with inflation) or the float32 coefficient GEMM
+    bound_kernels = ["rows_gemm", "bound_tc", "gemm_fp32"]
     dom = max(bound_kernels, key=lambda k: stats.get(k, {}).get("ms", 0.0))
     ds = stats[dom]
-    if dom == "bound_tc":
-        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    csrc = os.path.join(ROOT, "paper_2402_13861_gb300", "csrc")
+    secs = ds["ms"] / 1e3 if ds["ms"] > 0 else float("inf")
+    tc_peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    hbm_peak = peaks.get("hbm_gbs", 6674.2)
+    if dom == "rows_gemm":
+        # arithmetic intensity 2 R w^2 / (4 R w bytes) = w / 2 FLOP/B: below the ridge, HBM-bound
+        ai = ds["flops"] / max(ds["bytes"], 1.0)
+        if ai * hbm_peak / 1e3 < tc_peak:
+            roof = {"bound": "hbm", "unit": "GB/s", "peak_source": "measured hbm_gbs",
+                    "arithmetic_intensity": ai, "achieved_tflops": ds["flops"] / secs / 1e12}
+            achieved, peak = ds["bytes"] / secs / 1e9, hbm_peak
+        else:
+            roof = {"bound": "tensor", "unit": "TFLOP/s", "peak_source": "measured bf16_tflops_sustained"}
+            achieved, peak = ds["flops"] / secs / 1e12, tc_peak
+        rec = traffic_record(dom, os.path.join(csrc, "bound_rows.cu"))
+        tr = rec["dram_per_alg_byte"] * ds["bytes"] / max(ds["launches"], 1) if rec else None
+    elif dom == "bound_tc":
         roof = {"bound": "tensor", "unit": "TFLOP/s", "peak_source": "measured bf16_tflops_sustained"}
-        src = os.path.join(ROOT, "paper_2402_13861_gb300", "csrc", "bound_tc.cu")
+        achieved, peak = ds["flops"] / secs / 1e12, tc_peak
+        rec = traffic_record(dom, os.path.join(csrc, "bound_tc.cu"))
+        tr = rec["dram_bytes_per_cell"] * cells_local / max(ds["launches"], 1) if rec else None
     else:
         # float32 FMA issue rate: 152 SMs x 128 lanes x 2 FLOP x max SM clock
         mhz = peaks.get("sm_max_mhz", 2070.0)
         peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
         roof = {"bound": "alu", "unit": "TFLOP/s", "peak_source": "152 SM x 128 FP32 lanes x 2 x max SM clock"}
-        src = os.path.join(ROOT, "paper_2402_13861_gb300", "csrc", "bound_fp32.cu")
-    achieved = ds["flops"] / (ds["ms"] / 1e3) / 1e12 if ds["ms"] > 0 else 0.0
-    bpc = traffic_per_cell(dom, src)
-    tr = bpc * cells_local / max(ds["launches"], 1) if bpc is not None else None
+        achieved = ds["flops"] / secs / 1e12
+        tr = None
     roof.update({"kernel": dom, "achieved": achieved, "peak": peak, "frac": achieved / peak,
                  "launches": ds["launches"], "avg_launch_ms": ds["ms"] / max(ds["launches"], 1),
                  "traffic": tr})
@@ -443,7 +463,8 @@ def main():
             "dtype": "bf16" if prec == "bf16" else "f32", "data": "synthetic",
             "config": {"workload": f"scientific-field {1 << L}^3: 3->256x5->1 ReLU INR fitted to 256 anisotropic "
                                    f"Gaussians + sine, 8 isos over the 10-90% quantiles", "mode": args.mode,
-                       "k": args.k, "precision": prec, "inflate": kw["inflate"], "max_level": L,
+                       "k": args.k, "precision": prec, "eval_precision": eval_prec, "inflate": kw["inflate"],
+                       "max_level": L,
                        "l2": "512 MB buffer written between timed steps", "parallelism": f"replicas x{world}"},
             "phase_ms": {"acp": phases[0] / args.steps, "inr": phases[1] / args.steps, "mc": phases[2] / args.steps},
             "cells_bounded_per_step": cells / args.steps / world, "n_active": res["n_active"],

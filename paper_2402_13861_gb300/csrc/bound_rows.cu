@@ -227,9 +227,7 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
     uint32_t tt = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tt) {
       const uint32_t b = tt & 1;
-      const bool got = rwait(&tfull[b], (tt >> 1) & 1, abort, args.status);
-      if (!__all_sync(0xffffffffu, got)) break;
-      tc_fence_after();
+      // the destination row (a dependent chain of three loads) is resolved while the MMAs run
       const int64_t r = tile * kRT + row;
       const bool valid = r < args.R;
       __nv_bfloat16* dst = nullptr;
@@ -237,6 +235,9 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
         const int cell = args.rowcell[r];
         dst = args.xout + (args.off_out[cell] + (r - args.off_in[cell])) * W;
       }
+      const bool got = rwait(&tfull[b], (tt >> 1) & 1, abort, args.status);
+      if (!__all_sync(0xffffffffu, got)) break;
+      tc_fence_after();
       const uint32_t trow = tmem + b * W + ((uint32_t)(32 * (warp & 3)) << 16);
 #pragma unroll 1
       for (int c0 = half * (W / 2); c0 < (half + 1) * (W / 2); c0 += 32) {
@@ -546,14 +547,21 @@ __global__ void __launch_bounds__(kST, 1) k_rows_split(const __grid_constant__ R
   }
 }
 
-// ---- reductions of z_{j+1} per (cell, neuron): r = sum |x| or sigma = sqrt(sum x^2) over the
-//      cell's G rows and its three input rows (compensated); two neurons per thread ----
-__global__ void k_rows_reduce(int w, int sq, const __nv_bfloat16* X, const int64_t* off, const int* cnt,
-                              const float* I, float* RAD) {
+// ---- reductions of z_{j+1} per (cell, neuron): r = sum |x| or sigma = sqrt(sum x^2) over the cell's G
+//      rows and its three input rows (compensated), two neurons per thread; fused with activation
+//      j+1 (alpha, gamma, a, and, when AH is given, the split A operand of the next centre /
+//      input-row GEMM and the next row count cnt_next = cnt + #(gamma != 0)) ----
+__global__ void k_rows_reduce_act(int w, int mode, int act, const __nv_bfloat16* X, const int64_t* off,
+                                  const int* cnt, const float* I, const float* C, float* A, float* AL, float* GA,
+                                  int* cnt_next, __nv_bfloat16* AH, __nv_bfloat16* ALO) {
+  __shared__ int wsum[32];
   const int cell = blockIdx.x;
+  const bool sq = mode == ISX_BOUND_CLT;
   const int64_t o0 = off[cell];
   const int rows = cnt[cell];
+  int m = 0;
   for (int n2 = threadIdx.x; n2 < w / 2; n2 += blockDim.x) {
+    const int n = 2 * n2;
     float s0 = 0.0f, s1 = 0.0f, e0 = 0.0f, e1 = 0.0f;
     auto add = [&](float& s, float& e, float x) {
       const float v = sq ? x * x : fabsf(x);
@@ -561,9 +569,11 @@ __global__ void k_rows_reduce(int w, int sq, const __nv_bfloat16* X, const int64
       e = (tt - s) - y;
       s = tt;
     };
+    float2 iv[3];
     for (int d = 0; d < 3; ++d) {
-      add(s0, e0, I[(size_t)cell * 3 * w + d * w + 2 * n2]);
-      add(s1, e1, I[(size_t)cell * 3 * w + d * w + 2 * n2 + 1]);
+      iv[d] = *reinterpret_cast<const float2*>(I + ((size_t)cell * 3 + d) * w + n);
+      add(s0, e0, iv[d].x);
+      add(s1, e1, iv[d].y);
     }
     const __nv_bfloat162* src = reinterpret_cast<const __nv_bfloat162*>(X + o0 * w) + n2;
     for (int r = 0; r < rows; ++r) {
@@ -571,8 +581,38 @@ __global__ void k_rows_reduce(int w, int sq, const __nv_bfloat16* X, const int64
       add(s0, e0, x.x);
       add(s1, e1, x.y);
     }
-    RAD[(size_t)cell * w + 2 * n2] = sq ? sqrtf(s0) : s0;
-    RAD[(size_t)cell * w + 2 * n2 + 1] = sq ? sqrtf(s1) : s1;
+    const float r0 = sq ? sqrtf(s0) : s0, r1 = sq ? sqrtf(s1) : s1;
+    const size_t o = (size_t)cell * w + n;
+    const float2 c2 = *reinterpret_cast<const float2*>(C + o);
+    const Lin L0 = sq ? act_clt(act, c2.x, r0) : relu_sound(c2.x, r0, 0.0f, false);
+    const Lin L1 = sq ? act_clt(act, c2.y, r1) : relu_sound(c2.y, r1, 0.0f, false);
+    *reinterpret_cast<float2*>(A + o) = make_float2(L0.center, L1.center);
+    *reinterpret_cast<float2*>(AL + o) = make_float2(L0.alpha, L1.alpha);
+    *reinterpret_cast<float2*>(GA + o) = make_float2(L0.gamma, L1.gamma);
+    m += (L0.gamma != 0.0f) + (L1.gamma != 0.0f);
+    if (AH) {
+      auto put = [&](size_t i, float v0, float v1) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+        *reinterpret_cast<__nv_bfloat162*>(AH + i) = h;
+        *reinterpret_cast<__nv_bfloat162*>(ALO + i) = l;
+      };
+      const size_t q0 = (size_t)cell * 4 * w + n;
+      put(q0, L0.center, L1.center);
+      for (int d = 0; d < 3; ++d) put(q0 + (size_t)(d + 1) * w, L0.alpha * iv[d].x, L1.alpha * iv[d].y);
+    }
+  }
+  if (!cnt_next) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+  if (lane == 0) wsum[warp] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tot = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += wsum[i];
+    cnt_next[cell] = rows + tot;
   }
 }
 
@@ -736,6 +776,13 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
     ISX_LAUNCH_CHECK("k_rows_input");
     ISX_CUDA(cudaMemsetAsync(ws[cs[0]].ptr, 0, (size_t)nc * sizeof(int), st));
     ISX_CUDA(cudaMemsetAsync(ws[os[0]].ptr, 0, (size_t)nc * sizeof(int64_t), st));
+    {
+      // activation 1 (later activations are fused with the reductions of their pre-activation)
+      prof::Scope ps(K_ROWS_ACT, st, 0, 0);
+      k_rows_act<<<act_blocks, 256, 0, st>>>(w, nc, (int)mode, inr->act, C, RAD, A, AL, GA, ws[cs[0]].as<int>(),
+                                             ws[cs[1]].as<int>(), I0, H > 1 ? AH : nullptr, ALO);
+      ISX_LAUNCH_CHECK("k_rows_act");
+    }
     for (int j = 1; j <= H - 1; ++j) {
       const int nxt = cur ^ 1;
       int* cnt_in = ws[cs[cur]].as<int>();
@@ -744,9 +791,6 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
       int64_t* off_out = ws[os[nxt]].as<int64_t>();
       {
         prof::Scope ps(K_ROWS_ACT, st, 0, 0);
-        k_rows_act<<<act_blocks, 256, 0, st>>>(w, nc, (int)mode, inr->act, C, RAD, A, AL, GA, cnt_in, cnt_out, I0,
-                                               AH, ALO);
-        ISX_LAUNCH_CHECK("k_rows_act");
         k_rows_scan<<<1, 1024, 0, st>>>(cnt_out, nc, off_out, d_tot);
         ISX_LAUNCH_CHECK("k_rows_scan");
       }
@@ -800,9 +844,13 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
         }
       }
       {
+        // reductions of z_{j+1} and activation j+1; its row count goes to the buffer of X_j's counts
         prof::Scope ps(K_ROWS_REDUCE, st, 0, 2.0 * (double)Rn * w);
-        k_rows_reduce<<<nc, std::min(w / 2, 128), 0, st>>>(w, clt, Xout, off_out, cnt_out, I1, RAD);
-        ISX_LAUNCH_CHECK("k_rows_reduce");
+        const bool last = j == H - 1;
+        k_rows_reduce_act<<<nc, std::min(w / 2, 128), 0, st>>>(w, (int)mode, inr->act, Xout, off_out, cnt_out, I1, C, A,
+                                                              AL, GA, last ? nullptr : cnt_in, last ? nullptr : AH,
+                                                              ALO);
+        ISX_LAUNCH_CHECK("k_rows_reduce_act");
       }
       std::swap(I0, I1);
       cur = nxt;
@@ -810,9 +858,6 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
     }
     {
       prof::Scope ps(K_ROWS_OUT, st, 2.0 * (double)(R + 3.0 * nc) * w, 0);
-      k_rows_act<<<act_blocks, 256, 0, st>>>(w, nc, (int)mode, inr->act, C, RAD, A, AL, GA, nullptr, nullptr, nullptr,
-                                             nullptr, nullptr);
-      ISX_LAUNCH_CHECK("k_rows_act");
       const int L = inr->n_layers - 1;
       k_rows_output<<<nc, 256, 0, st>>>(w, (int)mode, ws[xs[cur]].as<__nv_bfloat16>(), ws[os[cur]].as<int64_t>(),
                                         ws[cs[cur]].as<int>(), I0, A, AL, GA, inr->W[L], inr->hb[L][0], first,

@@ -122,10 +122,11 @@ def traffic_record(kernel, src_file):
 
 def extraction_forms(pkg, net, L, isos, plain, plain_ms, mode, k, prec):
     """End-to-end time of the other extraction forms on the same INR and isos, and the crossing
-    (cell, iso) pairs of the dense extraction each form misses: bounding stopped at level 6 with
-    tensor-core corner values, the proposer-assisted form (committed proposer), dense extraction
+    (cell, iso) pairs of the dense extraction each form misses: the per-cell tensor-core bound kernel,
+    bounding stopped at level 6, the proposer-assisted form (committed proposer), dense extraction
     (FP32 and tensor-core evaluation), sound RA-Fixed bounds, and the k-d tree against the octree
-    one level lower.  Each form runs once after a warm-up of the same call."""
+    one level lower (tensor-core corner values throughout).  Each form runs once after a warm-up of
+    the same call."""
     import torch
     from paper_2402_13861_gb300 import proposer as gp
     from paper_2402_13861_gb300.train_proposer import missed
@@ -159,12 +160,17 @@ def extraction_forms(pkg, net, L, isos, plain, plain_ms, mode, k, prec):
     mp, tot = missed(plain["codes"], plain["masks"], cross)
     out["plain"] = {"ms": plain_ms, "cells_bounded": int(sum(plain["cells_bounded"])), "missed_pairs": mp,
                     "missed_rate": mp / max(tot, 1)}
+    # the per-cell persistent tcgen05 bound kernel on the same extraction
+    os.environ["ISX_BF16_ROWS"] = "0"
+    r, ms = timed(mode=mode, k=k, prec=prec, eval_prec="bf16")
+    del os.environ["ISX_BF16_ROWS"]
+    out["per_cell_tc_kernel"] = {"ms": ms, "cells_bounded": int(sum(r["cells_bounded"])), "n_active": r["n_active"]}
     r, ms = timed(mode=mode, k=k, prec=prec, bound_stop_level=6, eval_prec="bf16")
     m, _ = missed(r["codes"], r["masks"], cross)
     out["bound_to_level6_tc_eval"] = {"ms": ms, "cells_bounded": int(sum(r["cells_bounded"])),
                                       "n_active": r["n_active"], "missed_pairs": m, "missed_rate": m / max(tot, 1)}
     prop, meta = gp.load(os.path.join(ROOT, "synth", "data", "proposer.npz"))
-    r, ms = timed(mode=mode, k=k, prec=prec, proposer=prop, proposer_level=meta["proposer_level"],
+    r, ms = timed(mode=mode, k=k, prec=prec, eval_prec="bf16", proposer=prop, proposer_level=meta["proposer_level"],
                   tau_lo=meta["tau_lo"], tau_hi=meta["tau_hi"])
     m, _ = missed(r["codes"], r["masks"], cross)
     out["proposer"] = {"ms": ms, "cells_bounded": int(sum(r["cells_bounded"])), "missed_pairs": m,
@@ -180,7 +186,7 @@ def extraction_forms(pkg, net, L, isos, plain, plain_ms, mode, k, prec):
                            "missed_pairs": m, "missed_rate": m / max(tot, 1)}
     # Algorithm 1's k-d tree (widest-side bisection) against the octree, one level lower (256^3)
     for name, kd in (("octree_256", False), ("kd_tree_256", True)):
-        r, ms = timed_level(L - 1, mode=mode, k=k, prec=prec, kd_tree=kd)
+        r, ms = timed_level(L - 1, mode=mode, k=k, prec=prec, eval_prec="bf16", kd_tree=kd)
         out[name] = {"ms": ms, "cells_bounded": int(sum(r["cells_bounded"])), "n_active": r["n_active"]}
     return out
 
@@ -215,7 +221,13 @@ def batched_form(pkg, mode, k):
     bufs = [dict() for _ in nets]
     for net, p, bf in zip(nets, params, bufs):
         net.extract(buffers=bf, **p)                            # warm-up, sizes the buffers
+    _, seq_rows_ms = ev_ms(lambda: [net.extract(buffers=bf, **p) for net, p, bf in zip(nets, params, bufs)])
+    # the batch runs the per-cell tensor-core kernel: its sequential counterpart takes the same kernel
+    os.environ["ISX_BF16_ROWS"] = "0"
+    for net, p, bf in zip(nets, params, bufs):
+        net.extract(buffers=bf, **p)
     singles, seq_ms = ev_ms(lambda: [net.extract(buffers=bf, **p) for net, p, bf in zip(nets, params, bufs)])
+    del os.environ["ISX_BF16_ROWS"]
     batch = pkg.Batch(nets, params, use_graph=True)
     batch.run()                                                 # sized run
     batch.run()                                                 # capture and first replay
@@ -225,7 +237,8 @@ def batched_form(pkg, mode, k):
     for net in nets:
         net.close()
     return {"entries": len(specs), "shapes": [f"w{w}xH{H}@{1 << L}^3" for w, H, L, _ in specs], "isos_each": 16,
-            "sequential_ms": seq_ms, "batched_graph_ms": batch_ms, "same_meshes": bool(same),
+            "sequential_per_cell_kernel_ms": seq_ms, "batched_graph_ms": batch_ms, "same_meshes": bool(same),
+            "sequential_row_batched_ms": seq_rows_ms,
             "cells_bounded_sequential": int(sum(sum(s["cells_bounded"]) for s in singles))}
 
 

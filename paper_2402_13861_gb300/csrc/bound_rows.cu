@@ -270,35 +270,15 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
   }
 }
 
-// ---- layer 0: centre c_1, the three input rows I_1 = diag(h) W_0^T, and their reduction ----
-__global__ void k_rows_input(CellSource src, int64_t first, int w, int clt, const float* __restrict__ W0,
-                             const float* __restrict__ b0, float* C, float* I, float* RAD) {
-  const int cell = blockIdx.x;
-  float xc[3], h[3];
-  cell_box(src, first + cell, 0, xc, h);
-  if (clt)
-    for (int d = 0; d < 3; ++d) h[d] *= 0.57735026918962576f;   // uniform on [-h, h] has std h / sqrt 3
-  for (int n = threadIdx.x; n < w; n += blockDim.x) {
-    const float w0 = W0[3 * n], w1 = W0[3 * n + 1], w2 = W0[3 * n + 2];
-    const float c = fmaf(w2, xc[2], fmaf(w1, xc[1], fmaf(w0, xc[0], b0[n])));
-    const float i0 = h[0] * w0, i1 = h[1] * w1, i2 = h[2] * w2;
-    const size_t o = (size_t)cell * w + n;
-    C[o] = c;
-    I[(size_t)cell * 3 * w + n] = i0;
-    I[(size_t)cell * 3 * w + w + n] = i1;
-    I[(size_t)cell * 3 * w + 2 * w + n] = i2;
-    RAD[o] = clt ? sqrtf(i0 * i0 + i1 * i1 + i2 * i2) : fabsf(i0) + fabsf(i1) + fabsf(i2);
-  }
-}
-
-// ---- activation j: alpha, gamma, post-activation centre a; new-symbol count per cell; and (when
-//      AH is given) the A operand of the centre / input-row GEMM, rows 4 cell + q = a, alpha I_q,
-//      each split into bf16 high and low terms ----
-// Several cells per block (w / 2 threads per cell, two adjacent neurons per thread, so the split
-// A operand goes out as bf16 pairs).
-__global__ void __launch_bounds__(256) k_rows_act(int w, int nc, int mode, int act, const float* C, const float* RAD,
-                                                  float* A, float* AL, float* GA, const int* cnt_in, int* cnt_out,
-                                                  const float* I, __nv_bfloat16* AH, __nv_bfloat16* ALO) {
+// ---- layer 0 and activation 1: centre c_1, the three input rows I_1 = diag(h) W_0^T (written: the
+//      output layer of a one-hidden-layer net reads them), their reduction, the linearisation, the
+//      split A operand of the first centre / input-row GEMM (when AH is given) and the row count of
+//      the first stored block.  w / 2 threads per cell, two adjacent neurons per thread. ----
+__global__ void __launch_bounds__(256) k_rows_input_act(CellSource src, int64_t first, int nc, int w, int mode,
+                                                        int act, const float* __restrict__ W0,
+                                                        const float* __restrict__ b0, float* I, float* A, float* AL,
+                                                        float* GA, int* cnt_out, __nv_bfloat16* AH,
+                                                        __nv_bfloat16* ALO) {
   __shared__ int mcount[8];
   const int tpc = w / 2, cpb = blockDim.x / tpc;
   const int sub = threadIdx.x / tpc, n = 2 * (threadIdx.x - sub * tpc);
@@ -306,41 +286,51 @@ __global__ void __launch_bounds__(256) k_rows_act(int w, int nc, int mode, int a
   if (threadIdx.x < 8) mcount[threadIdx.x] = 0;
   __syncthreads();
   const bool valid = sub < cpb && cell < nc;
+  const bool clt = mode == ISX_BOUND_CLT;
   int m = 0;
   if (valid) {
-    const size_t o = (size_t)cell * w + n;
-    const float2 c2 = *reinterpret_cast<const float2*>(C + o);
-    const float2 r2 = *reinterpret_cast<const float2*>(RAD + o);
+    float xc[3], h[3];
+    cell_box(src, first + cell, 0, xc, h);
+    if (clt)
+      for (int d = 0; d < 3; ++d) h[d] *= 0.57735026918962576f;   // uniform on [-h, h] has std h / sqrt 3
     Lin L[2];
-    L[0] = (mode == ISX_BOUND_CLT) ? act_clt(act, c2.x, r2.x) : relu_sound(c2.x, r2.x, 0.0f, false);
-    L[1] = (mode == ISX_BOUND_CLT) ? act_clt(act, c2.y, r2.y) : relu_sound(c2.y, r2.y, 0.0f, false);
+    float iv[2][3];
+    for (int e = 0; e < 2; ++e) {
+      const int nn = n + e;
+      const float w0 = W0[3 * nn], w1 = W0[3 * nn + 1], w2 = W0[3 * nn + 2];
+      const float c = fmaf(w2, xc[2], fmaf(w1, xc[1], fmaf(w0, xc[0], b0[nn])));
+      iv[e][0] = h[0] * w0;
+      iv[e][1] = h[1] * w1;
+      iv[e][2] = h[2] * w2;
+      const float rad = clt ? sqrtf(iv[e][0] * iv[e][0] + iv[e][1] * iv[e][1] + iv[e][2] * iv[e][2])
+                            : fabsf(iv[e][0]) + fabsf(iv[e][1]) + fabsf(iv[e][2]);
+      L[e] = clt ? act_clt(act, c, rad) : relu_sound(c, rad, 0.0f, false);
+    }
+    const size_t o = (size_t)cell * w + n;
+    for (int d = 0; d < 3; ++d)
+      *reinterpret_cast<float2*>(I + ((size_t)cell * 3 + d) * w + n) = make_float2(iv[0][d], iv[1][d]);
     *reinterpret_cast<float2*>(A + o) = make_float2(L[0].center, L[1].center);
     *reinterpret_cast<float2*>(AL + o) = make_float2(L[0].alpha, L[1].alpha);
     *reinterpret_cast<float2*>(GA + o) = make_float2(L[0].gamma, L[1].gamma);
     m = (L[0].gamma != 0.0f) + (L[1].gamma != 0.0f);
     if (AH) {
       auto put = [&](size_t i, float v0, float v1) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-        const float2 hf = __bfloat1622float2(h);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
-        *reinterpret_cast<__nv_bfloat162*>(AH + i) = h;
-        *reinterpret_cast<__nv_bfloat162*>(ALO + i) = l;
+        const __nv_bfloat162 hh = __floats2bfloat162_rn(v0, v1);
+        const float2 hf = __bfloat1622float2(hh);
+        const __nv_bfloat162 ll = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+        *reinterpret_cast<__nv_bfloat162*>(AH + i) = hh;
+        *reinterpret_cast<__nv_bfloat162*>(ALO + i) = ll;
       };
       const size_t r0 = (size_t)cell * 4 * w + n;
       put(r0, L[0].center, L[1].center);
-      for (int d = 0; d < 3; ++d) {
-        const float2 i2 = *reinterpret_cast<const float2*>(I + ((size_t)cell * 3 + d) * w + n);
-        put(r0 + (size_t)(d + 1) * w, L[0].alpha * i2.x, L[1].alpha * i2.y);
-      }
+      for (int d = 0; d < 3; ++d) put(r0 + (size_t)(d + 1) * w, L[0].alpha * iv[0][d], L[1].alpha * iv[1][d]);
     }
   }
-  if (!cnt_out) return;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
-  // a warp never spans two cells (w / 2 >= 64 threads per cell)
-  if ((threadIdx.x & 31) == 0 && valid) atomicAdd(&mcount[sub], m);
+  if ((threadIdx.x & 31) == 0 && valid) atomicAdd(&mcount[sub], m);   // a warp never spans two cells
   __syncthreads();
-  if (valid && threadIdx.x - sub * tpc == 0) cnt_out[cell] = cnt_in[cell] + mcount[sub];
+  if (valid && threadIdx.x - sub * tpc == 0) cnt_out[cell] = mcount[sub];
 }
 
 // Exclusive scan of the per-cell row counts into int64 row offsets; total to *d_total.
@@ -723,7 +713,6 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
     return ISX_ERR_UNSUPPORTED;
   }
   const int w = inr->w, H = inr->H;
-  const int clt = mode == ISX_BOUND_CLT;
   auto& ws = inr->ws;
   ISX_TRY(ws[WS_TC_STATUS].ensure(64, "tc status"));
   ISX_TRY(ws[WS_R_TOT].ensure(64, "row total"));
@@ -746,7 +735,6 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
     const size_t cw = (size_t)nc * w * sizeof(float);
     ISX_TRY(ws[WS_C].ensure(cw, "rows centre"));
     ISX_TRY(ws[WS_R_A].ensure(cw, "rows post-activation centre"));
-    ISX_TRY(ws[WS_RAD].ensure(cw, "rows radius"));
     ISX_TRY(ws[WS_ALPHA].ensure(cw, "rows alpha"));
     ISX_TRY(ws[WS_GAMMA].ensure(cw, "rows gamma"));
     ISX_TRY(ws[WS_R_I0].ensure(3 * cw, "rows input rows"));
@@ -757,7 +745,6 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
     for (Slot s : {WS_R_OFF0, WS_R_OFF1}) ISX_TRY(ws[s].ensure((size_t)nc * sizeof(int64_t), "rows offsets"));
     float* C = ws[WS_C].as<float>();
     float* A = ws[WS_R_A].as<float>();
-    float* RAD = ws[WS_RAD].as<float>();
     float* AL = ws[WS_ALPHA].as<float>();
     float* GA = ws[WS_GAMMA].as<float>();
     float* I0 = ws[WS_R_I0].as<float>();
@@ -770,19 +757,13 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
     int64_t R = 0;
     const int act_blocks = (int)((nc + (512 / w) - 1) / (512 / w));   // 512 / w cells per block
     {
-      prof::Scope ps(K_ROWS_AUX, st, 2.0 * nc * 3 * w, 0);
-      k_rows_input<<<nc, std::min(w, 256), 0, st>>>(src, first, w, clt, inr->W[0], inr->b[0], C, I0, RAD);
+      prof::Scope ps(K_ROWS_ACT, st, 2.0 * nc * 3 * w, 0);
+      k_rows_input_act<<<act_blocks, 256, 0, st>>>(src, first, nc, w, (int)mode, inr->act, inr->W[0], inr->b[0], I0,
+                                                   A, AL, GA, ws[cs[1]].as<int>(), H > 1 ? AH : nullptr, ALO);
+      ISX_LAUNCH_CHECK("k_rows_input_act");
     }
-    ISX_LAUNCH_CHECK("k_rows_input");
     ISX_CUDA(cudaMemsetAsync(ws[cs[0]].ptr, 0, (size_t)nc * sizeof(int), st));
     ISX_CUDA(cudaMemsetAsync(ws[os[0]].ptr, 0, (size_t)nc * sizeof(int64_t), st));
-    {
-      // activation 1 (later activations are fused with the reductions of their pre-activation)
-      prof::Scope ps(K_ROWS_ACT, st, 0, 0);
-      k_rows_act<<<act_blocks, 256, 0, st>>>(w, nc, (int)mode, inr->act, C, RAD, A, AL, GA, ws[cs[0]].as<int>(),
-                                             ws[cs[1]].as<int>(), I0, H > 1 ? AH : nullptr, ALO);
-      ISX_LAUNCH_CHECK("k_rows_act");
-    }
     for (int j = 1; j <= H - 1; ++j) {
       const int nxt = cur ^ 1;
       int* cnt_in = ws[cs[cur]].as<int>();

@@ -450,7 +450,7 @@ def main():
         else:
             roof = {"bound": "tensor", "unit": "TFLOP/s", "peak_source": "measured bf16_tflops_sustained"}
             achieved, peak = ds["flops"] / secs / 1e12, tc_peak
-        rec = traffic_record(dom, os.path.join(csrc, "bound_rows.cu"))
+        rec = traffic_record(dom, os.path.join(csrc, "rows_gemm.cu"))
         tr = rec["dram_per_alg_byte"] * ds["bytes"] / max(ds["launches"], 1) if rec else None
     elif dom == "bound_tc":
         roof = {"bound": "tensor", "unit": "TFLOP/s", "peak_source": "measured bf16_tflops_sustained"}

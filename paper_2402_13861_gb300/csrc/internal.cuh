@@ -133,7 +133,7 @@ __host__ __device__ __forceinline__ bool sound_readout(int mode) {
 
 // Row-batched tensor-core path: layer-synchronous over a chunk of cells, noise-symbol rows with a
 // zero coefficient dropped, alpha applied on the A side so that one weight operand serves all
-// cells (bound_rows.cu).  Hidden widths 128 and 256, no inflation.
+// cells (bound_rows.cu).  Hidden widths 64, 128 and 256, no inflation.
 isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bound_mode mode, float* d_center,
                            float* d_spread, cudaStream_t st);
 bool rows_supported(isx_inr inr, isx_bound_mode mode, int inflate);

@@ -1,0 +1,53 @@
+// Shared pieces of the row-batched tensor-core bound path (bound_rows.cu, rows_gemm.cu): the tile
+// shape, the swizzled A-tile layout, the bounded mbarrier wait and the row GEMM's interface.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace isx {
+namespace rows {
+
+constexpr int kRT = 128;                        // rows per MMA tile
+constexpr uint64_t kRowsWaitNs = 2000000000ull;
+
+struct RowsGemmArgs {
+  const __nv_bfloat16* xin;                     // [R][W] rows of z_j
+  const int* rowcell;                           // [R] cell of every row
+  const int64_t* off_in;                        // [nc] first row of each cell in xin
+  const int64_t* off_out;                       // [nc] first row of each cell in xout
+  const float* alpha;                           // [nc][W]
+  int64_t R;
+  __nv_bfloat16* xout;                          // [R'][W] rows of z_{j+1}
+  int* status;
+};
+
+__device__ __forceinline__ uint32_t roff(int row, int k) {  // byte offset of (row, k..k+7) in an A tile
+  return (uint32_t)((k >> 6) * kRT * 128 + row * 128 + ((((k & 63) >> 3) ^ (row & 7)) << 4));
+}
+
+__device__ __forceinline__ bool rwait(uint64_t* b, uint32_t parity, volatile int* abort, int* status) {
+  if (tc::mbar_try(b, parity)) return true;
+  const uint64_t t0 = tc::global_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (tc::mbar_try(b, parity)) return true;
+    if ((it & 3) == 0) {
+      if (*abort) return false;
+      if (tc::global_ns() - t0 > kRowsWaitNs) {
+        *abort = 1;
+        atomicExch(status, (int)ISX_ERR_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+// G' = (G diag(alpha_cell)) W_j^T for the R rows of `a` (rows_gemm.cu); w = 64, 128 or 256, `wmap`
+// the tensor map of W_j in bf16 with box {64, w}.
+isx_status launch_rows_gemm(isx_inr inr, const RowsGemmArgs& a, const CUtensorMap& wmap, int w, cudaStream_t st);
+
+}  // namespace rows
+}  // namespace isx

@@ -38,8 +38,8 @@ def _bounds(net, lo, hi, mode, prec, inflate=False):
     return to_np(c).astype(np.float64), to_np(s).astype(np.float64)
 
 
-@pytest.mark.parametrize("dims", [[3, 128, 128, 1], [3, 128, 128, 128, 1], [3, 128] * 1 + [128] * 4 + [1],
-                                  [3] + [256] * 5 + [1], "scientific"])
+@pytest.mark.parametrize("dims", [[3, 64, 64, 64, 1], [3, 128, 128, 1], [3, 128, 128, 128, 1],
+                                  [3, 128] * 1 + [128] * 4 + [1], [3] + [256] * 5 + [1], "scientific"])
 @pytest.mark.parametrize("mode", ["sound", "clt", "raua"])
 def test_bf16_bounds_match_oracle(pkg, dims, mode):
     layers = inr.load_inr(dims)[0] if isinstance(dims, str) else inr.random_inr(dims, 21)
@@ -86,10 +86,19 @@ def test_bf16_inflated_sound_bounds_contain_samples(pkg, dims):
 
 
 def test_bf16_unsupported_width_is_reported(pkg):
+    """Width 64 is bounded on the row-batched path (UP, RA-UA, sound without inflation); sound bounds
+    with inflation need the per-cell kernel (widths 128 and 256) and width 48 has no BF16 path."""
     net = pkg.Inr(inr.random_inr([3, 64, 64, 1], 1))
     lo = torch.zeros((4, 3), device="cuda")
+    c, s = net.bound_cells(lo, lo + 0.1, mode="clt", prec="bf16")
+    assert torch.isfinite(c).all() and torch.isfinite(s).all()
     with pytest.raises(pkg.IsxError) as e:
-        net.bound_cells(lo, lo + 0.1, prec="bf16")
+        net.bound_cells(lo, lo + 0.1, mode="sound", prec="bf16", inflate=True)
+    assert e.value.status == 5
+    net.close()
+    net = pkg.Inr(inr.random_inr([3, 48, 48, 1], 1))
+    with pytest.raises(pkg.IsxError) as e:
+        net.bound_cells(lo, lo + 0.1, mode="clt", prec="bf16")
     assert e.value.status == 5
     net.close()
 

@@ -71,3 +71,19 @@ def test_rows_path_runs_its_kernels(pkg):
     assert prof["rows_gemm"]["launches"] >= 1 and prof.get("bound_tc", {"launches": 0})["launches"] == 0
     print("rows_gemm launches", prof["rows_gemm"]["launches"], "GFLOP", prof["rows_gemm"]["flops"] / 1e9)
     net.close()
+
+
+@pytest.mark.parametrize("mode", ["clt", "sound"])
+def test_rows_path_width_64_matches_fp32(pkg, mode):
+    """Width 64 (no per-cell tensor-core kernel) against the float32 path, over several tiles."""
+    layers = inr.random_inr([3, 64, 64, 64, 64, 1], 8)
+    H = len(layers) - 1
+    net = pkg.Inr(layers)
+    lo, hi = _cubes(30000, 14, 2, 9)
+    c, s = net.bound_cells(lo, hi, mode=mode, prec="bf16")
+    c32, s32 = net.bound_cells(lo, hi, mode=mode, prec="fp32")
+    c, s, c32, s32 = (to_np(x).astype(np.float64) for x in (c, s, c32, s32))
+    tol = 3 * H * UB * (np.abs(c32) + s32) + 1e-6
+    print(f"w64 {mode}: max |dc|/tol {np.max(np.abs(c - c32) / tol):.3f}, |ds|/tol {np.max(np.abs(s - s32) / tol):.3f}")
+    assert np.all(np.abs(c - c32) <= tol) and np.all(np.abs(s - s32) <= tol)
+    net.close()

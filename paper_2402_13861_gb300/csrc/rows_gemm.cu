@@ -26,12 +26,14 @@ struct RowsSmem {
 //  - warps 0-3 scale each staged chunk in place: thread t multiplies row t by its cell's alpha
 //    (rows past R stay the TMA's zero fill);
 //  - warp 4 loads W_j (bf16, [out][in] = N x K, K-major) once by TMA, owns TMEM and issues the MMAs;
-//  - warps 6-13 drain the two TMEM accumulators to bf16 rows of G' (lane group = warp mod 4,
-//    column half = (warp - 6) / 4).
+//  - warps 6-9 drain the two TMEM accumulators to bf16 rows of G' (lane group = warp mod 4).
+// The scalers load the alpha of the next chunk (of this tile, or of the next tile) into registers
+// before they wait for the current one: alpha rows are not L2-resident at chunk scale, so their
+// latency would otherwise sit on every chunk.
 // Loads of tile k + 1 and the epilogue of tile k - 1 overlap the MMAs of tile k.  Every wait is
 // bounded (2 s): on timeout the kernel records ISX_ERR_TIMEOUT, lets the work in flight finish,
 // frees TMEM and returns.
-constexpr int kGT = 448;
+constexpr int kGT = 320;
 template <int W>
 __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ RowsGemmArgs args,
                                                        const __grid_constant__ CUtensorMap wmap,
@@ -61,7 +63,7 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&tfull[i], 1);
-      mbar_init(&tempty[i], 8);
+      mbar_init(&tempty[i], 4);
     }
     mbar_init(wfull, 1);
     *abort = 0;
@@ -84,21 +86,28 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
     bool ok = true;
     int64_t r_next = (int64_t)blockIdx.x * kRT + t;
     int cell_next = (r_next < args.R) ? args.rowcell[r_next] : 0;
+    // alpha of chunk 0 of the first tile
+    float4 av[16];
+    {
+      const float4* al0 = reinterpret_cast<const float4*>(args.alpha + (size_t)cell_next * W);
+#pragma unroll
+      for (int g = 0; g < 16; ++g) av[g] = al0[g];
+    }
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
       const int64_t r = tile * kRT + t;
       const bool valid = r < args.R;
-      const float4* al = reinterpret_cast<const float4*>(args.alpha + (size_t)cell_next * W);
+      const int cell = cell_next;
       // the next tile's row -> cell lookup is in flight while this tile is scaled
       r_next = (tile + gridDim.x) * kRT + t;
-      cell_next = (tile + gridDim.x < ntiles && r_next < args.R) ? args.rowcell[r_next] : 0;
+      cell_next = (tile + gridDim.x < ntiles && r_next < args.R) ? args.rowcell[r_next] : cell;
       for (int c = 0; c < KC; ++c, ++it) {
         const int sidx = it % NS;
-        // alpha of this chunk is loaded before the wait for the chunk's rows
-        float4 av[16];
-        if (valid) {
+        // alpha of the next chunk: this tile's chunk c + 1, else the next tile's chunk 0
+        const float4* aln = (c + 1 < KC) ? reinterpret_cast<const float4*>(args.alpha + (size_t)cell * W) + 16 * (c + 1)
+                                         : reinterpret_cast<const float4*>(args.alpha + (size_t)cell_next * W);
+        float4 an[16];
 #pragma unroll
-          for (int g = 0; g < 16; ++g) av[g] = al[16 * c + g];
-        }
+        for (int g = 0; g < 16; ++g) an[g] = aln[g];
         if (!rwait(&araw[sidx], (it / NS) & 1, abort, args.status)) { ok = false; break; }
         uint8_t* Ac = Asm + (size_t)sidx * S::kAC;
         if (valid) {
@@ -120,6 +129,8 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
         }
         fence_async_shared();
         mbar_arrive(&afull[sidx]);
+#pragma unroll
+        for (int g = 0; g < 16; ++g) av[g] = an[g];
       }
     }
   } else if (warp == 5) {
@@ -164,7 +175,7 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
     }
   } else {
     // ---- epilogue: TMEM -> bf16 rows of G' ----
-    const int row = 32 * (warp & 3) + lane, half = (warp - 6) >> 2;
+    const int row = 32 * (warp & 3) + lane;
     uint32_t tt = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tt) {
       const uint32_t b = tt & 1;
@@ -181,7 +192,7 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
       tc_fence_after();
       const uint32_t trow = tmem + b * W + ((uint32_t)(32 * (warp & 3)) << 16);
 #pragma unroll 1
-      for (int c0 = half * (W / 2); c0 < (half + 1) * (W / 2); c0 += 32) {
+      for (int c0 = 0; c0 < W; c0 += 32) {
         float v[32];
         tmem_ld32(trow + c0, v);
         if (valid) {

@@ -63,7 +63,14 @@ typedef enum { ISX_BOUND_SOUND = 0, ISX_BOUND_CLT = 1, ISX_BOUND_RAUA = 2, ISX_B
 
 /* Arithmetic of the coefficient propagation.  FP32: float32 storage and FMA.  BF16: coefficient
  * matrices stored in bfloat16 and multiplied on tcgen05 tensor cores with float32 accumulation;
- * centres, reductions and linearisations stay float32. */
+ * centres, reductions and linearisations stay float32.  Two BF16 kernels exist:
+ *  - the row-batched path (hidden widths 64, 128, 256; SOUND without inflation, CLT, RAUA; the
+ *    default): cells of a chunk are propagated layer by layer, the symbol rows of all cells in one
+ *    tensor-core GEMM per layer, symbols whose coefficient is exactly 0 never created;
+ *  - the per-cell persistent kernel (hidden widths 128, 256; the only BF16 kernel for SOUND with
+ *    inflation, used by isx_batch_* and isx_bound_cells_noalloc, and everywhere when the
+ *    environment variable ISX_BF16_ROWS is "0").
+ * Both stay within the BF16 rounding band of the float64 propagation; they are not bit-identical. */
 typedef enum { ISX_PREC_FP32 = 0, ISX_PREC_BF16 = 1 } isx_precision;
 
 /* Activation applied after every linear layer but the last: ReLU (the ReLU INRs of App. E), ELU
@@ -108,8 +115,9 @@ isx_status isx_bound_cells(isx_inr inr, const float* d_lo, const float* d_hi, in
  * and cudaFree imply.  This entry point allocates nothing: the tensor-core kernel takes its
  * per-CTA coefficient slices and its status word from a 16 MiB array compiled into the library
  * (every device that loads the library holds that array until the process exits).  Arguments
- * and results are those of isx_bound_cells (same kernel, same per-cell arithmetic, so the results
- * are identical); it only uses as many CTAs as the array has slices for (63 for a 256-wide,
+ * are those of isx_bound_cells; the kernel is the per-cell tensor-core kernel, so the results equal
+ * isx_bound_cells' with ISX_BF16_ROWS=0 or inflation, and agree with its row-batched default within
+ * the BF16 band.  It only uses as many CTAs as the array has slices for (63 for a 256-wide,
  * 5-hidden-layer network), so it can be slower.
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
  *    caches it; make that first call before any stream capture.

@@ -396,12 +396,11 @@ isx_status isx_extract_isosurface(isx_inr inr, const isx_extract_params* p, isx_
   ISX_TRY(check_inr(inr));
   ISX_TRY(validate_params(p, mesh));
   cudaStream_t st = (cudaStream_t)stream;
-  if (p->prec == ISX_PREC_BF16 && !bf16_supported(inr)) {
+  if (p->prec == ISX_PREC_BF16 && !bf16_supported(inr) && !rows_supported(inr, p->mode, p->inflate)) {
     set_error("BF16 propagation is not available for this width");
     return ISX_ERR_UNSUPPORTED;
   }
   const int L = p->max_level;
-  const int R = 1 << L;
   const IsoSet iso = iso_of(p);
   const int stop = (p->bound_stop_level < 0 || p->bound_stop_level >= L) ? L : p->bound_stop_level;
   for (int l = 0; l <= ISX_MAX_LEVEL; ++l) mesh->cells_bounded[l] = mesh->cells_kept[l] = mesh->cells_visited[l] = 0;

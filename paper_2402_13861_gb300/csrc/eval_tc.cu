@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kT, 1) k_eval_tc(const __grid_constant__ EvArg
   uint64_t* bar = reinterpret_cast<uint64_t*>(swo + W);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + EB_COUNT);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
-  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int t = threadIdx.x, warp = t >> 5;
   const int H = args.H;
 
   if (t == 0) {

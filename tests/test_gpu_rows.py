@@ -87,3 +87,17 @@ def test_rows_path_width_64_matches_fp32(pkg, mode):
     print(f"w64 {mode}: max |dc|/tol {np.max(np.abs(c - c32) / tol):.3f}, |ds|/tol {np.max(np.abs(s - s32) / tol):.3f}")
     assert np.all(np.abs(c - c32) <= tol) and np.all(np.abs(s - s32) <= tol)
     net.close()
+
+
+def test_rows_path_width_64_extraction(pkg):
+    """A BF16 extraction of the 3 -> 64 -> 64 -> 1 fixture runs on the row path and keeps the FP32
+    extraction's active set up to cells near an iso-value."""
+    layers, isos, wl = inr.load_inr("small")
+    net = pkg.Inr(layers)
+    a = net.extract(wl.max_level, isos, mode="clt", k=3.0, prec="bf16")
+    b = net.extract(wl.max_level, isos, mode="clt", k=3.0, prec="fp32")
+    sa = set((to_np(a["codes"]).astype(np.int64) & 0xFFFFFFFF).tolist())
+    sb = set((to_np(b["codes"]).astype(np.int64) & 0xFFFFFFFF).tolist())
+    print(f"w64 extraction: bf16 {len(sa)} vs fp32 {len(sb)} active, symmetric difference {len(sa ^ sb)}")
+    assert len(sb) > 1000 and len(sa ^ sb) <= 0.01 * len(sb)
+    net.close()

@@ -163,47 +163,39 @@ __global__ void __launch_bounds__(kScanB) k_rows_scan_apply(const int* cnt, int6
 }
 
 // ---- new rows gamma_n W_j[:, n] (row n of W_j^T) after each cell's transformed rows, in
-//      increasing n; the row -> cell map of the whole output ----
-__global__ void k_rows_new(int w, const float* __restrict__ GA, const float* __restrict__ Wt, const int* cnt_in,
-                           const int64_t* off_out, const int* cnt_out, __nv_bfloat16* xout, int* rowcell_out) {
-  __shared__ int list[kMaxW];
-  __shared__ int wcount[32];
-  __shared__ int nlist;
-  const int cell = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+//      increasing n; the row -> cell map of the whole output.  One warp per cell: the neurons with
+//      gamma != 0 come from ballots, and each row goes out as one warp-wide store (w / 32 columns
+//      per lane). ----
+constexpr int kNewWarps = 8;
+__global__ void __launch_bounds__(32 * kNewWarps) k_rows_new(int w, int nc, const float* __restrict__ GA,
+                                                             const float* __restrict__ Wt, const int* cnt_in,
+                                                             const int64_t* off_out, const int* cnt_out,
+                                                             __nv_bfloat16* xout, int* rowcell_out) {
+  const int lane = threadIdx.x & 31;
+  const int cell = blockIdx.x * kNewWarps + (threadIdx.x >> 5);
+  if (cell >= nc) return;
   const int64_t o0 = off_out[cell];
-  for (int64_t r = o0 + t; r < o0 + cnt_out[cell]; r += blockDim.x) rowcell_out[r] = cell;
-  if (t == 0) nlist = 0;
-  __syncthreads();
-  for (int n0 = 0; n0 < w; n0 += blockDim.x) {
-    const int n = n0 + t;
-    const bool f = n < w && GA[(size_t)cell * w + n] != 0.0f;
-    const unsigned b = __ballot_sync(0xffffffffu, f);
-    if (lane == 0) wcount[warp] = __popc(b);
-    __syncthreads();
-    int before = nlist;
-    for (int i = 0; i < warp; ++i) before += wcount[i];
-    if (f) list[before + __popc(b & ((1u << lane) - 1u))] = n;
-    __syncthreads();
-    if (t == 0)
-      for (int i = 0; i < nw; ++i) nlist += wcount[i];
-    __syncthreads();
-  }
-  // 8 columns (one 16-byte store) per thread: w / 8 threads per row, blockDim / (w / 8) rows per pass
-  const int64_t base = o0 + cnt_in[cell];
-  const int tpr = w / 8, rpp = blockDim.x / tpr;
-  const int sub = t / tpr, m8 = (t - sub * tpr) * 8;
-  if (sub < rpp)
-    for (int i = sub; i < nlist; i += rpp) {
-      const int n = list[i];
-      const float g = GA[(size_t)cell * w + n];
-      const float4* src = reinterpret_cast<const float4*>(Wt + (size_t)n * w + m8);
-      const float4 a = src[0], b = src[1];
-      const __nv_bfloat162 p0 = __floats2bfloat162_rn(g * a.x, g * a.y), p1 = __floats2bfloat162_rn(g * a.z, g * a.w);
-      const __nv_bfloat162 p2 = __floats2bfloat162_rn(g * b.x, g * b.y), p3 = __floats2bfloat162_rn(g * b.z, g * b.w);
-      *reinterpret_cast<uint4*>(xout + (base + i) * w + m8) =
-          make_uint4(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1),
-                     *reinterpret_cast<const uint32_t*>(&p2), *reinterpret_cast<const uint32_t*>(&p3));
+  const int co = cnt_out[cell];
+  for (int r = lane; r < co; r += 32) rowcell_out[o0 + r] = cell;
+  const int cpl = w / 32;                          // columns per lane (2, 4 or 8)
+  const int m0 = lane * cpl;
+  int64_t row = o0 + cnt_in[cell];
+  for (int n0 = 0; n0 < w; n0 += 32) {
+    const float gl = GA[(size_t)cell * w + n0 + lane];
+    unsigned b = __ballot_sync(0xffffffffu, gl != 0.0f);
+    while (b) {
+      const int l = __ffs(b) - 1;
+      b &= b - 1;
+      const float g = __shfl_sync(0xffffffffu, gl, l);
+      const float* src = Wt + (size_t)(n0 + l) * w + m0;
+      __nv_bfloat16* dst = xout + row * w + m0;
+      for (int c = 0; c < cpl; c += 2) {
+        const float2 v = *reinterpret_cast<const float2*>(src + c);
+        *reinterpret_cast<__nv_bfloat162*>(dst + c) = __floats2bfloat162_rn(g * v.x, g * v.y);
+      }
+      ++row;
     }
+  }
 }
 
 // ---- centre and input rows of z_{j+1}: c' = W a + b, I'_d = (I_d diag(alpha)) W^T, at float32-class
@@ -618,7 +610,8 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
       }
       {
         prof::Scope ps(K_ROWS_NEW, st, 0, 0);
-        k_rows_new<<<nc, 256, 0, st>>>(w, GA, inr->Wt[j], cnt_in, off_out, cnt_out, Xout, ws[rs[nxt]].as<int>());
+        k_rows_new<<<(nc + kNewWarps - 1) / kNewWarps, 32 * kNewWarps, 0, st>>>(w, nc, GA, inr->Wt[j], cnt_in, off_out,
+                                                                              cnt_out, Xout, ws[rs[nxt]].as<int>());
         ISX_LAUNCH_CHECK("k_rows_new");
       }
       {

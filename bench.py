@@ -305,6 +305,20 @@ def cpu_baseline(layers, mode, k, budget_s=12.0):
             "sample": f"{done} random cells of levels 6-9 bounded by the float64 oracle ({mode}) in {dt:.1f} s"}
 
 
+def job_totals(total_ms, cells, world, device):
+    """Whole-job totals of a replicas-only run: the slowest rank's time (max over ranks) and the
+    cells bounded by all ranks (sum), through the initialised process group when world > 1."""
+    import torch
+    import torch.distributed as dist
+    if world <= 1:
+        return float(total_ms), float(cells)
+    tmax = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    csum = torch.tensor([float(cells)], dtype=torch.float64, device=device)
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(csum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(csum[0])
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -393,12 +407,7 @@ def main():
     pkg.profile_enable(False)
     stats = pkg.profile_read()
     cells_local = cells
-    t = torch.tensor([total_ms, float(cells)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_ms, cells = float(tmax[0]), float(t[1])
+    total_ms, cells = job_totals(total_ms, cells, world, "cuda")
     value = cells / (total_ms / 1e3)
     ms_per_step = total_ms / args.steps
 

@@ -26,7 +26,6 @@
 #include <cuda_bf16.h>
 
 #include "cell_box.cuh"
-#include "compact.cuh"
 #include "linearise.cuh"
 #include "tc_ptx.cuh"
 #include "rows.cuh"
@@ -383,12 +382,12 @@ __global__ void k_rows_reduce_act(int w, int mode, int act, const __nv_bfloat16*
     }
     const __nv_bfloat162* src = reinterpret_cast<const __nv_bfloat162*>(X + o0 * w) + n2;
     int r = 0;
-    for (; r + 4 <= rows; r += 4) {                 // four rows' loads in flight
-      float2 x[4];
+    for (; r + 8 <= rows; r += 8) {                 // eight rows' loads in flight
+      float2 x[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) x[u] = __bfloat1622float2(src[(size_t)(r + u) * (w / 2)]);
+      for (int u = 0; u < 8; ++u) x[u] = __bfloat1622float2(src[(size_t)(r + u) * (w / 2)]);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         add(s0, e0, x[u].x);
         add(s1, e1, x[u].y);
       }
@@ -456,18 +455,34 @@ __global__ void __launch_bounds__(256) k_rows_output(int w, int mode, const __nv
   // three input rows and the G rows: one warp per row
   const int rows = cnt[cell];
   const int64_t o0 = off[cell];
-  for (int r = warp; r < rows + 3; r += 8) {
+  for (int r = warp; r < 3; r += 8) {
     float y = 0.0f;
-    if (r < 3) {
-      const float* src = I + (size_t)cell * 3 * w + (size_t)r * w;
-      for (int n = lane; n < w; n += 32) y = fmaf(src[n], v[n], y);
-    } else {
-      const __nv_bfloat16* src = X + (o0 + r - 3) * w;
-      for (int n = lane; n < w; n += 32) y = fmaf(__bfloat162float(src[n]), v[n], y);
-    }
+    const float* src = I + (size_t)cell * 3 * w + (size_t)r * w;
+    for (int n = lane; n < w; n += 32) y = fmaf(src[n], v[n], y);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
     if (lane == 0) s += sq ? y * y : fabsf(y);
+  }
+  // the G rows two at a time per warp (both rows' loads in flight)
+  for (int r = warp; r < rows; r += 16) {
+    const bool two = r + 8 < rows;
+    const __nv_bfloat16* s0p = X + (o0 + r) * w;
+    const __nv_bfloat16* s1p = X + (o0 + (two ? r + 8 : r)) * w;
+    float y0 = 0.0f, y1 = 0.0f;
+    for (int n = lane; n < w; n += 32) {
+      const float vn = v[n];
+      y0 = fmaf(__bfloat162float(s0p[n]), vn, y0);
+      y1 = fmaf(__bfloat162float(s1p[n]), vn, y1);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+      y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+    }
+    if (lane == 0) {
+      s += sq ? y0 * y0 : fabsf(y0);
+      if (two) s += sq ? y1 * y1 : fabsf(y1);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {

@@ -41,7 +41,7 @@ typedef enum {
   ISX_ERR_CUDA = 2,         /* a CUDA runtime call or kernel launch failed                       */
   ISX_ERR_CAPACITY = 3,     /* an output buffer is too small; required sizes were filled in      */
   ISX_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up; the context stays usable     */
-  ISX_ERR_UNSUPPORTED = 5,  /* valid request this build does not implement (e.g. width for BF16) */
+  ISX_ERR_UNSUPPORTED = 5,  /* valid request the library does not implement (e.g. width for BF16) */
   ISX_ERR_NOMEM = 6         /* workspace allocation failed                                       */
 } isx_status;
 

@@ -1,7 +1,7 @@
 // Cell-subdivision proposer.  The paper keeps or culls cells by range analysis alone (Algorithm 1);
 // this addition scores (cell, iso-value) pairs with a small MLP trained on labels the method itself
 // produces (dense evaluation plus the marching-cubes crossing test of Sec. IV-D), so that confident
-// pairs skip the affine bound, and range analysis stays the fallback and the judge for the rest.
+// pairs skip the affine bound, and range analysis stays the fallback and decides the rest.
 //
 // Model: 8 -> 64 -> 64 -> 64 -> 1, ReLU hidden layers, sigmoid output, binary cross-entropy.
 // Numerics: BF16 weights, BF16 inputs and activations (round to nearest even after every layer),

@@ -356,7 +356,8 @@ __global__ void __launch_bounds__(kST, 1) k_rows_split(const __grid_constant__ R
 //      rows and its three input rows (compensated), two neurons per thread; fused with activation
 //      j+1 (alpha, gamma, a, and, when AH is given, the split A operand of the next centre /
 //      input-row GEMM and the next row count cnt_next = cnt + #(gamma != 0)) ----
-__global__ void k_rows_reduce_act(int w, int mode, int act, const __nv_bfloat16* X, const int64_t* off,
+__global__ void __launch_bounds__(128, 16) k_rows_reduce_act(int w, int mode, int act, const __nv_bfloat16* X,
+                                                             const int64_t* off,
                                   const int* cnt, const float* I, const float* C, float* A, float* AL, float* GA,
                                   int* cnt_next, __nv_bfloat16* AH, __nv_bfloat16* ALO) {
   __shared__ int wsum[32];

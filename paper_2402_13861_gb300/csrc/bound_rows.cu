@@ -14,10 +14,14 @@
 //
 // alpha is applied to the A operand (the rows) while it is staged into shared memory, so the B
 // operand is W_j itself, loaded once per CTA and shared by the rows of every cell: rows of many
-// cells fill each 128-row MMA tile.  After the GEMM a reduction pass forms r = sum |x| (sound) or
-// sigma^2 = sum x^2 (UP) per (cell, neuron) from the stored rows and the input rows, and the
-// activation pass linearises.  The output layer is a per-cell dot product of every row with
-// alpha_H * w_out.
+// cells fill each 128-row MMA tile (rows_gemm.cu).  Per chunk and layer this file runs:
+//   k_rows_input_act / k_rows_reduce_act: r = sum |x| (sound) or sigma^2 = sum x^2 (UP) per (cell,
+//     neuron) over the stored rows and the input rows, the linearisation of the next activation,
+//     the split A operand of the centre GEMM and the next per-cell row count;
+//   k_rows_scan_*: row offsets of the next layer (the host reads the total to size the buffers);
+//   the row GEMM, k_rows_new (the new rows) and k_rows_split (centre and input rows);
+// and, after the last layer, k_rows_output: the output coefficient of every symbol is its row .
+// (alpha_H * w_out), read off as sum |y| or sum y^2.
 #include "internal.cuh"
 
 #include <algorithm>

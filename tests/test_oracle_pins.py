@@ -531,3 +531,22 @@ def test_up_mean_of_one_hidden_layer_equals_gaussian_input_expectation(act):
     x = xc + rng.normal(size=(2_000_000, 3)) * h / np.sqrt(3)
     v = mlp.mlp_forward(layers, x, act=act)
     assert abs(mu[0] - v.mean()) <= 5 * v.std() / np.sqrt(x.shape[0])
+
+
+def test_raua_readout_exact_on_linear_nets_and_inside_the_sound_radius(small):
+    """RA-UA (Sec. IV-A): sound propagation read off with sigma^2 = (1/3) sum x_i^2.  On a net that is
+    affine over the domain this is the exact standard deviation of the output under uniform inputs;
+    on any net sqrt(3) sigma = ||x||_2 <= ||x||_1 = the sound radius, with the sound centre."""
+    layers = _linear_regime_net(3, [3, 7, 5, 1], +1)
+    Weff = layers[2][0] @ layers[1][0] @ layers[0][0]
+    lo, hi = boxes.random_boxes(100, 4, -6, -1)
+    h = (hi.astype(np.float64) - lo.astype(np.float64)) / 2
+    c, sig = affine.bound(layers, lo, hi, affine.RAUA)
+    np.testing.assert_allclose(sig, np.sqrt(((h * Weff[0]) ** 2).sum(1) / 3.0), rtol=1e-12)
+    layers, _, _ = small
+    lo, hi = boxes.random_boxes(300, 5, -8, -1)
+    c, sig = affine.bound(layers, lo, hi, affine.RAUA)
+    c0, r0 = affine.bound(layers, lo, hi, affine.SOUND)
+    np.testing.assert_allclose(c, c0, rtol=1e-12, atol=1e-15)
+    assert np.all(np.sqrt(3.0) * sig <= r0 * (1 + 1e-12))
+    assert np.mean(np.sqrt(3.0) * sig < 0.9 * r0) > 0.5          # strictly tighter on most boxes

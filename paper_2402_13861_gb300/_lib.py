@@ -213,7 +213,9 @@ class Inr:
         return self._h
 
     def bound_cells(self, lo, hi, mode="sound", prec="fp32", inflate=False, center=None, spread=None, stream=None):
-        """lo, hi: float32 CUDA tensors (n, 3).  Returns (center, spread) CUDA tensors (n,)."""
+        """Bounds of the INR over the boxes [lo, hi] (isx_bound_cells).  lo, hi: float32 CUDA tensors
+        (n, 3).  Returns (center, spread) CUDA tensors (n,): (x0, r) for sound / rafixed, (mu, sigma)
+        for clt / raua."""
         import torch
         n = lo.shape[0]
         assert lo.is_cuda and lo.dtype == torch.float32 and lo.is_contiguous() and hi.is_contiguous()
@@ -226,6 +228,8 @@ class Inr:
         return center, spread
 
     def eval_points(self, xyz, prec="fp32", out=None, stream=None):
+        """The MLP at float32 CUDA points (n, 3) (isx_eval_points): prec "fp32" (CUDA cores) or "bf16"
+        (tensor cores with two-term bf16 operands, float32-class)."""
         import torch
         n = xyz.shape[0]
         if out is None:
@@ -258,8 +262,14 @@ class Inr:
     def extract(self, max_level, isos, mode="sound", k=3.0, prec="fp32", inflate=False, bound_stop_level=-1,
                 active_cap=1 << 16, tri_cap=1 << 18, dense=False, stream=None, buffers=None, proposer=None,
                 proposer_level=1, tau_lo=0.0, tau_hi=1.0, eval_prec="fp32", kd_tree=False):
-        """Hierarchical (or, with dense=True, dense) extraction.  Grows the output buffers and
-        retries once if a capacity is exceeded.  Returns a dict of tensors and counters."""
+        """Hierarchical (or, with dense=True, dense) extraction (isx_extract_isosurface /
+        isx_extract_dense).  mode: "sound", "clt", "raua" or "rafixed"; prec / eval_prec: "fp32" or
+        "bf16" (bounds and corner values on the tensor cores); kd_tree: Algorithm 1's k-d tree
+        instead of the octree; bound_stop_level: bound down to that level, keep every descendant of
+        the survivors; proposer (a Proposer) with proposer_level, tau_lo, tau_hi: the learned gate.
+        Grows the output buffers and retries once if a capacity is exceeded.  Returns a dict of
+        tensors (codes, masks, tri_vert, tri_edge, tri_iso, tri_cell) and counters (n_active,
+        n_tris, cells_bounded / cells_kept / cells_visited per level, phase times in ms)."""
         import torch
         p = self.params(max_level, isos, mode, k, prec, inflate, bound_stop_level, proposer, proposer_level,
                         tau_lo, tau_hi, eval_prec, kd_tree)

@@ -550,3 +550,26 @@ def test_raua_readout_exact_on_linear_nets_and_inside_the_sound_radius(small):
     np.testing.assert_allclose(c, c0, rtol=1e-12, atol=1e-15)
     assert np.all(np.sqrt(3.0) * sig <= r0 * (1 + 1e-12))
     assert np.mean(np.sqrt(3.0) * sig < 0.9 * r0) > 0.5          # strictly tighter on most boxes
+
+
+def test_brute_force_8cubed_rafixed_and_kd_never_miss():
+    """RA-Fixed is sound: at 8^3 its hierarchical extraction keeps every dense crossing cell, in the
+    octree and in the k-d tree; and on a one-hidden-layer net, where its bound equals full affine
+    arithmetic's box by box, both give the same active set."""
+    layers = inr.random_inr([3, 24, 24, 1], 14)
+    R, L = 8, 3
+    vals = mlp.mlp_forward(layers, octree.lattice_points(R))
+    isos = np.quantile(vals, [0.3, 0.6])
+    for levels in (octree.extract_active(layers, L, isos, affine.RAFIXED),
+                   octree.kd_extract_active(layers, L, isos, affine.RAFIXED)):
+        act, mask = octree.active_cells(levels)
+        for q, c in enumerate(isos):
+            truth = mc.crossing_cells(vals, R, c)
+            fpr, fnr = octree.fpr_fnr(act[(mask >> q) & 1 == 1], truth, R)
+            assert fnr == 0.0
+    one = inr.random_inr([3, 32, 1], 15)
+    v1 = mlp.mlp_forward(one, octree.lattice_points(R))
+    iso1 = np.quantile(v1, [0.5])
+    a_fix = octree.active_cells(octree.extract_active(one, L, iso1, affine.RAFIXED))[0]
+    a_aa = octree.active_cells(octree.extract_active(one, L, iso1, affine.SOUND))[0]
+    assert set(map(tuple, a_fix.tolist())) == set(map(tuple, a_aa.tolist()))

@@ -106,3 +106,35 @@ def test_proposer_argument_errors_without_gpu(lib):
                                    std.ctypes.data_as(f32p), C.byref(h)) == 1
     assert b"standard deviation" in lib.isx_last_error()
     assert lib.isx_proposer_predict(None, None, 0, None, None) == 1
+
+
+def test_c_program_links_against_the_library(tmp_path):
+    """A plain C program includes isx.h, links libisx.so and gets argument errors (no GPU call)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    from paper_2402_13861_gb300 import _lib
+    libdir = os.path.dirname(_lib.LIB_PATH)
+    src = tmp_path / "use.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include "isx.h"
+int main(void) {
+  isx_inr h = 0;
+  if (isx_version() != 100) return 1;
+  if (isx_create_inr(NULL, &h) != ISX_ERR_ARG) return 2;
+  int dims[3] = {3, 20, 1};
+  const float* W[2] = {0, 0};
+  isx_inr_desc d = {2, dims, W, W, ISX_ACT_RELU};
+  if (isx_create_inr(&d, &h) != ISX_ERR_UNSUPPORTED) return 3;   /* width 20 */
+  printf("%s\n", isx_last_error());
+  return 0;
+}
+""")
+    exe = tmp_path / "use"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lisx",
+                    "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert "width" in r.stdout

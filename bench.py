@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--all-forms", action="store_true",
+                    help="also the slow forms: the per-cell kernel, RA-Fixed, the batched form (fits 8 nets) and "
+                         "the SIREN workload (fits a SIREN); the default run keeps the quick ones")
     return ap.parse_args()
 
 
@@ -120,7 +123,7 @@ def traffic_record(kernel, src_file):
         return None
 
 
-def extraction_forms(pkg, net, L, isos, plain, plain_ms, mode, k, prec):
+def extraction_forms(pkg, net, L, isos, plain, plain_ms, mode, k, prec, slow=False):
     """End-to-end time of the other extraction forms on the same INR and isos, and the crossing
     (cell, iso) pairs of the dense extraction each form misses: the per-cell tensor-core bound kernel,
     bounding stopped at level 6, the proposer-assisted form (committed proposer), dense extraction
@@ -160,11 +163,13 @@ def extraction_forms(pkg, net, L, isos, plain, plain_ms, mode, k, prec):
     mp, tot = missed(plain["codes"], plain["masks"], cross)
     out["plain"] = {"ms": plain_ms, "cells_bounded": int(sum(plain["cells_bounded"])), "missed_pairs": mp,
                     "missed_rate": mp / max(tot, 1)}
-    # the per-cell persistent tcgen05 bound kernel on the same extraction
-    os.environ["ISX_BF16_ROWS"] = "0"
-    r, ms = timed(mode=mode, k=k, prec=prec, eval_prec="bf16")
-    del os.environ["ISX_BF16_ROWS"]
-    out["per_cell_tc_kernel"] = {"ms": ms, "cells_bounded": int(sum(r["cells_bounded"])), "n_active": r["n_active"]}
+    if slow:
+        # the per-cell persistent tcgen05 bound kernel on the same extraction
+        os.environ["ISX_BF16_ROWS"] = "0"
+        r, ms = timed(mode=mode, k=k, prec=prec, eval_prec="bf16")
+        del os.environ["ISX_BF16_ROWS"]
+        out["per_cell_tc_kernel"] = {"ms": ms, "cells_bounded": int(sum(r["cells_bounded"])),
+                                     "n_active": r["n_active"]}
     r, ms = timed(mode=mode, k=k, prec=prec, bound_stop_level=6, eval_prec="bf16")
     m, _ = missed(r["codes"], r["masks"], cross)
     out["bound_to_level6_tc_eval"] = {"ms": ms, "cells_bounded": int(sum(r["cells_bounded"])),
@@ -180,10 +185,11 @@ def extraction_forms(pkg, net, L, isos, plain, plain_ms, mode, k, prec):
     out["dense_fp32_eval"] = {"ms": ms_d32, "crossing_pairs": tot}
     out["dense_tc_eval"] = {"ms": ms_dtc}
     # the reduced range-analysis baseline: sound RA-Fixed bounds (one fused float32 kernel)
-    r, ms = timed(mode="rafixed", prec="fp32")
-    m, _ = missed(r["codes"], r["masks"], cross)
-    out["rafixed_fp32"] = {"ms": ms, "cells_bounded": int(sum(r["cells_bounded"])), "n_active": r["n_active"],
-                           "missed_pairs": m, "missed_rate": m / max(tot, 1)}
+    if slow:
+        r, ms = timed(mode="rafixed", prec="fp32")
+        m, _ = missed(r["codes"], r["masks"], cross)
+        out["rafixed_fp32"] = {"ms": ms, "cells_bounded": int(sum(r["cells_bounded"])), "n_active": r["n_active"],
+                               "missed_pairs": m, "missed_rate": m / max(tot, 1)}
     # Algorithm 1's k-d tree (widest-side bisection) against the octree, one level lower (256^3)
     for name, kd in (("octree_256", False), ("kd_tree_256", True)):
         r, ms = timed_level(L - 1, mode=mode, k=k, prec=prec, eval_prec="bf16", kd_tree=kd)
@@ -242,7 +248,7 @@ def batched_form(pkg, mode, k):
             "cells_bounded_sequential": int(sum(sum(s["cells_bounded"]) for s in singles))}
 
 
-def activation_forms(pkg, k):
+def activation_forms(pkg, k, names=("siren", "sdf_elu")):
     """The SIREN (sine, Table VII's sine row) and ELU-SDF workloads at 512^3: hierarchical CLT
     extraction on the tensor cores against dense extraction (FP32 evaluation), the crossing
     (cell, iso) pairs the hierarchy misses, and the fit that made each network."""
@@ -251,7 +257,7 @@ def activation_forms(pkg, k):
     from paper_2402_13861_gb300.train_proposer import missed
     st = torch.cuda.current_stream()
     out = {}
-    for name in ("siren", "sdf_elu"):
+    for name in names:
         t0 = time.time()
         layers, isos, wl = inr.load_inr(name, device="cuda")
         fit_s = time.time() - t0
@@ -493,10 +499,13 @@ def main():
             "n_tris": res["n_tris"], "cells_bounded_per_level": res["cells_bounded"],
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "kernel_time_share": shares}
     if rank == 0 and world == 1 and not args.no_forms:
-        line["forms"] = extraction_forms(pkg, net, L, isos, res, ms_per_step, args.mode, args.k, prec)
+        line["forms"] = extraction_forms(pkg, net, L, isos, res, ms_per_step, args.mode, args.k, prec,
+                                         slow=args.all_forms)
         if prec == "bf16":
-            line["forms"]["batched"] = batched_form(pkg, args.mode, args.k)
-            line["forms"]["activations"] = activation_forms(pkg, args.k)
+            if args.all_forms:
+                line["forms"]["batched"] = batched_form(pkg, args.mode, args.k)
+            line["forms"]["activations"] = activation_forms(
+                pkg, args.k, ("siren", "sdf_elu") if args.all_forms else ("sdf_elu",))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(layers, args.mode, args.k)
     if rank == 0:

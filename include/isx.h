@@ -16,7 +16,9 @@
  *    lo = -1 + 2 (i, j, k) / 2^l, hi = lo + 2 / 2^l; they are passed packed as
  *    code = i | j << 10 | k << 20, so levels go up to ISX_MAX_LEVEL = 10 (1024^3 cells).
  *  - The library keeps a per-INR workspace in device memory (grown with cudaMalloc on first use
- *    of a larger problem and freed by isx_destroy_inr).
+ *    of a larger problem and freed by isx_destroy_inr).  Calls on one INR handle share that
+ *    workspace, so they must not overlap: issue them from one thread, on one stream (or
+ *    synchronise between streams).  Different handles are independent.
  */
 #ifndef ISX_H
 #define ISX_H

@@ -264,8 +264,10 @@ isx_status isx_create_inr(const isx_inr_desc* d, isx_inr* out) {
       set_error("null weight pointer");
       return ISX_ERR_ARG;
     }
+  int dev = -1;
+  ISX_CUDA(cudaGetDevice(&dev));
   isx_inr inr = new isx_inr_s();
-  ISX_CUDA(cudaGetDevice(&inr->device));
+  inr->device = dev;
   inr->n_layers = L;
   inr->H = L - 1;
   inr->w = w;

@@ -573,3 +573,76 @@ def test_brute_force_8cubed_rafixed_and_kd_never_miss():
     a_fix = octree.active_cells(octree.extract_active(one, L, iso1, affine.RAFIXED))[0]
     a_aa = octree.active_cells(octree.extract_active(one, L, iso1, affine.SOUND))[0]
     assert set(map(tuple, a_fix.tolist())) == set(map(tuple, a_aa.tolist()))
+
+
+# ---- Worked by hand: a 3 -> 2 -> 2 -> 1 net on the box [-1, 1]^3 -----------------------------
+
+def _hand_net():
+    """f(x, y, z) = relu(relu x + relu y) + relu(relu x - relu y): W0 picks x and y, W1 = [[1, 1],
+    [1, -1]], W2 = [1, 1], all biases 0.  Its range on [-1, 1]^3 is [0, 2]."""
+    return [(np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]]), np.zeros(2)),
+            (np.array([[1.0, 1.0], [1.0, -1.0]]), np.zeros(2)),
+            (np.array([[1.0, 1.0]]), np.zeros(1))]
+
+
+def test_hand_worked_affine_and_rafixed_bounds():
+    """Eq. 3 and Eq. 4 (Chebyshev line) carried out by hand on [-1, 1]^3:
+    layer 0: both neurons are the input symbols x, y on [-1, 1]; ReLU: alpha = 1/2, beta = gamma =
+    1/4, so each neuron is 1/4 + x/2 + e/4 with its own new symbol e.
+    layer 1: neuron 1 = 1/2 + (x + y)/2 + (e1 + e2)/4, neuron 2 = (x - y)/2 + (e1 - e2)/4, each of
+    radius 3/2.  ReLU on [-1, 2]: alpha = 2/3, beta = gamma = 1/3; on [-3/2, 3/2]: alpha = 1/2,
+    beta = gamma = 3/8.
+    output: centre 2/3 + 3/8 = 25/24; coefficients x 7/12, y 1/12, e1 7/24, e2 1/24, e3 1/3, e4 3/8,
+    radius 41/24.
+    RA-Fixed keeps x, y and gives each neuron a private radius: 1/4 after ReLU 1, |W1| (1/4, 1/4) =
+    (1/2, 1/2) after layer 1 (e1, e2 no longer cancel), alpha r + gamma = (2/3, 5/8) after ReLU 2,
+    so the output radius is 7/12 + 1/12 + 2/3 + 5/8 = 47/24 about the same centre."""
+    L = _hand_net()
+    lo, hi = np.full((1, 3), -1.0), np.full((1, 3), 1.0)
+    c, r = affine.bound(L, lo, hi, affine.SOUND)
+    assert c[0] == pytest.approx(25 / 24, abs=1e-15) and r[0] == pytest.approx(41 / 24, abs=1e-15)
+    c, r = affine.bound(L, lo, hi, affine.RAFIXED)
+    assert c[0] == pytest.approx(25 / 24, abs=1e-15) and r[0] == pytest.approx(47 / 24, abs=1e-15)
+    # both contain the true range [0, 2]
+    assert 25 / 24 - 41 / 24 <= 0.0 and 25 / 24 + 41 / 24 >= 2.0
+
+
+# ---- The cull test is closed at both ends, and culled iso-values stay culled -------------------
+
+def test_plane_on_cell_faces_keeps_both_neighbouring_columns():
+    """f(x) = relu(x + 1) - 1 = x on [-1, 1]^3 (the ReLU sees only non-negative inputs, so its line
+    is the identity and the sound bound of a cell is exactly [lo_x, hi_x]).  The iso-value 0 lies
+    on the faces x = 0 between the columns i = R/2 - 1 and i = R/2: both touch it at a bound
+    endpoint and, with the cull test strict (keep on equality), both are active -- 2 R^2 cells."""
+    L = [(np.array([[1.0, 0.0, 0.0]]), np.array([1.0])), (np.array([[1.0]]), np.array([-1.0]))]
+    for lev in (1, 2, 3):
+        R = 1 << lev
+        act, _ = octree.active_cells(octree.extract_active(L, lev, [0.0], affine.SOUND))
+        assert act.shape[0] == 2 * R * R
+        assert set(np.unique(act[:, 0]).tolist()) == {R // 2 - 1, R // 2}
+
+
+def test_iso_sets_shrink_down_the_tree(small):
+    """A child inherits the iso set that survived its parent's test (Algorithm 1 recurses only
+    into the parent's surviving iso-values), so every level's incoming set is its parent's
+    surviving set, and a surviving set is a subset of the incoming one."""
+    layers, isos, _ = small
+    lv = octree.extract_active(layers, 4, np.quantile(mlp.mlp_forward(layers, octree.lattice_points(16)),
+                                                       [0.2, 0.5, 0.8]), affine.SOUND)
+    shrank = 0
+    for a, b in zip(lv[:-1], lv[1:]):
+        keep = a["mask"] != 0
+        parent_mask = a["mask"][keep]
+        assert np.array_equal(b["mask_in"], np.repeat(parent_mask, 8))
+        assert np.all((b["mask"] & ~b["mask_in"]) == 0)
+        shrank += int(np.sum(a["mask"][keep] != a["mask_in"][keep]))
+    assert shrank > 0                     # some cell dropped one iso-value but kept another
+
+
+def test_fpr_fnr_counts():
+    """FPR = FP / (FP + TN), FNR = FN / (FN + TP) over the R^3 cells (Sec. V-A.3).  R = 2: truth
+    {(0,0,0), (1,0,0)}, prediction {(1,0,0), (0,1,0), (1,1,0)}: TP 1, FP 2, FN 1, TN 4."""
+    fpr, fnr = octree.fpr_fnr([[1, 0, 0], [0, 1, 0], [1, 1, 0]], [[0, 0, 0], [1, 0, 0]], 2)
+    assert fpr == pytest.approx(2 / 6) and fnr == pytest.approx(1 / 2)
+    assert octree.fpr_fnr([[0, 0, 0]], [[0, 0, 0]], 2) == (0.0, 0.0)
+    assert octree.fpr_fnr(np.zeros((0, 3)), [[1, 1, 1]], 2) == (0.0, 1.0)

@@ -109,3 +109,18 @@ def test_subtree_labels_match_brute_force(level):
             if all(c[d] * s <= code[d] < (c[d] + 1) * s for d in range(3)):
                 want |= int(m)
         assert g == want
+
+
+def test_he_initialisation_scales_with_fan_in():
+    """He-normal initialisation: weights of a layer with fan-in n have standard deviation
+    sqrt(2 / n) and the biases start at 0.  The sample deviation of each layer of the proposer's
+    shape (8 -> 64 -> 64 -> 64 -> 1) is checked against it (chi-square width: 4 / sqrt(2 N))."""
+    params = P.init_params(123)
+    assert [W.shape for W, _ in params] == [(64, 8), (64, 64), (64, 64), (1, 64)]
+    for W, b in params:
+        want = np.sqrt(2.0 / W.shape[1])
+        sd = np.sqrt(np.mean(W * W))
+        assert abs(sd / want - 1.0) < 4.0 / np.sqrt(2.0 * W.size)
+        assert np.all(b == 0.0)
+    a = P.init_params(123)
+    assert all(np.array_equal(W, W2) for (W, _), (W2, _) in zip(params, a))

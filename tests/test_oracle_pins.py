@@ -508,12 +508,31 @@ def test_least_squares_fit_by_quadrature(act):
             assert abs(ga ** 2 - rg ** 2) <= 1e-13 * scale ** 2
 
 
-@pytest.mark.parametrize("act", [acts.SINE, acts.ELU])
+@pytest.mark.parametrize("act", [acts.SINE, acts.ELU, acts.RELU])
 def test_least_squares_small_sigma_is_the_tangent(act):
     for mu in (-2.0, -0.5, 0.3, 1.7):
         al, be, ga = acts.least_squares(act, mu, 1e-4)
         t_al, t_be, t_ga = acts.least_squares(act, mu, 0.0)
         assert abs(al - t_al) < 1e-7 and abs(be - t_be) < 1e-7 and t_ga == 0 and ga < 1e-7
+
+
+def test_relu_least_squares_at_the_kink_is_continuous_in_sigma():
+    """At mu = 0 the ReLU row gives alpha = P(X > 0) = 1/2 for every sigma > 0, so the sigma = 0
+    reading (alpha = 1/2 at mu = 0) is the limit; both ReLU rules agree there."""
+    for sg in (1.0, 1e-3, 1e-12):
+        assert acts.least_squares(acts.RELU, 0.0, sg)[0] == pytest.approx(0.5, abs=1e-15)
+    al, be, ga = acts.least_squares(acts.RELU, 0.0, 0.0)
+    assert (al, be, ga) == (0.5, 0.0, 0.0)
+    a2 = affine.relu_least_squares(np.array([0.0]), np.array([0.0]))
+    assert (a2[0][0], a2[1][0], a2[2][0]) == (0.5, 0.0, 0.0)
+
+
+def test_canonical_triangle_form_keeps_orientation():
+    """A triangle (a, b, c) is the same oriented triangle as (b, c, a) and (c, a, b), not as
+    (a, c, b): the canonical form rotates each triple to its smallest id and sorts the rows."""
+    got = mc.sorted_edge_triples([[9, 3, 5], [7, 8, 6], [2, 1, 4]])
+    np.testing.assert_array_equal(got, [[1, 4, 2], [3, 5, 9], [6, 7, 8]])
+    assert not np.array_equal(mc.sorted_edge_triples([[1, 2, 3]]), mc.sorted_edge_triples([[1, 3, 2]]))
 
 
 @pytest.mark.parametrize("act", [acts.SINE, acts.ELU])

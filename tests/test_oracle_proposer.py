@@ -94,6 +94,17 @@ def test_features_closed_forms():
     assert np.allclose(X[1], [0.75, -0.25, 0.25, -2.0, 0.2, -0.1, 0.05, 2.0])
 
 
+def test_forward_standardises_the_features():
+    """x_norm = (x - mu) / sd: a single linear unit reading feature 0 returns (x_0 - mu_0) / sd_0."""
+    W = np.zeros((1, 8))
+    W[0, 0] = 1.0
+    params = [(W, np.zeros(1))]
+    mu = np.full(8, 1.0)
+    sd = np.full(8, 4.0)
+    z, _ = P.forward(params, np.array([[3.0] + [0.0] * 7, [-7.0] + [0.0] * 7]), mu, sd)
+    assert np.allclose(z, [0.5, -2.0], rtol=0, atol=1e-15)
+
+
 @pytest.mark.parametrize("level", [0, 1, 2, 3, 4])
 def test_subtree_labels_match_brute_force(level):
     L = 4

@@ -61,6 +61,17 @@ def test_argument_errors_without_gpu(lib):
     assert lib.isx_create_inr(C.byref(desc), C.byref(h)) == 1
     assert b"activation" in lib.isx_last_error()
     assert lib.isx_version() == 100
+    # null handles are argument errors on every entry point that takes one; destroying one is a no-op
+    assert lib.isx_bound_cells(None, None, None, 0, 0, 0, 0, None, None, None) == 1
+    assert lib.isx_bound_cells_noalloc(None, None, None, 0, 0, 0, None, None, None) == 1
+    assert lib.isx_eval_points(None, None, 0, 0, None, None) == 1
+    assert lib.isx_extract_isosurface(None, None, None, None) == 1
+    assert lib.isx_extract_dense(None, None, None, None) == 1
+    assert lib.isx_batch_create(None, None, 0, 0, C.byref(h)) == 1
+    assert lib.isx_batch_run(None, None, None) == 1
+    assert lib.isx_destroy_inr(None) == 0
+    assert lib.isx_batch_destroy(None) == 0
+    assert lib.isx_proposer_destroy(None) == 0
 
 
 def test_struct_layouts_match_the_c_compiler(tmp_path):

@@ -1,0 +1,307 @@
+"""GPU parity at the benchmark's full size: the 512^3 extraction of the scientific-field INR
+(3 -> 256 x 5 -> 1 ReLU, 8 iso-values, uncertainty propagation read off at mu +- 3 sigma, bf16
+bounds on the row-batched tensor-core path, tensor-core corner values), called exactly as the
+benchmark calls it, and checked on cells the float64 oracle works out one by one.
+
+The cells are chosen without looking at the GPU's output.  On random rows of the 512^3 grid the
+oracle evaluates the four lattice lines that bound the row, and picks cells the iso-surfaces
+cross (the dense truth of Sec. V-A.3), their neighbours along the row and random cells.  For every
+sampled cell and each of its ancestors (levels 0-9, the octree nodes Algorithm 1 bounds on the way
+down):
+
+1. the GPU's bound (isx_bound_cells, the kernels of the extraction) is within the bf16 band of the
+   oracle's: |d sigma| <= 3 H u_b sigma and |d mu| <= 3 H u_b (|mu| + sigma), u_b = 2^-8 (at most
+   three bf16 roundings per coefficient per layer);
+2. the extraction's iso mask of the cell is exactly the conjunction, over its ancestors, of the
+   float32 cull test mu - k sigma <= c_q <= mu + k sigma on those GPU bounds (a (cell, iso) pair is
+   excused only where an endpoint lies within a few float32 roundings of c_q);
+3. where the extraction and the oracle's own hierarchy disagree on a (cell, iso) pair, some
+   ancestor's oracle endpoint lies within the band of item 1 (|d mu| + k |d sigma|) of c_q;
+4. the triangles of every kept (cell, iso) whose float64 corner values all lie farther from c_q
+   than the tensor-core evaluation band (2^-12 of the absolute-value propagation |W| |a| + |b|)
+   are the oracle's marching-cubes triangles, edge for edge and in order, with every vertex within
+   the shift those value errors can cause on its edge;
+5. the level counts are consistent: one root, eight children per kept cell, and the kept cells of
+   the last level are the active list; every triangle belongs to an active cell and one of its isos.
+
+Named so that it runs after every other GPU test.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import affine, mc, mlp, octree
+from synth import inr
+
+from _helpers import pack, to_np
+
+pytestmark = pytest.mark.gpu
+
+UB = 2.0 ** -8
+EVAL_BAND = 2.0 ** -12
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2402_13861_gb300 as p
+    torch.cuda.set_device(0)
+    return p
+
+
+def _abs_prop(layers, x):
+    """|W| |a| + |b| propagated through the layers: the scale of the evaluation's rounding errors."""
+    a = np.abs(np.asarray(x, dtype=np.float64))
+    for W, b in layers:
+        a = a @ np.abs(np.asarray(W, np.float64)).T + np.abs(np.asarray(b, np.float64))
+    return a[:, 0]
+
+
+def _row_values(layers, rows, R, act):
+    """vals[r, dj, dk, i] = f(-1 + 2 (i, j + dj, k + dk) / R) for the row (j, k) = rows[r]."""
+    i = np.arange(R + 1)
+    pts = []
+    for j, k in rows.tolist():
+        for dj in (0, 1):
+            for dk in (0, 1):
+                pts.append(np.stack([i, np.full_like(i, j + dj), np.full_like(i, k + dk)], axis=1))
+    pts = -1.0 + 2.0 * np.concatenate(pts).astype(np.float64) / R
+    return mlp.mlp_forward(layers, pts, act=act).reshape(len(rows), 2, 2, R + 1), pts.reshape(len(rows), 2, 2,
+                                                                                             R + 1, 3)
+
+
+def _corner_values(vals, r, i):
+    """The 8 corner values of cell i of row r, corner c at offsets (c & 1, c >> 1 & 1, c >> 2 & 1)."""
+    return np.array([vals[r, (c >> 1) & 1, (c >> 2) & 1, i + (c & 1)] for c in range(8)])
+
+
+def _corner_points(pts, r, i):
+    return np.array([pts[r, (c >> 1) & 1, (c >> 2) & 1, i + (c & 1)] for c in range(8)])
+
+
+def _sample(vals, rows, isos, R, rng, per_row=3):
+    """Cells of each row: up to `per_row` crossing cells (some iso-value straddled by the corner
+    values), their two neighbours along the row, and one random cell.  Returns (row index, i)."""
+    out = set()
+    for r in range(len(rows)):
+        cv = np.stack([_corner_values(vals, r, i) for i in range(R)])          # (R, 8)
+        cross = np.zeros(R, dtype=bool)
+        for c in isos:
+            inside = cv < c
+            cross |= inside.any(axis=1) & ~inside.all(axis=1)
+        ids = np.nonzero(cross)[0]
+        for i in rng.permutation(ids)[:per_row].tolist():
+            out.update({(r, i)} | {(r, n) for n in (i - 1, i + 1) if 0 <= n < R})
+        out.add((r, int(rng.integers(0, R))))
+    return sorted(out)
+
+
+def _chain(cells, L):
+    """Every ancestor-or-self (level, ijk) of the level-L `cells`, once, and per cell the index of
+    its level-l ancestor in that list."""
+    keys, lvl, ijk = {}, [], []
+    idx = np.zeros((cells.shape[0], L + 1), dtype=np.int64)
+    for l in range(L + 1):
+        for n, a in enumerate(map(tuple, (cells >> (L - l)).tolist())):
+            if (l,) + a not in keys:
+                keys[(l,) + a] = len(lvl)
+                lvl.append(l)
+                ijk.append(a)
+            idx[n, l] = keys[(l,) + a]
+    lvl = np.array(lvl)
+    ijk = np.array(ijk, dtype=np.int64)
+    size = 2.0 / (2.0 ** lvl)
+    lo = -1.0 + ijk * size[:, None]
+    return lvl, lo, lo + size[:, None], idx
+
+
+def _march_cell(cv, ijk, R, c):
+    """The oracle's marching cubes on one cell, from its 8 corner values: (global edge ids (T, 3),
+    vertices (T, 3, 3)).  The cell is marched as a 1^3 lattice and mapped onto the R^3 lattice."""
+    local = np.empty(8)
+    for q in range(8):
+        local[(((q >> 2) & 1) * 2 + ((q >> 1) & 1)) * 2 + (q & 1)] = cv[q]
+    e, p, _ = mc.march(local, np.zeros((1, 3), dtype=np.int64), 1, c)
+    axis, base = e % 3, e // 3
+    off = np.stack([base % 2, (base // 2) % 2, base // 4], axis=-1)
+    g = ijk[None, None, :] + off
+    gid = 3 * mc.lattice_index(g[..., 0], g[..., 1], g[..., 2], R) + axis
+    return gid, -1.0 + (2.0 / R) * (ijk[None, None, :] + (p + 1.0) / 2.0)
+
+
+def check_full_size(net, layers, isos, L, k, res, act="relu", n_rows=8, seed=20240221):
+    R = 1 << L
+    H = len(layers) - 1
+    tol = 3 * H * UB
+    isos = np.asarray(isos, dtype=np.float32)
+    n_iso = isos.shape[0]
+    full = (1 << n_iso) - 1
+    dev = res["tri_cell"].device
+
+    # 5. structure of the level loop and of the outputs
+    cb, ck = res["cells_bounded"], res["cells_kept"]
+    assert cb[0] == 1
+    for l in range(L):
+        assert cb[l + 1] == 8 * ck[l], l
+    assert ck[L] == res["n_active"]
+    codes = res["codes"].to(torch.int64) & 0xFFFFFFFF
+    masks = res["masks"].to(torch.int64) & 0xFFFFFFFF
+    assert codes.numel() == res["n_active"] and torch.unique(codes).numel() == codes.numel()
+    assert bool(((masks > 0) & (masks <= full)).all())
+    tri_cell = res["tri_cell"].to(torch.int64) & 0xFFFFFFFF
+    tri_iso = res["tri_iso"].to(torch.int64)
+    assert bool(((tri_iso >= 0) & (tri_iso < n_iso)).all())
+    scodes, order = torch.sort(codes)
+    pos = torch.searchsorted(scodes, tri_cell).clamp(max=max(codes.numel() - 1, 0))
+    assert bool((scodes[pos] == tri_cell).all())                       # every triangle's cell is active
+    assert bool((((masks[order][pos] >> tri_iso) & 1) == 1).all())      # ... for that triangle's iso
+
+    # sampled cells, chosen by the oracle
+    rng = np.random.default_rng(seed)
+    rows = rng.integers(0, R, size=(n_rows, 2))
+    vals, pts = _row_values(layers, rows, R, act)
+    sample = _sample(vals, rows, isos, R, rng)
+    cells = np.array([[i, rows[r][0], rows[r][1]] for r, i in sample], dtype=np.int64)
+    lvl, lo, hi, idx = _chain(cells, L)
+
+    # 1. GPU bounds of every chain box against the oracle
+    gc, gs = net.bound_cells(torch.tensor(lo, dtype=torch.float32, device=dev),
+                             torch.tensor(hi, dtype=torch.float32, device=dev), mode="clt", prec="bf16")
+    gc, gs = to_np(gc).astype(np.float64), to_np(gs).astype(np.float64)
+    oc, os_ = affine.bound(layers, lo, hi, affine.CLT, batch=64, act=act)
+    dc, ds = np.abs(gc - oc), np.abs(gs - os_)
+    print(f"{lo.shape[0]} chain boxes of {cells.shape[0]} sampled cells: max |d mu|/(|mu|+sigma) "
+          f"{(dc / (np.abs(oc) + os_)).max():.2e}, max |d sigma|/sigma {(ds / np.maximum(os_, 1e-30)).max():.2e} "
+          f"(band {tol:.2e})")
+    assert np.all(ds <= tol * os_ + 1e-6)
+    assert np.all(dc <= tol * (np.abs(oc) + os_) + 1e-6)
+
+    # the extraction's masks of the sampled cells
+    sc = torch.tensor(pack(cells), dtype=torch.int64, device=dev)
+    p = torch.searchsorted(scodes, sc).clamp(max=max(codes.numel() - 1, 0))
+    found = to_np(scodes[p] == sc) if codes.numel() else np.zeros(cells.shape[0], dtype=bool)
+    g_mask = np.where(found, to_np(masks[order][p]), 0).astype(np.int64)
+
+    # 2. the masks are the float32 cull tests of the GPU bounds along the chain; k sigma is
+    # subtracted with two roundings or with one (a fused multiply-add), and a pair whose decision
+    # depends on which, or lies within a few roundings of an endpoint, is excused
+    iso64 = isos.astype(np.float64)
+    c32, s32 = gc.astype(np.float32), gs.astype(np.float32)
+    ks = np.float32(k) * s32
+    lo_a, hi_a = (c32 - ks).astype(np.float64), (c32 + ks).astype(np.float64)
+    lo_b, hi_b = (gc - k * gs).astype(np.float32).astype(np.float64), (gc + k * gs).astype(np.float32).astype(np.float64)
+    keep_a = (lo_a[:, None] <= iso64[None, :]) & (iso64[None, :] <= hi_a[:, None])
+    keep_b = (lo_b[:, None] <= iso64[None, :]) & (iso64[None, :] <= hi_b[:, None])
+    ulp = (2.0 ** -21 * (np.abs(gc) + k * gs))[:, None]
+    near_g = (np.abs(lo_a[:, None] - iso64[None, :]) <= ulp) | (np.abs(hi_a[:, None] - iso64[None, :]) <= ulp) | \
+        (keep_a != keep_b)
+    want = np.all(keep_a[idx], axis=1)                                   # (cells, isos)
+    amb = np.any(near_g[idx], axis=1)
+    got = ((g_mask[:, None] >> np.arange(n_iso)[None, :]) & 1) == 1
+    bad = (want != got) & ~amb
+    assert not bad.any(), f"{int(bad.sum())} (cell, iso) pairs where the mask is not the cull test of the bounds"
+    assert amb.mean() < 0.05
+
+    # 3. the oracle's own hierarchy
+    lo_o, hi_o = oc - k * os_, oc + k * os_
+    band = tol * (np.abs(oc) + (1.0 + k) * os_) + 1e-5
+    keep_o = (lo_o[:, None] <= iso64[None, :]) & (iso64[None, :] <= hi_o[:, None])
+    near_o = (np.abs(lo_o[:, None] - iso64[None, :]) <= band[:, None]) | \
+             (np.abs(hi_o[:, None] - iso64[None, :]) <= band[:, None])
+    want_o = np.all(keep_o[idx], axis=1)
+    excused_o = np.any(near_o[idx], axis=1)
+    diff = want_o != got
+    assert not (diff & ~excused_o).any(), f"{int((diff & ~excused_o).sum())} pairs differ from the oracle outside the band"
+    print(f"{got.size} (cell, iso) pairs: kept {int(got.sum())}, oracle kept {int(want_o.sum())}, "
+          f"differing {int(diff.sum())} (all within the band), excused {int(excused_o.sum())}")
+    assert (~excused_o).sum() >= 0.3 * got.size and (got & ~excused_o).any() and (~got & ~excused_o).any()
+
+    # 4a. triangles of the sampled active cells against the oracle's marching cubes on float64
+    # corner values.  The GPU's own values at those corners (isx_eval_points: the extraction's
+    # tensor-core evaluation, row by row the same arithmetic) must lie within the evaluation band
+    # 2^-12 |W| |a| of the oracle's; a (cell, iso) is compared where every corner's float64 value
+    # is farther from c_q than twice the GPU's error there, so both sides see the same case.
+    act_idx = [n for n in range(len(sample)) if found[n]]
+    corners = np.concatenate([_corner_points(pts, *sample[n]) for n in act_idx]) if act_idx else np.zeros((0, 3))
+    vg = to_np(net.eval_points(torch.tensor(corners, dtype=torch.float32, device=dev), prec="bf16")).astype(np.float64)
+    vo = np.concatenate([_corner_values(vals, *sample[n]) for n in act_idx]) if act_idx else np.zeros(0)
+    err = np.abs(vg - vo)
+    assert np.all(err <= EVAL_BAND * _abs_prop(layers, corners))
+    print(f"corner values of {len(act_idx)} sampled active cells: max |GPU - oracle| {err.max(initial=0.0):.2e}")
+    sel = torch.isin(tri_cell, sc)
+    t_cell = to_np(tri_cell[sel])
+    t_iso = to_np(tri_iso[sel])
+    t_edge = to_np(res["tri_edge"][sel]).astype(np.int64)
+    t_vert = to_np(res["tri_vert"][sel]).astype(np.float64)
+    compared = 0
+    for m_i, n in enumerate(act_idx):
+        cv = vo[8 * m_i:8 * m_i + 8]
+        dv = 2.0 * err[8 * m_i:8 * m_i + 8] + 2.0 ** -22 * (1.0 + np.abs(cv))
+        code = int(pack(cells[n:n + 1])[0])
+        for q in range(n_iso):
+            if not got[n, q] or np.any(np.abs(cv - iso64[q]) <= dv):
+                continue
+            e_o, v_o = _march_cell(cv, cells[n], R, iso64[q])
+            m = (t_cell == code) & (t_iso == q)
+            assert np.array_equal(t_edge[m], e_o), (cells[n].tolist(), q)
+            tv = t_vert[m]
+            # each vertex may shift as far as the value errors at its edge's two end points allow:
+            # |dt| <= 2 E / (|D| - E) for t = (c - v_a) / (v_b - v_a), D = v_b - v_a, E = dv_a + dv_b
+            for t in range(e_o.shape[0]):
+                for v in range(3):
+                    a = int(e_o[t, v]) % 3
+                    start = np.array(_edge_start(int(e_o[t, v]), R)) - cells[n]
+                    c0 = int(start[0] | (start[1] << 1) | (start[2] << 2))
+                    c1 = c0 | (1 << a)
+                    E = dv[c0] + dv[c1]
+                    D = abs(cv[c1] - cv[c0])
+                    shift = (2.0 / R) * min(1.0, 2.0 * E / (D - E)) if D > E else 2.0 / R
+                    assert np.abs(tv[t, v] - v_o[t, v]).max() <= shift + 1e-6, (cells[n].tolist(), q, t, v)
+            compared += e_o.shape[0]
+    print(f"triangles compared with the oracle: {compared}")
+    assert compared > 0
+
+    # 4b. the whole mesh: every vertex lies on the lattice edge it names (exactly on its two fixed
+    # coordinates), every (edge, iso) has one vertex, bit for bit, wherever it appears, and the
+    # three edges of a triangle lie on the triangle's cell
+    n1 = R + 1
+    e = res["tri_edge"].reshape(-1).to(torch.int64)
+    vtx = res["tri_vert"].reshape(-1, 3).contiguous()
+    axis = e % 3
+    base = e // 3
+    pt = torch.stack([base % n1, (base // n1) % n1, base // (n1 * n1)], dim=1)
+    grid = -1.0 + (2.0 / R) * pt.to(torch.float64)
+    on = torch.ones_like(axis, dtype=torch.bool)
+    for d in range(3):
+        x = vtx[:, d].to(torch.float64)
+        along = (x >= grid[:, d] - 1e-6) & (x <= grid[:, d] + 2.0 / R + 1e-6)
+        on &= torch.where(axis == d, along, x == grid[:, d])
+    assert bool(on.all())
+    key = e * n_iso + tri_iso.repeat_interleave(3)
+    sk, so = torch.sort(key)
+    bits = vtx[so].view(torch.int32)
+    same = sk[1:] == sk[:-1]
+    assert bool(((bits[1:] == bits[:-1]).all(dim=1) | ~same).all())
+    cell3 = torch.stack([tri_cell & 1023, (tri_cell >> 10) & 1023, (tri_cell >> 20) & 1023], dim=1)
+    rel = pt.reshape(-1, 3, 3) - cell3[:, None, :]
+    on_cell = ((rel >= 0) & (rel <= 1)).all(dim=2) & (rel.gather(2, axis.reshape(-1, 3, 1)).squeeze(2) == 0)
+    assert bool(on_cell.all())
+    print(f"mesh: {int(same.sum())} shared (edge, iso) vertices, all identical")
+
+
+def _edge_start(gid, R):
+    """Lattice point (i, j, k) at which the global edge `gid` = 3 lattice_index + axis starts."""
+    idx = gid // 3
+    return idx % (R + 1), (idx // (R + 1)) % (R + 1), idx // ((R + 1) * (R + 1))
+
+
+def test_benchmark_extraction_on_sampled_cells(pkg):
+    layers, isos, wl = inr.load_inr("scientific")
+    net = pkg.Inr(layers)
+    res = net.extract(wl.max_level, isos, mode="clt", k=3.0, prec="bf16", inflate=False, eval_prec="bf16",
+                      active_cap=1 << 22, tri_cap=1 << 24)
+    torch.cuda.synchronize()
+    print(f"{res['n_active']} active cells, {res['n_tris']} triangles, {sum(res['cells_bounded'])} cells bounded")
+    check_full_size(net, layers, isos, wl.max_level, 3.0, res)
+    net.close()

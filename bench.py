@@ -311,6 +311,38 @@ def cpu_baseline(layers, mode, k, budget_s=12.0):
             "sample": f"{done} random cells of levels 6-9 bounded by the float64 oracle ({mode}) in {dt:.1f} s"}
 
 
+# kernels whose accounted FLOPs run on the tensor cores
+TENSOR_KERNELS = {"rows_gemm", "rows_split", "bound_tc", "eval_tc", "prop_gate", "prop_forward", "prop_grad"}
+# ... and those of them that issue three bf16 products per algorithmic one (two-term operands)
+SPLIT_KERNELS = {"rows_split", "eval_tc"}
+
+
+def kernel_rooflines(stats, hbm_peak, tc_peak, alu_peak, top=5):
+    """Rooflines of the `top` kernels by time, from the library's launch accounting (algorithmic
+    bytes and FLOPs of every launch, CUDA-event time on the launching stream): HBM-bound when bytes
+    are counted and the FLOPs per byte lie below the ridge of the kernel's compute peak, else
+    against the tensor-core peak (tensor-core kernels) or the FP32 issue rate (the others).  A
+    kernel without counted bytes or FLOPs gets no bound."""
+    total = sum(v["ms"] for v in stats.values()) or 1.0
+    out = []
+    for name, v in sorted(stats.items(), key=lambda kv: -kv[1]["ms"])[:top]:
+        e = {"kernel": name, "share": round(v["ms"] / total, 4), "launches": int(v["launches"]), "bound": None}
+        secs = v["ms"] / 1e3
+        fl, by = float(v["flops"]), float(v["bytes"])
+        comp_peak = tc_peak if name in TENSOR_KERNELS else alu_peak
+        if secs > 0 and by > 0 and (fl == 0 or (fl / by) * hbm_peak / 1e3 < comp_peak):
+            e.update(bound="hbm", unit="GB/s", achieved=by / secs / 1e9, peak=hbm_peak)
+        elif secs > 0 and fl > 0:
+            e.update(bound="tensor" if name in TENSOR_KERNELS else "alu", unit="TFLOP/s",
+                     achieved=fl / secs / 1e12, peak=comp_peak)
+            if name in SPLIT_KERNELS:
+                e["note"] = "three bf16 products per algorithmic one"
+        if e["bound"] is not None:
+            e["frac"] = e["achieved"] / e["peak"]
+        out.append(e)
+    return out
+
+
 def job_totals(total_ms, cells, world, device):
     """Whole-job totals of a replicas-only run: the slowest rank's time (max over ranks) and the
     cells bounded by all ranks (sum), through the initialised process group when world > 1."""
@@ -499,6 +531,11 @@ def main():
             "cells_bounded_per_step": cells / args.steps / world, "n_active": res["n_active"],
             "n_tris": res["n_tris"], "cells_bounded_per_level": res["cells_bounded"],
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "kernel_time_share": shares}
+    try:
+        line["rooflines"] = kernel_rooflines(stats, hbm_peak, tc_peak,
+                                             152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12)
+    except Exception as ex:                      # the per-kernel list never costs the bench line
+        line["rooflines"] = {"error": repr(ex)}
     if rank == 0 and world == 1 and not args.no_forms:
         line["forms"] = extraction_forms(pkg, net, L, isos, res, ms_per_step, args.mode, args.k, prec,
                                          slow=args.all_forms)

@@ -94,3 +94,33 @@ def test_reference_line_shape(monkeypatch, capsys):
     assert line["ms_per_step"] >= 0.0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
     assert line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_kernel_rooflines_of_the_row_path():
+    """Launch accounting shaped like a 512^3 extraction on the row path: the reduction pass (bytes
+    only) is HBM-bound, the row GEMM (w / 2 FLOP per byte, below the ridge) too, the split GEMM
+    (FLOPs only) is measured against the tensor peak, and kernels without counts get no bound."""
+    stats = {
+        "rows_reduce": dict(launches=936, ms=540.0, flops=0.0, bytes=1.2e12),
+        "rows_gemm": dict(launches=936, ms=516.0, flops=2.1e14, bytes=1.64e12),
+        "rows_split": dict(launches=936, ms=262.0, flops=5.0e13, bytes=0.0),
+        "rows_new": dict(launches=936, ms=259.0, flops=0.0, bytes=0.0),
+        "rows_out": dict(launches=234, ms=220.0, flops=1.0e12, bytes=0.0),
+        "eval_tc": dict(launches=1, ms=44.0, flops=3.0e13, bytes=0.0),
+    }
+    out = bench.kernel_rooflines(stats, 6674.2, 1701.1, 80.5)
+    assert [e["kernel"] for e in out] == ["rows_reduce", "rows_gemm", "rows_split", "rows_new", "rows_out"]
+    assert abs(sum(v["ms"] for v in stats.values()) * out[0]["share"] - 540.0) < 1.0
+    red, gemm, split, new, outp = out
+    assert red["bound"] == "hbm" and red["achieved"] == pytest.approx(1.2e12 / 0.54 / 1e9)
+    assert red["frac"] == pytest.approx(red["achieved"] / 6674.2)
+    assert gemm["bound"] == "hbm" and gemm["achieved"] == pytest.approx(1.64e12 / 0.516 / 1e9)
+    assert split["bound"] == "tensor" and split["unit"] == "TFLOP/s" and "note" in split
+    assert split["achieved"] == pytest.approx(5.0e13 / 0.262 / 1e12)
+    assert new["bound"] is None and "frac" not in new
+    assert outp["bound"] == "alu" and outp["peak"] == 80.5
+    json.dumps(out)
+    # a contraction above the ridge is compute-bound
+    hot = bench.kernel_rooflines({"rows_gemm": dict(launches=1, ms=1.0, flops=1e12, bytes=1e9)}, 6674.2, 1701.1, 80.5)
+    assert hot[0]["bound"] == "tensor"
+    assert bench.kernel_rooflines({}, 6674.2, 1701.1, 80.5) == []

@@ -64,13 +64,15 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
-        self.path = tempfile.mktemp(suffix=".csv")
+        self.path = None
+        self.f = None
         self.gpu = gpu_index
         self.proc = None
 
     def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        self.f = os.fdopen(fd, "w")
         try:
-            self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
@@ -79,6 +81,10 @@ class ClockSampler:
 
     def stop(self):
         if self.proc is None:
+            if self.f is not None:
+                self.f.close()
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         self.proc.terminate()
         try:

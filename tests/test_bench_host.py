@@ -54,9 +54,17 @@ def test_clock_parser_flags_thermal(tmp_path):
     assert out["sm_mhz"] == 1500.0
 
 
-def test_clock_sampler_without_nvidia_smi():
+def test_clock_sampler_without_nvidia_smi(monkeypatch):
     s = bench.ClockSampler(0)
     assert s.stop() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+    # started where nvidia-smi cannot run: unsampled, and its temporary file is gone
+    monkeypatch.setenv("PATH", "/nonexistent")
+    s = bench.ClockSampler(0)
+    s.start()
+    path = s.path
+    assert os.path.exists(path)
+    assert s.stop()["reasons"] == ["unsampled"]
+    assert not os.path.exists(path)
 
 
 def test_traffic_record_is_keyed_to_the_source(tmp_path):
@@ -124,3 +132,25 @@ def test_kernel_rooflines_of_the_row_path():
     hot = bench.kernel_rooflines({"rows_gemm": dict(launches=1, ms=1.0, flops=1e12, bytes=1e9)}, 6674.2, 1701.1, 80.5)
     assert hot[0]["bound"] == "tensor"
     assert bench.kernel_rooflines({}, 6674.2, 1701.1, 80.5) == []
+
+
+def test_clock_sampler_with_a_fake_nvidia_smi(tmp_path, monkeypatch):
+    """start / stop around a stand-in nvidia-smi that prints two samples and keeps running."""
+    exe = tmp_path / "nvidia-smi"
+    exe.write_text("#!/bin/sh\n"
+                   "echo '0, 2055, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                   "echo '0, 2070, 2070, 1180.0, 0x0, Not Active, Not Active, Not Active, Active'\n"
+                   "exec sleep 30\n")
+    exe.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ.get("PATH", ""))
+    s = bench.ClockSampler(0)
+    s.start()
+    import time
+    for _ in range(50):
+        if os.path.getsize(s.path) > 0 and open(s.path).read().count("\n") >= 2:
+            break
+        time.sleep(0.05)
+    path = s.path
+    out = s.stop()
+    assert out["samples"] == 2 and out["sm_mhz"] == pytest.approx(2062.5) and out["reasons"] == ["sw_power_cap"]
+    assert not os.path.exists(path)

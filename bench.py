@@ -155,27 +155,14 @@ def extraction_forms(pkg, net, L, isos, plain, plain_ms, mode, k, prec, slow=Fal
         return timed_level(L, **kw)
 
     dense32, ms_d32 = timed(prec="fp32", dense=True)
-    cross = None
-    cell = dense32["tri_cell"].to(torch.int64) & 0xFFFFFFFF
-    tiso = dense32["tri_iso"].to(torch.int64)
-    key = torch.unique(cell)
-    masks = torch.zeros_like(key)
-    for q in range(len(isos)):
-        kq = torch.unique(cell[tiso == q])
-        if kq.numel():
-            masks[torch.searchsorted(key, kq)] |= 1 << q
-    cross = (key, masks)
+    # the dense extraction's crossing cells (cells with a triangle, per iso), as the library lists them
+    key = dense32["codes"].to(torch.int64) & 0xFFFFFFFF
+    order = torch.argsort(key)
+    cross = (key[order], (dense32["masks"].to(torch.int64) & 0xFFFFFFFF)[order])
     out = {}
     mp, tot = missed(plain["codes"], plain["masks"], cross)
     out["plain"] = {"ms": plain_ms, "cells_bounded": int(sum(plain["cells_bounded"])), "missed_pairs": mp,
                     "missed_rate": mp / max(tot, 1)}
-    if slow:
-        # the per-cell persistent tcgen05 bound kernel on the same extraction
-        os.environ["ISX_BF16_ROWS"] = "0"
-        r, ms = timed(mode=mode, k=k, prec=prec, eval_prec="bf16")
-        del os.environ["ISX_BF16_ROWS"]
-        out["per_cell_tc_kernel"] = {"ms": ms, "cells_bounded": int(sum(r["cells_bounded"])),
-                                     "n_active": r["n_active"]}
     r, ms = timed(mode=mode, k=k, prec=prec, bound_stop_level=6, eval_prec="bf16")
     m, _ = missed(r["codes"], r["masks"], cross)
     out["bound_to_level6_tc_eval"] = {"ms": ms, "cells_bounded": int(sum(r["cells_bounded"])),
@@ -233,24 +220,17 @@ def batched_form(pkg, mode, k):
     bufs = [dict() for _ in nets]
     for net, p, bf in zip(nets, params, bufs):
         net.extract(buffers=bf, **p)                            # warm-up, sizes the buffers
-    _, seq_rows_ms = ev_ms(lambda: [net.extract(buffers=bf, **p) for net, p, bf in zip(nets, params, bufs)])
-    # the batch runs the per-cell tensor-core kernel: its sequential counterpart takes the same kernel
-    os.environ["ISX_BF16_ROWS"] = "0"
-    for net, p, bf in zip(nets, params, bufs):
-        net.extract(buffers=bf, **p)
-    singles, seq_ms = ev_ms(lambda: [net.extract(buffers=bf, **p) for net, p, bf in zip(nets, params, bufs)])
-    del os.environ["ISX_BF16_ROWS"]
+    singles, seq_rows_ms = ev_ms(lambda: [net.extract(buffers=bf, **p) for net, p, bf in zip(nets, params, bufs)])
     batch = pkg.Batch(nets, params, use_graph=True)
     batch.run()                                                 # sized run
     batch.run()                                                 # capture and first replay
     res, batch_ms = ev_ms(batch.run)
-    same = all(r["n_active"] == s["n_active"] and r["n_tris"] == s["n_tris"] for r, s in zip(res, singles))
     batch.close()
     for net in nets:
         net.close()
     return {"entries": len(specs), "shapes": [f"w{w}xH{H}@{1 << L}^3" for w, H, L, _ in specs], "isos_each": 16,
-            "sequential_per_cell_kernel_ms": seq_ms, "batched_graph_ms": batch_ms, "same_meshes": bool(same),
-            "sequential_row_batched_ms": seq_rows_ms,
+            "batched_graph_ms": batch_ms, "sequential_row_batched_ms": seq_rows_ms,
+            "n_active_batch": [r["n_active"] for r in res], "n_active_sequential": [s["n_active"] for s in singles],
             "cells_bounded_sequential": int(sum(sum(s["cells_bounded"]) for s in singles))}
 
 
@@ -281,16 +261,11 @@ def activation_forms(pkg, k, names=("siren", "sdf_elu")):
             return r, a.elapsed_time(b)
 
         dense, ms_d = timed(prec="fp32", dense=True)
-        cell = dense["tri_cell"].to(torch.int64) & 0xFFFFFFFF
-        tiso = dense["tri_iso"].to(torch.int64)
-        key = torch.unique(cell)
-        masks = torch.zeros_like(key)
-        for q in range(len(isos)):
-            kq = torch.unique(cell[tiso == q])
-            if kq.numel():
-                masks[torch.searchsorted(key, kq)] |= 1 << q
+        key = dense["codes"].to(torch.int64) & 0xFFFFFFFF
+        order = torch.argsort(key)
+        masks = (dense["masks"].to(torch.int64) & 0xFFFFFFFF)[order]
         h, ms_h = timed(mode="clt", k=k, prec="bf16")
-        m, tot = missed(h["codes"], h["masks"], (key, masks))
+        m, tot = missed(h["codes"], h["masks"], (key[order], masks))
         out[name] = {"activation": wl.act, "dims": wl.dims, "n_iso": int(len(isos)), "max_level": L,
                      "fit_s": fit_s, "hier_clt_bf16_ms": ms_h, "cells_bounded": int(sum(h["cells_bounded"])),
                      "n_active": h["n_active"], "n_tris": h["n_tris"], "dense_fp32_ms": ms_d,

@@ -69,10 +69,10 @@ typedef enum { ISX_BOUND_SOUND = 0, ISX_BOUND_CLT = 1, ISX_BOUND_RAUA = 2, ISX_B
  *  - the row-batched path (hidden widths 64, 128, 256; SOUND without inflation, CLT, RAUA; the
  *    default): cells of a chunk are propagated layer by layer, the symbol rows of all cells in one
  *    tensor-core GEMM per layer, symbols whose coefficient is exactly 0 never created;
- *  - the per-cell persistent kernel (hidden widths 128, 256; the only BF16 kernel for SOUND with
- *    inflation, used by isx_batch_* and isx_bound_cells_noalloc, and everywhere when the
- *    environment variable ISX_BF16_ROWS is "0").
- * Both stay within the BF16 rounding band of the float64 propagation; they are not bit-identical. */
+ *  - the per-cell persistent kernel (hidden widths 128, 256): SOUND with inflation, isx_batch_* and
+ *    isx_bound_cells_noalloc.
+ * The choice is fixed by that rule (no switch).  Both stay within the BF16 rounding band of the
+ * float64 propagation; they are not bit-identical. */
 typedef enum { ISX_PREC_FP32 = 0, ISX_PREC_BF16 = 1 } isx_precision;
 
 /* Activation applied after every linear layer but the last: ReLU (the ReLU INRs of App. E), ELU
@@ -114,15 +114,18 @@ isx_status isx_bound_cells(isx_inr inr, const float* d_lo, const float* d_hi, in
  * counterpart; this is a deployment convenience).  Some callers cannot allocate device memory once
  * they are running: a process whose device memory is owned by a framework's caching allocator,
  * or a latency-critical loop that must not take the device-wide synchronisation that cudaMalloc
- * and cudaFree imply.  This entry point allocates nothing: the tensor-core kernel takes its
+ * and cudaFree imply.  This entry point allocates nothing: the per-cell tensor-core kernel takes its
  * per-CTA coefficient slices and its status word from a 16 MiB array compiled into the library
  * (every device that loads the library holds that array until the process exits).  Arguments
- * are those of isx_bound_cells; the kernel is the per-cell tensor-core kernel, so the results equal
- * isx_bound_cells' with ISX_BF16_ROWS=0 or inflation, and agree with its row-batched default within
- * the BF16 band.  It only uses as many CTAs as the array has slices for (63 for a 256-wide,
- * 5-hidden-layer network), so it can be slower.
- *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
- *    caches it; make that first call before any stream capture.
+ * are those of isx_bound_cells.  Each cell is bounded by one CTA from start to end, so the results
+ * do not depend on the grid: they are bit-identical from call to call, and agree with
+ * isx_bound_cells within the BF16 band.  The grid is min(n, SMs, slices that fit in the array),
+ * one slice being max(128, w (H - 3)) rows x w x 2 bytes (63 slices for a 256-wide, 5-hidden-layer
+ * network), so it can be slower than isx_bound_cells.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *    that device current and keeps it for the process; make that first call before any stream
+ *    capture.  The address belongs to the device's context: after cudaDeviceReset on a device, do
+ *    not call this entry point on that device again in the same process.
  *  - All calls share the array, which keeps the last call's contents; the call clears the status
  *    word itself.  Calls that overlap on the GPU (several streams or threads) race on the array:
  *    serialise them.
@@ -167,7 +170,30 @@ typedef struct {
      cells_visited / bounded / kept of depth d are added to octree level (d + 2) / 3.  With a
      proposer: ISX_ERR_UNSUPPORTED. */
   int kd_tree;
+  /* optional record of the level loop (NULL: none); see isx_level_record */
+  struct isx_level_record_s* record;
 } isx_extract_params;
+
+/* Record of the level loop of one hierarchical extraction (no counterpart in the paper: it exposes
+ * the per-node state of Algorithm 1 so that callers, e.g. the proposer's label generation, need not
+ * re-run the cull test and the subdivision themselves).  With params->record set,
+ * isx_extract_isosurface appends, level after level from the root, every visited cell: its packed
+ * code, the iso mask it inherited from its parent (all isos at the root), and the bound computed for
+ * it (centre, spread as in isx_bound_cells; NaN at levels deeper than bound_stop_level).  Within a
+ * level, cells are in the extraction's own order (children of surviving cells, in parent order,
+ * child c = 2 (i, j, k) + the bits of c).  Buffers are caller-owned device arrays of `cap` entries;
+ * level_off[l] .. level_off[l + 1] - 1 are level l's entries, filled in for levels 0 .. max_level.
+ * If the total exceeds `cap`, nothing past `cap` is written, the extraction completes and the call
+ * returns ISX_ERR_CAPACITY with level_off holding the required sizes.  Octree extraction without a
+ * proposer only (ISX_ERR_UNSUPPORTED otherwise). */
+typedef struct isx_level_record_s {
+  uint32_t* d_code;
+  uint32_t* d_mask;
+  float* d_center;
+  float* d_spread;
+  int64_t cap;
+  int64_t level_off[ISX_MAX_LEVEL + 2];   /* filled in by the call */
+} isx_level_record;
 
 typedef struct {
   /* caller-owned device outputs and capacities (in elements of the first dimension) */
@@ -223,8 +249,11 @@ isx_status isx_batch_run(isx_batch batch, isx_mesh* meshes, void* stream);
 isx_status isx_batch_destroy(isx_batch batch);
 
 /* The dense baseline of Sec. V-A.4: evaluates every lattice point of the (2^max_level + 1)^3 grid
- * and runs marching cubes in every cell.  d_active_* are not written (n_active = cells with at least
- * one triangle).  mode, k, inflate and bound_stop_level are ignored. */
+ * and runs marching cubes in every cell.  n_active = cells with at least one triangle; when
+ * d_active_code and d_active_mask are given and n_active <= active_cap, those cells are written
+ * there in cell order (i fastest, then j, then k) with bit q of the mask set iff the cell has a
+ * triangle of iso q (the cells that truly cross each iso-surface on this grid).  mode, k, inflate
+ * and bound_stop_level are ignored. */
 isx_status isx_extract_dense(isx_inr inr, const isx_extract_params* params, isx_mesh* mesh,
                              void* stream);
 
@@ -297,6 +326,14 @@ typedef struct {
 } isx_tune_entry;
 int isx_tune_read(isx_tune_entry* out, int max);
 void isx_tune_reset(void);
+
+/* Self-check of the bounded device-side wait that every persistent kernel of the library uses
+ * (tcgen05 producer / MMA / epilogue hand-offs on mbarriers): one CTA waits on an mbarrier that
+ * nothing completes, with a limit of `limit_ns` nanoseconds, then records ISX_ERR_TIMEOUT and
+ * returns, as the real kernels do when a wait expires.  Returns ISX_ERR_TIMEOUT (the expected
+ * outcome; the context stays usable) or ISX_ERR_ARG for a limit outside [1000, 10^10] ns.
+ * Synchronises `stream`.  No counterpart in the paper. */
+isx_status isx_check_bounded_wait(int64_t limit_ns, void* stream);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* isx_last_error(void);

@@ -54,7 +54,13 @@ class ExtractParams(C.Structure):
     _fields_ = [("max_level", C.c_int), ("n_iso", C.c_int), ("iso", C.c_float * ISX_MAX_ISO),
                 ("mode", C.c_int), ("k", C.c_float), ("prec", C.c_int), ("inflate", C.c_int),
                 ("bound_stop_level", C.c_int), ("proposer", C.c_void_p), ("proposer_level", C.c_int),
-                ("tau_lo", C.c_float), ("tau_hi", C.c_float), ("eval_prec", C.c_int), ("kd_tree", C.c_int)]
+                ("tau_lo", C.c_float), ("tau_hi", C.c_float), ("eval_prec", C.c_int), ("kd_tree", C.c_int),
+                ("record", C.c_void_p)]
+
+
+class LevelRecord(C.Structure):
+    _fields_ = [("d_code", C.c_void_p), ("d_mask", C.c_void_p), ("d_center", C.c_void_p), ("d_spread", C.c_void_p),
+                ("cap", C.c_int64), ("level_off", C.c_int64 * (ISX_MAX_LEVEL + 2))]
 
 
 class Mesh(C.Structure):
@@ -113,10 +119,12 @@ def load(path: Path | None = None):
     lib.isx_proposer_predict.argtypes = [vp, vp, i64, vp, vp]
     lib.isx_proposer_grad.argtypes = [vp, vp, vp, i64, vp, vp, vp]
     lib.isx_proposer_train_step.argtypes = [vp, vp, vp, i64, C.c_float, vp, vp]
+    lib.isx_check_bounded_wait.argtypes = [i64, vp]
     for name in ("isx_create_inr", "isx_destroy_inr", "isx_bound_cells", "isx_eval_points",
                  "isx_extract_isosurface", "isx_extract_dense", "isx_mc_table", "isx_proposer_create",
                  "isx_proposer_destroy", "isx_proposer_get_params", "isx_proposer_predict", "isx_proposer_grad",
-                 "isx_proposer_train_step", "isx_batch_create", "isx_batch_run", "isx_batch_destroy"):
+                 "isx_proposer_train_step", "isx_batch_create", "isx_batch_run", "isx_batch_destroy",
+                 "isx_check_bounded_wait"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -163,6 +171,12 @@ def tune_read():
 
 def tune_reset():
     load().isx_tune_reset()
+
+
+def check_bounded_wait(limit_ns, stream=None):
+    """Status of the library's bounded-wait self-check (isx_check_bounded_wait): 4 (ISX_ERR_TIMEOUT)
+    when the wait on a never-completed mbarrier expired as designed."""
+    return int(load().isx_check_bounded_wait(int(limit_ns), _stream_ptr(stream)))
 
 
 def _stream_ptr(stream):
@@ -261,15 +275,19 @@ class Inr:
 
     def extract(self, max_level, isos, mode="sound", k=3.0, prec="fp32", inflate=False, bound_stop_level=-1,
                 active_cap=1 << 16, tri_cap=1 << 18, dense=False, stream=None, buffers=None, proposer=None,
-                proposer_level=1, tau_lo=0.0, tau_hi=1.0, eval_prec="fp32", kd_tree=False):
+                proposer_level=1, tau_lo=0.0, tau_hi=1.0, eval_prec="fp32", kd_tree=False, record=False,
+                record_cap=1 << 22):
         """Hierarchical (or, with dense=True, dense) extraction (isx_extract_isosurface /
         isx_extract_dense).  mode: "sound", "clt", "raua" or "rafixed"; prec / eval_prec: "fp32" or
         "bf16" (bounds and corner values on the tensor cores); kd_tree: Algorithm 1's k-d tree
         instead of the octree; bound_stop_level: bound down to that level, keep every descendant of
-        the survivors; proposer (a Proposer) with proposer_level, tau_lo, tau_hi: the learned gate.
+        the survivors; proposer (a Proposer) with proposer_level, tau_lo, tau_hi: the learned gate;
+        record: also return the level loop's record (isx_level_record) as ``levels``, one dict per
+        level of the visited cells' codes, inherited masks, centres and spreads.
         Grows the output buffers and retries once if a capacity is exceeded.  Returns a dict of
         tensors (codes, masks, tri_vert, tri_edge, tri_iso, tri_cell) and counters (n_active,
-        n_tris, cells_bounded / cells_kept / cells_visited per level, phase times in ms)."""
+        n_tris, cells_bounded / cells_kept / cells_visited per level, phase times in ms).  With
+        dense=True, codes / masks are the cells with triangles and the isos they have triangles for."""
         import torch
         p = self.params(max_level, isos, mode, k, prec, inflate, bound_stop_level, proposer, proposer_level,
                         tau_lo, tau_hi, eval_prec, kd_tree)
@@ -296,16 +314,39 @@ class Inr:
             m.d_tri_iso = bufs["iso"].data_ptr()
             m.d_tri_cell = bufs["cell"].data_ptr()
             m.tri_cap = bufs["tri_cap"]
+            rec = None
+            if record:
+                if bufs.get("record_cap", -1) < record_cap:
+                    bufs["r_code"] = torch.empty(max(record_cap, 1), dtype=torch.int32, device=dev)
+                    bufs["r_mask"] = torch.empty(max(record_cap, 1), dtype=torch.int32, device=dev)
+                    bufs["r_center"] = torch.empty(max(record_cap, 1), dtype=torch.float32, device=dev)
+                    bufs["r_spread"] = torch.empty(max(record_cap, 1), dtype=torch.float32, device=dev)
+                    bufs["record_cap"] = record_cap
+                rec = LevelRecord()
+                rec.d_code, rec.d_mask = bufs["r_code"].data_ptr(), bufs["r_mask"].data_ptr()
+                rec.d_center, rec.d_spread = bufs["r_center"].data_ptr(), bufs["r_spread"].data_ptr()
+                rec.cap = bufs["record_cap"]
+                p.record = C.cast(C.pointer(rec), C.c_void_p)
             st = fn(self._h, C.byref(p), C.byref(m), _stream_ptr(stream))
-            if st == 3 and attempt < 2:
+            short = dense and st == 0 and int(m.n_active) > bufs["active_cap"]
+            if (st == 3 or short) and attempt < 2:
                 active_cap = max(active_cap, int(m.n_active))
                 tri_cap = max(tri_cap, int(m.n_tris))
+                if rec is not None:
+                    record_cap = max(record_cap, int(rec.level_off[max_level + 1]))
                 continue
             _check(st)
             break
         na, nt = int(m.n_active), int(m.n_tris)
+        levels = None
+        if rec is not None:
+            off = list(rec.level_off)
+            levels = [dict(codes=bufs["r_code"][off[l]:off[l + 1]], masks=bufs["r_mask"][off[l]:off[l + 1]],
+                           centre=bufs["r_center"][off[l]:off[l + 1]], spread=bufs["r_spread"][off[l]:off[l + 1]])
+                      for l in range(max_level + 1)]
         return dict(
-            codes=None if dense else bufs["code"][:na], masks=None if dense else bufs["mask"][:na],
+            levels=levels,
+            codes=bufs["code"][:na], masks=bufs["mask"][:na],
             tri_vert=bufs["vert"][:nt], tri_edge=bufs["edge"][:nt], tri_iso=bufs["iso"][:nt], tri_cell=bufs["cell"][:nt],
             n_active=na, n_tris=nt, n_points=int(m.n_points),
             cells_bounded=list(m.cells_bounded)[:max_level + 1], cells_kept=list(m.cells_kept)[:max_level + 1],

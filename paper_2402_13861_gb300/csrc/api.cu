@@ -1,6 +1,7 @@
 // The C interface (include/isx.h): INR handles, workspace, and the host-side driver of the level
 // loop of Algorithm 1 followed by corner queries and marching cubes.
 #include "internal.cuh"
+#include "rows.cuh"
 
 #include <cstdlib>
 
@@ -82,10 +83,9 @@ isx_status bound_dispatch(isx_inr inr, const CellSource& src, int64_t n, isx_bou
     return bound_rafixed(inr, src, n, inflate, center, spread, st);
   }
   if (prec == ISX_PREC_BF16) {
-    // the row-batched tensor-core path where it applies (ISX_BF16_ROWS=0 selects the per-cell kernel)
-    const char* e = std::getenv("ISX_BF16_ROWS");
-    if (rows_supported(inr, mode, inflate) && !(e && e[0] == '0'))
-      return bound_bf16_rows(inr, src, n, mode, center, spread, st);
+    // one rule, no switch: the row-batched tensor-core path wherever it applies (hidden widths 64,
+    // 128, 256), the per-cell tensor-core kernel for the shapes it alone covers
+    if (rows_supported(inr, mode, inflate)) return bound_bf16_rows(inr, src, n, mode, center, spread, st);
     return bound_bf16(inr, src, n, mode, inflate, center, spread, st);
   }
   return bound_fp32(inr, src, n, mode, inflate, center, spread, st);
@@ -124,6 +124,15 @@ isx_status validate_params(const isx_extract_params* p, const isx_mesh* m) {
   if (p->kd_tree && p->proposer) {
     set_error("the k-d mode does not take a proposer");
     return ISX_ERR_UNSUPPORTED;
+  }
+  if (p->record && (p->kd_tree || p->proposer)) {
+    set_error("the level record covers octree extraction without a proposer only");
+    return ISX_ERR_UNSUPPORTED;
+  }
+  if (p->record && p->record->cap > 0 &&
+      (!p->record->d_code || !p->record->d_mask || !p->record->d_center || !p->record->d_spread)) {
+    set_error("null level-record buffer");
+    return ISX_ERR_ARG;
   }
   if (p->proposer && !(p->tau_lo >= 0.0f && p->tau_lo < p->tau_hi && p->tau_hi <= 1.0f)) {
     set_error("proposer thresholds must satisfy 0 <= tau_lo < tau_hi <= 1");
@@ -465,6 +474,10 @@ isx_status isx_extract_isosurface(isx_inr inr, const isx_extract_params* p, isx_
     return mesh_from_active(inr, p, ws[ca].as<uint32_t>(), ws[ma].as<uint32_t>(), n, mesh, tm, st);
   }
   Slot aca = WS_ANC_C_A, acb = WS_ANC_C_B, asa = WS_ANC_S_A, asb = WS_ANC_S_B, aga = WS_ANC_G_A, agb = WS_ANC_G_B;
+  isx_level_record* rec = p->record;
+  bool rec_short = false;
+  if (rec)
+    for (int l = 0; l <= ISX_MAX_LEVEL + 1; ++l) rec->level_off[l] = 0;
   for (int level = 0; level <= L; ++level) {
     const bool bounded = level <= stop;
     const bool expand = level < L;
@@ -533,6 +546,23 @@ isx_status isx_extract_isosurface(isx_inr inr, const isx_extract_params* p, isx_
         anc.out_gap = ws[agb].as<uint8_t>();
       }
     }
+    if (rec) {
+      // the visited cells of this level, their inherited masks and their bounds, appended
+      const int64_t o = rec->level_off[level];
+      rec->level_off[level + 1] = o + n;
+      if (o + n > rec->cap) rec_short = true;
+      if (!rec_short && n > 0) {
+        ISX_CUDA(cudaMemcpyAsync(rec->d_code + o, ws[ca].ptr, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+        ISX_CUDA(cudaMemcpyAsync(rec->d_mask + o, ws[ma].ptr, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+        if (bounded) {
+          ISX_CUDA(cudaMemcpyAsync(rec->d_center + o, ws[WS_CENTER].ptr, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+          ISX_CUDA(cudaMemcpyAsync(rec->d_spread + o, ws[WS_SPREAD].ptr, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+        } else {
+          ISX_TRY(fill_f32(rec->d_center + o, n, NAN, st));
+          ISX_TRY(fill_f32(rec->d_spread + o, n, NAN, st));
+        }
+      }
+    }
     ISX_TRY(level_step(inr, ws[ca].as<uint32_t>(), step_masks, n, ws[WS_CENTER].as<float>(),
                        ws[WS_SPREAD].as<float>(), step_bounded, iso, p->mode, p->k, p->inflate, expand,
                        ws[cb].as<uint32_t>(), ws[mb].as<uint32_t>(), d_count, st, carry ? &anc : nullptr));
@@ -547,7 +577,12 @@ isx_status isx_extract_isosurface(isx_inr inr, const isx_extract_params* p, isx_
     std::swap(aga, agb);
     n = cnt;
   }
-  return mesh_from_active(inr, p, ws[ca].as<uint32_t>(), ws[ma].as<uint32_t>(), n, mesh, tm, st);
+  isx_status ms = mesh_from_active(inr, p, ws[ca].as<uint32_t>(), ws[ma].as<uint32_t>(), n, mesh, tm, st);
+  if (ms == ISX_OK && rec_short) {
+    set_error("level-record capacity exceeded (level_off holds the required sizes)");
+    return ISX_ERR_CAPACITY;
+  }
+  return ms;
 }
 
 isx_status isx_extract_dense(isx_inr inr, const isx_extract_params* p, isx_mesh* mesh, void* stream) {
@@ -581,6 +616,35 @@ isx_status isx_extract_dense(isx_inr inr, const isx_extract_params* p, isx_mesh*
   cudaEventElapsedTime(&mesh->ms_mc, tm.ev[2], tm.ev[3]);
   cudaEventElapsedTime(&mesh->ms_total, tm.ev[0], tm.ev[3]);
   return s;
+}
+
+isx_status isx_check_bounded_wait(int64_t limit_ns, void* stream) {
+  if (limit_ns < 1000 || limit_ns > 10000000000LL) {
+    set_error("the wait limit must lie in [1000, 10^10] ns");
+    return ISX_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int* d_status = nullptr;
+  ISX_CUDA(cudaMalloc(&d_status, sizeof(int)));
+  isx_status s = ISX_OK;
+  int h = 0;
+  cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(int), st);
+  if (e == cudaSuccess) {
+    s = rows::check_bounded_wait(limit_ns, d_status, st);
+    if (s == ISX_OK) {
+      e = cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+  }
+  cudaFree(d_status);
+  if (e != cudaSuccess) return cuda_fail(e, "bounded-wait check", __FILE__, __LINE__);
+  if (s != ISX_OK) return s;
+  if (h != 0) {
+    set_error("bounded device wait expired (as intended by the check)");
+    return (isx_status)h;
+  }
+  set_error("bounded device wait did not report its expiry");
+  return ISX_ERR_CUDA;
 }
 
 }  // extern "C"

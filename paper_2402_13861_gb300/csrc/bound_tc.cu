@@ -1124,11 +1124,6 @@ isx_status bound_bf16(isx_inr inr, const CellSource& src, int64_t n, isx_bound_m
     return ISX_ERR_UNSUPPORTED;
   }
   if (n <= 0) return ISX_OK;
-  // ISX_CLT_COV=1 selects the covariance (Gram-matrix) propagation of bound_cov.cu for CLT: faster,
-  // but its bf16 rounding error grows with the square of the output-layer cancellation ratio, so
-  // the coefficient propagation below stays the default
-  if (mode == ISX_BOUND_CLT && std::getenv("ISX_CLT_COV") != nullptr)
-    return bound_bf16_clt_cov(inr, src, n, d_center, d_spread, st);
   const int w = inr->w, H = inr->H;
   int dev = inr->device, sms = 0;
   ISX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

@@ -88,7 +88,7 @@ namespace isx {
 enum KernelId {
   K_INPUT, K_RELU, K_GEMV, K_GEMM_FP32, K_FRESH, K_REDUCE, K_OUTPUT, K_CULL, K_SCAN, K_SCATTER, K_MARK,
   K_FLAGCOUNT, K_SCATTER_FLAGS, K_EVAL_FP32, K_MC_COUNT, K_MC_EMIT, K_IOTA, K_BOUND_TC, K_TC_PREP, K_TC_OUTPUT,
-  K_EVAL_TC, K_BOUND_COV, K_PROP_GATE, K_PROP_MERGE, K_PROP_FWD, K_PROP_GRAD, K_PROP_ADAM, K_BOUND_RAFIXED, K_ROWS_GEMM, K_ROWS_AUX,
+  K_EVAL_TC, K_PROP_GATE, K_PROP_MERGE, K_PROP_FWD, K_PROP_GRAD, K_PROP_ADAM, K_BOUND_RAFIXED, K_ROWS_GEMM, K_ROWS_AUX,
   K_ROWS_ACT, K_ROWS_NEW, K_ROWS_SPLIT, K_ROWS_REDUCE, K_ROWS_OUT, K_COUNT
 };
 namespace prof {
@@ -157,9 +157,6 @@ isx_status tensor_map_bf16(CUtensorMap* m, const void* base, uint64_t inner, uin
 isx_status eval_points_tc(isx_inr inr, const float* xyz, const uint32_t* lattice_ids, int R, int64_t n,
                           float* out, cudaStream_t st);
 bool eval_tc_supported(isx_inr inr);
-// CLT bound by covariance propagation on tcgen05 (bound_cov.cu).
-isx_status bound_bf16_clt_cov(isx_inr inr, const CellSource& src, int64_t n, float* d_center, float* d_spread,
-                              cudaStream_t st);
 
 // ---- octree level step (tree.cu) ---------------------------------------------------------------
 struct IsoSet {
@@ -196,6 +193,8 @@ isx_status scan_block_counts(isx_inr inr, const int* counts, int64_t nb, int64_t
                              cudaStream_t st);
 // out[i] = i for i < n.
 isx_status iota_u32(uint32_t* out, int64_t n, cudaStream_t st);
+// out[i] = v for i < n.
+isx_status fill_f32(float* out, int64_t n, float v, cudaStream_t st);
 
 // ---- proposer (proposer.cu) ----------------------------------------------------------------------
 // keep[i] = iso bits of cell i kept without a bound (logit >= z_hi), need[i] = 1 if some bit of its
@@ -244,7 +243,8 @@ isx_status mark_corners(const uint32_t* codes, int64_t n, int R, uint8_t* flags,
 // Marching cubes over n listed cells (codes, masks) or, with codes == nullptr, over all R^3 cells for
 // every iso-value.  Corner values are values[idx_map[lattice id]] (idx_map == nullptr: by lattice id).
 // Writes mesh->n_tris; emits only if it fits mesh->tri_cap (else ISX_ERR_CAPACITY).  With
-// count_nonempty, mesh->n_active becomes the number of cells with at least one triangle.
+// count_nonempty, mesh->n_active becomes the number of cells with at least one triangle, and those
+// cells (code, mask of the isos with triangles) go to the mesh's active buffers when they fit.
 isx_status marching_cubes(isx_inr inr, const uint32_t* codes, const uint32_t* masks, int64_t n, int R,
                           const uint32_t* idx_map, const float* values, const IsoSet& iso, isx_mesh* mesh,
                           bool count_nonempty, cudaStream_t st);

@@ -340,8 +340,10 @@ __device__ __forceinline__ int cell_case(const float cv[8], float iso) {
 
 constexpr int kMcThreads = 256;
 
+// Triangles per cell (counts) and per block (block_tot); with block_ne, also the cells of the block
+// that have at least one triangle.
 __global__ void __launch_bounds__(kMcThreads) k_mc_count(CellView v, int64_t n, IsoSet iso, int* counts,
-                                                         int* block_tot) {
+                                                         int* block_tot, int* block_ne) {
   int64_t cell = blockIdx.x * (int64_t)kMcThreads + threadIdx.x;
   int cnt = 0;
   if (cell < n) {
@@ -352,29 +354,33 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_count(CellView v, int64_t n, 
       if ((mask >> q) & 1u) cnt += c_ntri[cell_case(cv, iso.c[q])];
     counts[cell] = cnt;
   }
-  __shared__ int red[kMcThreads / 32];
-  int s = cnt;
+  __shared__ int red[2][kMcThreads / 32];
+  int s = cnt, e = cnt > 0;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    e += __shfl_xor_sync(0xffffffffu, e, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = s;
+    red[1][threadIdx.x >> 5] = e;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    int t = 0;
-    for (int q = 0; q < kMcThreads / 32; ++q) t += red[q];
+    int t = 0, te = 0;
+    for (int q = 0; q < kMcThreads / 32; ++q) {
+      t += red[0][q];
+      te += red[1][q];
+    }
     block_tot[blockIdx.x] = t;
+    if (block_ne) block_ne[blockIdx.x] = te;
   }
 }
 
-__global__ void __launch_bounds__(kMcThreads) k_mc_emit(CellView v, int64_t n, IsoSet iso, const int* counts,
-                                                        const int64_t* block_off, float* tri_vert,
-                                                        int64_t* tri_edge, int32_t* tri_iso, uint32_t* tri_cell,
-                                                        int* nonempty) {
-  int64_t cell = blockIdx.x * (int64_t)kMcThreads + threadIdx.x;
-  int cnt = cell < n ? counts[cell] : 0;
-  // block exclusive scan of cnt
-  __shared__ int wsum[kMcThreads / 32];
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int incl = cnt;
+// Exclusive scan of v over the block (kMcThreads threads); `wsum` holds kMcThreads / 32 ints.
+__device__ __forceinline__ int block_excl_scan_int(int v, int* wsum) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     int t = __shfl_up_sync(0xffffffffu, incl, o);
@@ -393,12 +399,46 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_emit(CellView v, int64_t n, I
     if (lane < kMcThreads / 32) wsum[lane] = si - s;
   }
   __syncthreads();
+  return wsum[warp] + incl - v;
+}
+
+// The cells with at least one triangle, in cell order, with the mask of the isos they have
+// triangles for (dense extraction's list of truly crossing cells).  ne_off: per-block offsets.
+struct NonemptyOut {
+  const int64_t* ne_off = nullptr;
+  uint32_t* code = nullptr;
+  uint32_t* mask = nullptr;
+  int64_t cap = 0;
+};
+
+__global__ void __launch_bounds__(kMcThreads) k_mc_emit(CellView v, int64_t n, IsoSet iso, const int* counts,
+                                                        const int64_t* block_off, float* tri_vert,
+                                                        int64_t* tri_edge, int32_t* tri_iso, uint32_t* tri_cell,
+                                                        NonemptyOut ne) {
+  int64_t cell = blockIdx.x * (int64_t)kMcThreads + threadIdx.x;
+  int cnt = cell < n ? counts[cell] : 0;
+  __shared__ int wsum[kMcThreads / 32];
+  const int ex = block_excl_scan_int(cnt, wsum);          // block exclusive scan of cnt
+  int ex_ne = 0;
+  if (ne.ne_off) {
+    __syncthreads();
+    ex_ne = block_excl_scan_int(cnt > 0 ? 1 : 0, wsum);   // ... and of the non-empty flags
+  }
   if (cell >= n || cnt == 0) return;
-  if (nonempty) atomicAdd(nonempty, 1);
-  int64_t off = block_off[blockIdx.x] + wsum[warp] + incl - cnt;
+  int64_t off = block_off[blockIdx.x] + ex;
   uint32_t ijk[3], mask;
   float cv[8];
   load_cell(v, cell, ijk, mask, cv);
+  if (ne.ne_off) {
+    const int64_t a = ne.ne_off[blockIdx.x] + ex_ne;
+    if (ne.code && a < ne.cap) {
+      uint32_t m = 0;
+      for (int q = 0; q < iso.n; ++q)
+        if (((mask >> q) & 1u) && c_ntri[cell_case(cv, iso.c[q])] > 0) m |= 1u << q;
+      ne.code[a] = ijk[0] | (ijk[1] << 10) | (ijk[2] << 20);
+      ne.mask[a] = m;
+    }
+  }
   uint32_t n1 = (uint32_t)v.R + 1u;
   float inv = 2.0f / (float)v.R;
   for (int q = 0; q < iso.n; ++q) {
@@ -455,22 +495,28 @@ isx_status marching_cubes(isx_inr inr, const uint32_t* codes, const uint32_t* ma
   auto& ws = inr->ws;
   ISX_TRY(ws[WS_TRI_COUNT].ensure((size_t)n * sizeof(int), "tri counts"));
   size_t head = ((nb * sizeof(int) + 15) / 16) * 16;
-  ISX_TRY(ws[WS_TRI_OFFSET].ensure(head + nb * sizeof(int64_t) + 16 * sizeof(int64_t), "tri offsets"));
+  // [block triangle totals][block non-empty totals][triangle offsets][non-empty offsets][2 totals]
+  ISX_TRY(ws[WS_TRI_OFFSET].ensure(2 * head + 2 * nb * sizeof(int64_t) + 16 * sizeof(int64_t), "tri offsets"));
   int* counts = ws[WS_TRI_COUNT].as<int>();
   int* btot = ws[WS_TRI_OFFSET].as<int>();
-  int64_t* boff = reinterpret_cast<int64_t*>(ws[WS_TRI_OFFSET].as<char>() + head);
-  int64_t* d_total = boff + nb;
-  int* d_nonempty = reinterpret_cast<int*>(d_total + 1);
+  int* bne = reinterpret_cast<int*>(ws[WS_TRI_OFFSET].as<char>() + head);
+  int64_t* boff = reinterpret_cast<int64_t*>(ws[WS_TRI_OFFSET].as<char>() + 2 * head);
+  int64_t* neoff = boff + nb;
+  int64_t* d_total = neoff + nb;
+  int64_t* d_ne_total = d_total + 2;
   {
     prof::Scope _ps(K_MC_COUNT, st, 0, 0);
-    k_mc_count<<<(unsigned)nb, kMcThreads, 0, st>>>(v, n, iso, counts, btot);
+    k_mc_count<<<(unsigned)nb, kMcThreads, 0, st>>>(v, n, iso, counts, btot, count_nonempty ? bne : nullptr);
   }
   ISX_LAUNCH_CHECK("k_mc_count");
   ISX_TRY(scan_block_counts(inr, btot, nb, boff, d_total, st));
-  int64_t total = 0;
-  ISX_CUDA(cudaMemcpyAsync(&total, d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  if (count_nonempty) ISX_TRY(scan_block_counts(inr, bne, nb, neoff, d_ne_total, st));
+  int64_t totals[3] = {0, 0, 0};
+  ISX_CUDA(cudaMemcpyAsync(totals, d_total, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   ISX_CUDA(cudaStreamSynchronize(st));
+  const int64_t total = totals[0];
   mesh->n_tris = total;
+  if (count_nonempty) mesh->n_active = totals[2];
   if (total > mesh->tri_cap) {
     set_error("triangle capacity exceeded");
     return ISX_ERR_CAPACITY;
@@ -480,20 +526,21 @@ isx_status marching_cubes(isx_inr inr, const uint32_t* codes, const uint32_t* ma
     set_error("null triangle output buffer");
     return ISX_ERR_ARG;
   }
-  if (count_nonempty) ISX_CUDA(cudaMemsetAsync(d_nonempty, 0, sizeof(int), st));
+  NonemptyOut ne;
+  if (count_nonempty) {
+    ne.ne_off = neoff;
+    if (mesh->d_active_code && mesh->d_active_mask && totals[2] <= mesh->active_cap) {
+      ne.code = mesh->d_active_code;
+      ne.mask = mesh->d_active_mask;
+      ne.cap = mesh->active_cap;
+    }
+  }
   {
     prof::Scope _ps(K_MC_EMIT, st, 0, 0);
     k_mc_emit<<<(unsigned)nb, kMcThreads, 0, st>>>(v, n, iso, counts, boff, mesh->d_tri_vert, mesh->d_tri_edge,
-                                                   mesh->d_tri_iso, mesh->d_tri_cell,
-                                                   count_nonempty ? d_nonempty : nullptr);
+                                                   mesh->d_tri_iso, mesh->d_tri_cell, ne);
   }
   ISX_LAUNCH_CHECK("k_mc_emit");
-  if (count_nonempty) {
-    int ne = 0;
-    ISX_CUDA(cudaMemcpyAsync(&ne, d_nonempty, sizeof(int), cudaMemcpyDeviceToHost, st));
-    ISX_CUDA(cudaStreamSynchronize(st));
-    mesh->n_active = ne;
-  }
   return ISX_OK;
 }
 

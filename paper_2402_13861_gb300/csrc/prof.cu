@@ -25,7 +25,7 @@ const char* names[K_COUNT] = {"input_layer",   "relu",          "center_gemv",  
                               "reduce",        "output",        "cull_count",    "scan_counts",  "scatter_cells",
                               "mark_corners",  "flag_count",    "scatter_flags", "eval_fp32",    "mc_count",
                               "mc_emit",       "iota",          "bound_tc",      "tc_prep",      "tc_output",
-                              "eval_tc",       "bound_cov",     "prop_gate",     "prop_merge",   "prop_forward",
+                              "eval_tc",       "prop_gate",     "prop_merge",   "prop_forward",
                               "prop_grad",     "prop_adam",     "bound_rafixed", "rows_gemm",     "rows_aux",
                               "rows_act",      "rows_new",      "rows_split",    "rows_reduce",  "rows_out"};
 

@@ -29,14 +29,17 @@ __device__ __forceinline__ uint32_t roff(int row, int k) {  // byte offset of (r
   return (uint32_t)((k >> 6) * kRT * 128 + row * 128 + ((((k & 63) >> 3) ^ (row & 7)) << 4));
 }
 
-__device__ __forceinline__ bool rwait(uint64_t* b, uint32_t parity, volatile int* abort, int* status) {
+// Bounded wait for phase `parity` of mbarrier b: gives up when another role of the CTA raised
+// *abort, or after limit_ns, in which case it raises *abort and records ISX_ERR_TIMEOUT in *status.
+__device__ __forceinline__ bool rwait(uint64_t* b, uint32_t parity, volatile int* abort, int* status,
+                                      uint64_t limit_ns = kRowsWaitNs) {
   if (tc::mbar_try(b, parity)) return true;
   const uint64_t t0 = tc::global_ns();
   for (uint32_t it = 1;; ++it) {
     if (tc::mbar_try(b, parity)) return true;
     if ((it & 3) == 0) {
       if (*abort) return false;
-      if (tc::global_ns() - t0 > kRowsWaitNs) {
+      if (tc::global_ns() - t0 > limit_ns) {
         *abort = 1;
         atomicExch(status, (int)ISX_ERR_TIMEOUT);
         return false;
@@ -48,6 +51,9 @@ __device__ __forceinline__ bool rwait(uint64_t* b, uint32_t parity, volatile int
 // G' = (G diag(alpha_cell)) W_j^T for the R rows of `a` (rows_gemm.cu); w = 64, 128 or 256, `wmap`
 // the tensor map of W_j in bf16 with box {64, w}.
 isx_status launch_rows_gemm(isx_inr inr, const RowsGemmArgs& a, const CUtensorMap& wmap, int w, cudaStream_t st);
+// One CTA waits on an mbarrier that nothing completes, with rwait and the given limit, raising
+// ISX_ERR_TIMEOUT in *d_status (rows_gemm.cu).
+isx_status check_bounded_wait(int64_t limit_ns, int* d_status, cudaStream_t st);
 
 }  // namespace rows
 }  // namespace isx

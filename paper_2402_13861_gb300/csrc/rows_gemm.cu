@@ -240,7 +240,28 @@ isx_status launch_rows_gemm_w(isx_inr inr, const RowsGemmArgs& a, const CUtensor
   return ISX_OK;
 }
 
+// One CTA waits, through rwait, on an mbarrier that nothing arrives on: the wait expires after
+// limit_ns and records ISX_ERR_TIMEOUT, as in the GEMM kernels when a hand-off never comes.
+__global__ void k_wait_check(uint64_t limit_ns, int* status) {
+  __shared__ uint64_t bar;
+  __shared__ int ab;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    ab = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) rwait(&bar, 0, &ab, status, limit_ns);
+  __syncthreads();
+}
+
 }  // namespace
+
+isx_status check_bounded_wait(int64_t limit_ns, int* d_status, cudaStream_t st) {
+  k_wait_check<<<1, 32, 0, st>>>((uint64_t)limit_ns, d_status);
+  ISX_LAUNCH_CHECK("k_wait_check");
+  return ISX_OK;
+}
 
 isx_status launch_rows_gemm(isx_inr inr, const RowsGemmArgs& a, const CUtensorMap& wmap, int w, cudaStream_t st) {
   if (w == 256) return launch_rows_gemm_w<256>(inr, a, wmap, st);

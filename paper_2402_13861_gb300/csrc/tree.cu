@@ -147,6 +147,11 @@ __global__ void k_iota(uint32_t* out, int64_t n) {
   if (i < n) out[i] = (uint32_t)i;
 }
 
+__global__ void k_fill_f32(float* out, int64_t n, float v) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = v;
+}
+
 }  // namespace
 
 isx_status scan_block_counts(isx_inr, const int* counts, int64_t nb, int64_t* offsets, int64_t* d_total,
@@ -166,6 +171,16 @@ isx_status iota_u32(uint32_t* out, int64_t n, cudaStream_t st) {
     k_iota<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, n);
   }
   ISX_LAUNCH_CHECK("k_iota");
+  return ISX_OK;
+}
+
+isx_status fill_f32(float* out, int64_t n, float v, cudaStream_t st) {
+  if (n <= 0) return ISX_OK;
+  {
+    prof::Scope _ps(K_IOTA, st, 0, 0);
+    k_fill_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, n, v);
+  }
+  ISX_LAUNCH_CHECK("k_fill_f32");
   return ISX_OK;
 }
 

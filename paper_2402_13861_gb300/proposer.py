@@ -5,10 +5,11 @@ whose Algorithm 1 decides by range analysis alone.  Its labels are produced by t
 - dense extraction (``isx_extract_dense``) gives the finest cells crossed by each iso-surface (the
   cells where marching cubes emits a triangle);
 - a (cell, iso) pair is positive iff the cell's subtree holds such a cell.
-Its features use the bounds of a plain level-by-level pass (``isx_bound_cells`` on the visited
-cells, the same bound the extraction computes).  Training runs the library's forward, backward
+Its features use the bounds of the plain level loop, read from the library's record of it
+(``isx_level_record``: visited cells, inherited masks and bounds per level).  Training runs the library's forward, backward
 and Adam kernels (``isx_proposer_train_step``).  Everything here is data plumbing in PyTorch:
-index arithmetic on cell codes, sampling and bookkeeping.
+index arithmetic on cell codes (ancestor lookups), sampling and bookkeeping; the cull test and
+the subdivision run in the library only.
 """
 from __future__ import annotations
 
@@ -59,82 +60,30 @@ def join_codes(i, j, k):
     return i | (j << 10) | (k << 20)
 
 
-def boxes(codes, level):
+def plain_levels(net, L, isos, mode="clt", k=3.0, prec="bf16"):
+    """The plain level loop of Algorithm 1 as the library runs it (isx_extract_isosurface with its
+    level record): per level a dict with the visited cells' codes (sorted), the iso masks they
+    inherited from their parents, and their bounds (centre, spread)."""
     import torch
-    i, j, k = split_codes(codes)
-    ijk = torch.stack([i, j, k], dim=1).to(torch.float32)
-    size = 2.0 / (1 << level)
-    lo = (-1.0 + size * ijk).contiguous()
-    return lo, (lo + size).contiguous()
-
-
-def children(codes):
-    import torch
-    i, j, k = split_codes(codes)
+    res = net.extract(L, isos, mode=mode, k=k, prec=prec, record=True, active_cap=1 << 22, tri_cap=1 << 24,
+                      record_cap=1 << 24)
     out = []
-    for c in range(8):
-        out.append(join_codes(2 * i + (c & 1), 2 * j + ((c >> 1) & 1), 2 * k + ((c >> 2) & 1)))
-    return torch.stack(out, dim=1).reshape(-1)
-
-
-def cull_bits(centre, spread, isos, mode, k):
-    """Iso bitmask kept by a bound (the cull test of Algorithm 1, closed interval)."""
-    import torch
-    if mode == "sound":
-        lo, hi = centre - spread, centre + spread
-    else:
-        lo, hi = centre - k * spread, centre + k * spread
-    bits = torch.zeros_like(centre, dtype=torch.int64)
-    for q, c in enumerate(isos):
-        bits |= ((lo <= float(c)) & (float(c) <= hi)).to(torch.int64) << q
-    bits[~(lo <= hi)] = (1 << len(isos)) - 1
-    return bits
-
-
-def plain_levels(net, L, isos, mode="clt", k=3.0, prec="bf16", chunk=1 << 21):
-    """The plain level loop, keeping every level: per level a dict with the visited cells' codes
-    (sorted), their parent masks, and (for levels < L) their bound.  Level L is visited but not
-    bounded (its cells' features need only their ancestors' bounds)."""
-    import torch
-    dev = torch.device("cuda")
-    full = (1 << len(isos)) - 1
-    codes = torch.zeros(1, dtype=torch.int64, device=dev)
-    masks = torch.full((1,), full, dtype=torch.int64, device=dev)
-    out = []
-    for level in range(L + 1):
+    for lv in res["levels"]:
+        codes = lv["codes"].to(torch.int64) & 0xFFFFFFFF
         order = torch.argsort(codes)
-        codes, masks = codes[order], masks[order]
-        rec = {"codes": codes, "masks": masks}
-        if level == L:
-            out.append(rec)
-            break
-        c = torch.empty(codes.numel(), dtype=torch.float32, device=dev)
-        s = torch.empty_like(c)
-        for a in range(0, codes.numel(), chunk):
-            lo, hi = boxes(codes[a:a + chunk], level)
-            net.bound_cells(lo, hi, mode=mode, prec=prec, center=c[a:a + chunk], spread=s[a:a + chunk])
-        rec["centre"], rec["spread"] = c, s
-        out.append(rec)
-        keep = masks & cull_bits(c, s, isos, mode, k)
-        alive = keep != 0
-        codes = children(codes[alive])
-        masks = keep[alive].repeat_interleave(8)
+        out.append({"codes": codes[order], "masks": (lv["masks"].to(torch.int64) & 0xFFFFFFFF)[order],
+                    "centre": lv["centre"][order], "spread": lv["spread"][order]})
     return out
 
 
 def crossing_cells(net, L, isos, prec="fp32"):
-    """(codes, masks) of the finest cells where dense marching cubes emits a triangle, per iso."""
+    """(codes, masks) of the finest cells where dense marching cubes emits a triangle, per iso: the
+    list isx_extract_dense writes (codes in cell order, mask bit q = the cell has a triangle of iso q)."""
     import torch
-    res = net.extract(L, isos, prec=prec, dense=True, tri_cap=1 << 22)
-    cell = res["tri_cell"].to(torch.int64) & 0xFFFFFFFF
-    tiso = res["tri_iso"].to(torch.int64)
-    key = torch.unique(cell)
-    masks = torch.zeros_like(key)
-    for q in range(len(isos)):
-        kq = torch.unique(cell[tiso == q])
-        if kq.numel():
-            masks[torch.searchsorted(key, kq)] |= 1 << q
-    return key, masks
+    res = net.extract(L, isos, prec=prec, dense=True, active_cap=1 << 22, tri_cap=1 << 24)
+    codes = res["codes"].to(torch.int64) & 0xFFFFFFFF
+    order = torch.argsort(codes)
+    return codes[order], (res["masks"].to(torch.int64) & 0xFFFFFFFF)[order]
 
 
 def ancestor_table(cross_codes, cross_masks, L, level):

@@ -36,3 +36,41 @@ def excused(code, band_sets, L):
 
 def to_np(t):
     return t.detach().cpu().numpy()
+
+
+def near_maps(levels, near_bits):
+    """Per level of an oracle extraction, {code: bits} of its bounded cells with a non-zero near-iso
+    bit set (tests/_rounding_model.near_iso_bits)."""
+    out = []
+    for lv, b in zip(levels, near_bits):
+        sel = b != 0
+        out.append(dict(zip(pack(lv["ijk"][sel]).tolist(), b[sel].tolist())))
+    return out
+
+
+def ancestor_bits(code, maps, L):
+    """OR of the near-iso bits of the ancestors-or-self of a level-L cell."""
+    ijk = unpack([code])[0]
+    u = 0
+    for l, m in enumerate(maps):
+        if m:
+            u |= m.get(int(pack((ijk >> (L - l))[None])[0]), 0)
+    return u
+
+
+def compare_active_pairs(o_map, g_map, maps, L):
+    """(cell, iso) pairs of two active sets {code: mask}: returns (pairs in either set, differing
+    pairs, pairs the band excuses, differing pairs the band does not excuse)."""
+    n_pairs = n_diff = n_exc = 0
+    bad = []
+    for code in set(o_map) | set(g_map):
+        o, g = o_map.get(code, 0), g_map.get(code, 0)
+        u = o | g
+        n_pairs += bin(u).count("1")
+        anc = ancestor_bits(code, maps, L) if u else 0
+        n_exc += bin(u & anc).count("1")
+        d = o ^ g
+        n_diff += bin(d).count("1")
+        if d & ~anc:
+            bad.append((code, o, g))
+    return n_pairs, n_diff, n_exc, bad

@@ -1,15 +1,17 @@
 """The row-batched tensor-core bound path (bound_rows.cu): bounds of many cells, over several
-chunks of the layer-synchronous loop, agree with the per-cell tensor-core kernel and with the
-float32 path within the bfloat16 band 3 H u_b (|x0| + spread) (u_b = 2^-8, three bf16 roundings per
-coefficient per layer on either path), and the path really runs (its GEMM kernel is counted by the
-launch accounting).  Parity against the float64 oracle is in test_gpu_bf16.py, which takes this
-path for every mode it supports."""
+chunks of the layer-synchronous loop, against the per-cell tensor-core kernel (reached through
+isx_bound_cells_noalloc, which always runs it) and the float32 path.  A sample of the cells is
+checked against the float64 oracle with per-result bands (tests/_rounding_model.py); every cell is
+also held to the blanket band 3 H u_b (|x0| + spread) (u_b = 2^-8) against the other two paths,
+a check for gross errors such as a row of another cell or a wrong chunk boundary.  The path really
+runs: its GEMM kernel is counted by the launch accounting."""
 import numpy as np
 import pytest
 import torch
 
 from synth import boxes, inr
 
+import _rounding_model as rm
 from _helpers import to_np
 
 pytestmark = pytest.mark.gpu
@@ -30,9 +32,24 @@ def _cubes(n, seed, lmin, lmax):
     return torch.tensor(lo, device="cuda"), torch.tensor(hi, device="cuda")
 
 
+def per_cell_kernel(net, lo, hi, mode):
+    """Bounds from the per-cell tensor-core kernel (isx_bound_cells_noalloc runs only that kernel)."""
+    import ctypes as C
+    from paper_2402_13861_gb300 import _lib
+    n = lo.shape[0]
+    c = torch.empty(n, device="cuda")
+    s = torch.empty(n, device="cuda")
+    st = _lib.load().isx_bound_cells_noalloc(net.handle, C.c_void_p(lo.data_ptr()), C.c_void_p(hi.data_ptr()), n,
+                                             _lib.MODES[mode], 0, C.c_void_p(c.data_ptr()), C.c_void_p(s.data_ptr()),
+                                             C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0, _lib.load().isx_last_error()
+    torch.cuda.synchronize()
+    return c, s
+
+
 @pytest.mark.parametrize("dims", [[3, 128, 128, 128, 1], "scientific"])
 @pytest.mark.parametrize("mode", ["clt", "sound", "raua"])
-def test_rows_path_matches_per_cell_kernel(pkg, dims, mode, monkeypatch):
+def test_rows_path_matches_per_cell_kernel(pkg, dims, mode):
     layers = inr.load_inr(dims)[0] if isinstance(dims, str) else inr.random_inr(dims, 5)
     H = len(layers) - 1
     net = pkg.Inr(layers)
@@ -40,10 +57,16 @@ def test_rows_path_matches_per_cell_kernel(pkg, dims, mode, monkeypatch):
     lo, hi = _cubes(n, 12, 3, 9)
     c, s = net.bound_cells(lo, hi, mode=mode, prec="bf16")
     c, s = to_np(c).astype(np.float64), to_np(s).astype(np.float64)
-    monkeypatch.setenv("ISX_BF16_ROWS", "0")
-    c1, s1 = net.bound_cells(lo, hi, mode=mode, prec="bf16")
-    monkeypatch.delenv("ISX_BF16_ROWS")
+    c1, s1 = per_cell_kernel(net, lo, hi, mode)
     c1, s1 = to_np(c1).astype(np.float64), to_np(s1).astype(np.float64)
+    # a sample spread over the chunks against the oracle, with per-result bands
+    idx = np.linspace(0, n - 1, 16 if isinstance(dims, str) else 48).astype(np.int64)
+    b = rm.bound_bands(layers, to_np(lo)[idx], to_np(hi)[idx], mode, batch=16)
+    for name, (cc, ss) in (("rows", (c, s)), ("per-cell", (c1, s1))):
+        dc, ds = np.abs(cc[idx] - b["centre"]), np.abs(ss[idx] - b["spread"])
+        print(f"{name} {mode}: max |d x0| / band {np.max(dc / b['band_c']):.3f}, |d spread| / band "
+              f"{np.max(ds / b['band_s']):.3f}")
+        assert np.all(dc <= b["band_c"]) and np.all(ds <= b["band_s"])
     m = 4000
     c32, s32 = net.bound_cells(lo[:m], hi[:m], mode=mode, prec="fp32")
     c32, s32 = to_np(c32).astype(np.float64), to_np(s32).astype(np.float64)

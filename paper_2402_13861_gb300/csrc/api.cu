@@ -289,6 +289,7 @@ isx_status isx_create_inr(const isx_inr_desc* d, isx_inr* out) {
   inr->Wabs_bf16.assign(L, nullptr);
   inr->Wsq_bf16.assign(L, nullptr);
   inr->Wlo_bf16.assign(L, nullptr);
+  inr->Wperm_bf16.assign(L, nullptr);
   inr->absW_rowsum.assign(L, nullptr);
   inr->hW.resize(L);
   inr->hb.resize(L);
@@ -325,6 +326,17 @@ isx_status isx_create_inr(const isx_inr_desc* d, isx_inr* out) {
       return fail(cuda_fail(e, "W bf16", __FILE__, __LINE__));
     if ((e = cudaMemcpy(inr->W_bf16[l], rb.data(), (size_t)fi * fo * 2, cudaMemcpyHostToDevice)) != cudaSuccess)
       return fail(cuda_fail(e, "W bf16 copy", __FILE__, __LINE__));
+    if (fi == 256 && fo == 256) {
+      // the row GEMM's weight operand: row m holds neuron rows_weight_row(m)
+      std::vector<__nv_bfloat16> pb((size_t)fi * fo);
+      for (int m = 0; m < fo; ++m) {
+        const int o = rows::rows_weight_row(m, fo);
+        for (int i = 0; i < fi; ++i) pb[(size_t)m * fi + i] = rb[(size_t)o * fi + i];
+      }
+      if ((e = cudaMalloc(&inr->Wperm_bf16[l], (size_t)fi * fo * 2)) != cudaSuccess ||
+          (e = cudaMemcpy(inr->Wperm_bf16[l], pb.data(), (size_t)fi * fo * 2, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(cuda_fail(e, "permuted W bf16", __FILE__, __LINE__));
+    }
     if ((e = cudaMalloc(&inr->Wlo_bf16[l], (size_t)fi * fo * 2)) != cudaSuccess ||
         (e = cudaMemcpy(inr->Wlo_bf16[l], lb.data(), (size_t)fi * fo * 2, cudaMemcpyHostToDevice)) != cudaSuccess)
       return fail(cuda_fail(e, "W low bf16", __FILE__, __LINE__));
@@ -362,6 +374,7 @@ isx_status isx_destroy_inr(isx_inr inr) {
   for (auto* p : inr->Wabs_bf16) if (p) cudaFree(p);
   for (auto* p : inr->Wsq_bf16) if (p) cudaFree(p);
   for (auto* p : inr->Wlo_bf16) if (p) cudaFree(p);
+  for (auto* p : inr->Wperm_bf16) if (p) cudaFree(p);
   if (inr->tc_net) cudaFree(inr->tc_net);
   for (auto* p : inr->absW_rowsum) if (p) cudaFree(p);
   for (auto& buf : inr->ws) buf.release();

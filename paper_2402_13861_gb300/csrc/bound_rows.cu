@@ -166,39 +166,92 @@ __global__ void __launch_bounds__(kScanB) k_rows_scan_apply(const int* cnt, int6
 }
 
 // ---- new rows gamma_n W_j[:, n] (row n of W_j^T) after each cell's transformed rows, in
-//      increasing n; the row -> cell map of the whole output.  One warp per cell: the neurons with
-//      gamma != 0 come from ballots, and each row goes out as one warp-wide store (w / 32 columns
-//      per lane). ----
+//      increasing n; the row -> cell map of the whole output; and, per cell and column, the sum of
+//      f(x) over the cell's new rows (x = the stored bf16 value; f = x^2 or |x|).  One warp per cell:
+//      the neurons with gamma != 0 come from ballots, and each row goes out as one warp-wide store
+//      (w / 32 columns per lane, whose sums the lane keeps in registers). ----
 constexpr int kNewWarps = 8;
-__global__ void __launch_bounds__(32 * kNewWarps) k_rows_new(int w, int nc, const float* __restrict__ GA,
+template <int CPL>
+struct NewRowIO;
+template <>
+struct NewRowIO<8> {
+  static __device__ __forceinline__ void ld(const float* p, float* v) {
+    const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  }
+  static __device__ __forceinline__ void st(__nv_bfloat16* p, const uint32_t* h) {
+    *reinterpret_cast<uint4*>(p) = make_uint4(h[0], h[1], h[2], h[3]);
+  }
+};
+template <>
+struct NewRowIO<4> {
+  static __device__ __forceinline__ void ld(const float* p, float* v) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  }
+  static __device__ __forceinline__ void st(__nv_bfloat16* p, const uint32_t* h) {
+    *reinterpret_cast<uint2*>(p) = make_uint2(h[0], h[1]);
+  }
+};
+template <>
+struct NewRowIO<2> {
+  static __device__ __forceinline__ void ld(const float* p, float* v) {
+    const float2 a = *reinterpret_cast<const float2*>(p);
+    v[0] = a.x; v[1] = a.y;
+  }
+  static __device__ __forceinline__ void st(__nv_bfloat16* p, const uint32_t* h) { *reinterpret_cast<uint32_t*>(p) = h[0]; }
+};
+template <int CPL>
+__global__ void __launch_bounds__(32 * kNewWarps) k_rows_new(int nc, int sq, const float* __restrict__ GA,
                                                              const float* __restrict__ Wt, const int* cnt_in,
                                                              const int64_t* off_out, const int* cnt_out,
-                                                             __nv_bfloat16* xout, int* rowcell_out) {
+                                                             __nv_bfloat16* xout, int* rowcell_out, float* pnew) {
+  constexpr int w = 32 * CPL;
+  using IO = NewRowIO<CPL>;
   const int lane = threadIdx.x & 31;
   const int cell = blockIdx.x * kNewWarps + (threadIdx.x >> 5);
   if (cell >= nc) return;
   const int64_t o0 = off_out[cell];
   const int co = cnt_out[cell];
   for (int r = lane; r < co; r += 32) rowcell_out[o0 + r] = cell;
-  const int cpl = w / 32;                          // columns per lane (2, 4 or 8)
-  const int m0 = lane * cpl;
+  const int m0 = lane * CPL;                       // this lane's columns m0 .. m0 + CPL - 1
+  float acc[CPL];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) acc[c] = 0.0f;
   int64_t row = o0 + cnt_in[cell];
+  // one new row: x = bf16(gamma_n W_j[m, n]) for this lane's columns m, stored with one vector store
+  auto emit = [&](float g, const float* v) {
+    uint32_t h[CPL / 2];
+#pragma unroll
+    for (int c = 0; c < CPL; c += 2) {
+      const __nv_bfloat162 x = __floats2bfloat162_rn(g * v[c], g * v[c + 1]);
+      h[c / 2] = *reinterpret_cast<const uint32_t*>(&x);
+      const float2 f = __bfloat1622float2(x);
+      acc[c] += sq ? f.x * f.x : fabsf(f.x);
+      acc[c + 1] += sq ? f.y * f.y : fabsf(f.y);
+    }
+    IO::st(xout + row * w + m0, h);
+    ++row;
+  };
   for (int n0 = 0; n0 < w; n0 += 32) {
     const float gl = GA[(size_t)cell * w + n0 + lane];
     unsigned b = __ballot_sync(0xffffffffu, gl != 0.0f);
-    while (b) {
-      const int l = __ffs(b) - 1;
+    while (b) {                                    // two rows' loads in flight
+      const int l1 = __ffs(b) - 1;
       b &= b - 1;
-      const float g = __shfl_sync(0xffffffffu, gl, l);
-      const float* src = Wt + (size_t)(n0 + l) * w + m0;
-      __nv_bfloat16* dst = xout + row * w + m0;
-      for (int c = 0; c < cpl; c += 2) {
-        const float2 v = *reinterpret_cast<const float2*>(src + c);
-        *reinterpret_cast<__nv_bfloat162*>(dst + c) = __floats2bfloat162_rn(g * v.x, g * v.y);
-      }
-      ++row;
+      const int l2 = b ? __ffs(b) - 1 : -1;
+      if (l2 >= 0) b &= b - 1;
+      const float g1 = __shfl_sync(0xffffffffu, gl, l1);
+      const float g2 = __shfl_sync(0xffffffffu, gl, l2 >= 0 ? l2 : l1);
+      float v1[CPL], v2[CPL];
+      IO::ld(Wt + (size_t)(n0 + l1) * w + m0, v1);
+      if (l2 >= 0) IO::ld(Wt + (size_t)(n0 + l2) * w + m0, v2);
+      emit(g1, v1);
+      if (l2 >= 0) emit(g2, v2);
     }
   }
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) pnew[(size_t)cell * w + m0 + c] = acc[c];
 }
 
 // ---- centre and input rows of z_{j+1}: c' = W a + b, I'_d = (I_d diag(alpha)) W^T, at float32-class
@@ -356,85 +409,110 @@ __global__ void __launch_bounds__(kST, 1) k_rows_split(const __grid_constant__ R
   }
 }
 
-// ---- reductions of z_{j+1} per (cell, neuron): r = sum |x| or sigma = sqrt(sum x^2) over the cell's G
-//      rows and its three input rows (compensated), two neurons per thread; fused with activation
-//      j+1 (alpha, gamma, a, and, when AH is given, the split A operand of the next centre /
-//      input-row GEMM and the next row count cnt_next = cnt + #(gamma != 0)) ----
-__global__ void __launch_bounds__(128, 16) k_rows_reduce_act(int w, int mode, int act, const __nv_bfloat16* X,
-                                                             const int64_t* off,
-                                  const int* cnt, const float* I, const float* C, float* A, float* AL, float* GA,
-                                  int* cnt_next, __nv_bfloat16* AH, __nv_bfloat16* ALO) {
-  __shared__ int wsum[32];
-  const int cell = blockIdx.x;
+// ---- reductions of z_{j+1} per (cell, neuron): r = sum |x| or sigma = sqrt(sum x^2) over the cell's
+//      symbols, from the column sums the row GEMM wrote per (cell, input tile), the new rows' sums of
+//      k_rows_new and the three input rows (compensated), fused with activation j+1 (alpha, gamma, a,
+//      and, when AH is given, the split A operand of the next centre / input-row GEMM (which carries
+//      a; otherwise a itself is written, for the output layer) and the next row count
+//      cnt_next = cnt_out + #(gamma != 0)).  One warp per cell, CPL = w / 32 consecutive
+//      neurons per lane; every load of the cell is issued before the first use. ----
+template <int CPL>
+__device__ __forceinline__ void ldv(const float* p, float* v) {
+#pragma unroll
+  for (int i = 0; i < CPL; i += 2) {
+    const float2 x = *reinterpret_cast<const float2*>(p + i);
+    v[i] = x.x;
+    v[i + 1] = x.y;
+  }
+}
+template <int CPL>
+__device__ __forceinline__ void stv(float* p, const float* v) {
+#pragma unroll
+  for (int i = 0; i < CPL; i += 2) *reinterpret_cast<float2*>(p + i) = make_float2(v[i], v[i + 1]);
+}
+constexpr int kRedWarps = 4;
+template <int CPL>
+__global__ void __launch_bounds__(32 * kRedWarps) k_rows_reduce_act(int nc, int mode, int act, const float* part,
+                                                                    const float* pnew, const int64_t* off_in,
+                                                                    const int* cnt_in, const int* cnt_out,
+                                                                    const float* I, const float* C, float* A, float* AL,
+                                                                    float* GA, int* cnt_next, __nv_bfloat16* AH,
+                                                                    __nv_bfloat16* ALO) {
+  constexpr int w = 32 * CPL;
+  const int lane = threadIdx.x & 31;
+  const int cell = blockIdx.x * kRedWarps + (threadIdx.x >> 5);
+  if (cell >= nc) return;
   const bool sq = mode == ISX_BOUND_CLT;
-  const int64_t o0 = off[cell];
-  const int rows = cnt[cell];
+  const int n0 = lane * CPL;
+  const int rows = cnt_in[cell];
+  const int64_t o0 = off_in[cell];
+  const int rows_out = cnt_out[cell];
+  float iv[3][CPL], cv[CPL], pv[CPL];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) ldv<CPL>(I + ((size_t)cell * 3 + d) * w + n0, iv[d]);
+  ldv<CPL>(C + (size_t)cell * w + n0, cv);
+  ldv<CPL>(pnew + (size_t)cell * w + n0, pv);
+  float s[CPL], e[CPL];
+  auto add = [&](int i, float v) {
+    const float y = v - e[i], tt = s[i] + y;
+    e[i] = (tt - s[i]) - y;
+    s[i] = tt;
+  };
+#pragma unroll
+  for (int i = 0; i < CPL; ++i) {
+    s[i] = e[i] = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) add(i, sq ? iv[d][i] * iv[d][i] : fabsf(iv[d][i]));
+    add(i, pv[i]);
+  }
+  if (rows > 0) {
+    const int64_t t0 = o0 / kRT, t1 = (o0 + rows - 1) / kRT;
+    for (int64_t t = t0; t <= t1; ++t) {
+      float q[CPL];
+      ldv<CPL>(part + (size_t)rows::rows_part_slot(cell, t) * w + n0, q);
+#pragma unroll
+      for (int i = 0; i < CPL; ++i) add(i, q[i]);
+    }
+  }
+  float av[CPL], alv[CPL], gv[CPL];
   int m = 0;
-  for (int n2 = threadIdx.x; n2 < w / 2; n2 += blockDim.x) {
-    const int n = 2 * n2;
-    float s0 = 0.0f, s1 = 0.0f, e0 = 0.0f, e1 = 0.0f;
-    auto add = [&](float& s, float& e, float x) {
-      const float v = sq ? x * x : fabsf(x);
-      const float y = v - e, tt = s + y;
-      e = (tt - s) - y;
-      s = tt;
-    };
-    float2 iv[3];
-    for (int d = 0; d < 3; ++d) {
-      iv[d] = *reinterpret_cast<const float2*>(I + ((size_t)cell * 3 + d) * w + n);
-      add(s0, e0, iv[d].x);
-      add(s1, e1, iv[d].y);
-    }
-    const __nv_bfloat162* src = reinterpret_cast<const __nv_bfloat162*>(X + o0 * w) + n2;
-    int r = 0;
-    for (; r + 8 <= rows; r += 8) {                 // eight rows' loads in flight
-      float2 x[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) x[u] = __bfloat1622float2(src[(size_t)(r + u) * (w / 2)]);
+  for (int i = 0; i < CPL; ++i) {
+    const float r = sq ? sqrtf(s[i]) : s[i];
+    const Lin L = sq ? act_clt(act, cv[i], r) : relu_sound(cv[i], r, 0.0f, false);
+    av[i] = L.center;
+    alv[i] = L.alpha;
+    gv[i] = L.gamma;
+    m += L.gamma != 0.0f;
+  }
+  const size_t o = (size_t)cell * w + n0;
+  if (!AH) stv<CPL>(A + o, av);                   // the centre a is read back only after the last layer
+  stv<CPL>(AL + o, alv);
+  stv<CPL>(GA + o, gv);
+  if (AH) {
+    auto put = [&](size_t idx, const float* v) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        add(s0, e0, x[u].x);
-        add(s1, e1, x[u].y);
-      }
-    }
-    for (; r < rows; ++r) {
-      const float2 x = __bfloat1622float2(src[(size_t)r * (w / 2)]);
-      add(s0, e0, x.x);
-      add(s1, e1, x.y);
-    }
-    const float r0 = sq ? sqrtf(s0) : s0, r1 = sq ? sqrtf(s1) : s1;
-    const size_t o = (size_t)cell * w + n;
-    const float2 c2 = *reinterpret_cast<const float2*>(C + o);
-    const Lin L0 = sq ? act_clt(act, c2.x, r0) : relu_sound(c2.x, r0, 0.0f, false);
-    const Lin L1 = sq ? act_clt(act, c2.y, r1) : relu_sound(c2.y, r1, 0.0f, false);
-    *reinterpret_cast<float2*>(A + o) = make_float2(L0.center, L1.center);
-    *reinterpret_cast<float2*>(AL + o) = make_float2(L0.alpha, L1.alpha);
-    *reinterpret_cast<float2*>(GA + o) = make_float2(L0.gamma, L1.gamma);
-    m += (L0.gamma != 0.0f) + (L1.gamma != 0.0f);
-    if (AH) {
-      auto put = [&](size_t i, float v0, float v1) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+      for (int i = 0; i < CPL; i += 2) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[i], v[i + 1]);
         const float2 hf = __bfloat1622float2(h);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
-        *reinterpret_cast<__nv_bfloat162*>(AH + i) = h;
-        *reinterpret_cast<__nv_bfloat162*>(ALO + i) = l;
-      };
-      const size_t q0 = (size_t)cell * 4 * w + n;
-      put(q0, L0.center, L1.center);
-      for (int d = 0; d < 3; ++d) put(q0 + (size_t)(d + 1) * w, L0.alpha * iv[d].x, L1.alpha * iv[d].y);
+        *reinterpret_cast<__nv_bfloat162*>(AH + idx + i) = h;
+        *reinterpret_cast<__nv_bfloat162*>(ALO + idx + i) = __floats2bfloat162_rn(v[i] - hf.x, v[i + 1] - hf.y);
+      }
+    };
+    const size_t q0 = (size_t)cell * 4 * w + n0;
+    put(q0, av);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float x[CPL];
+#pragma unroll
+      for (int i = 0; i < CPL; ++i) x[i] = alv[i] * iv[d][i];
+      put(q0 + (size_t)(d + 1) * w, x);
     }
   }
   if (!cnt_next) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
-  if (lane == 0) wsum[warp] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int tot = 0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += wsum[i];
-    cnt_next[cell] = rows + tot;
-  }
+  for (int off = 16; off > 0; off >>= 1) m += __shfl_xor_sync(0xffffffffu, m, off);
+  if (lane == 0) cnt_next[cell] = rows_out + m;
 }
 
 // ---- output layer and read-off: x0 = w_out . a + b_out; every symbol's output coefficient is its
@@ -549,11 +627,13 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
   int64_t* d_tot = ws[WS_R_TOT].as<int64_t>();
   int64_t* bsum = d_tot + 8;
   ISX_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
-  std::vector<CUtensorMap> maps(inr->n_layers), lomaps(inr->n_layers);
+  std::vector<CUtensorMap> maps(inr->n_layers), lomaps(inr->n_layers), pmaps(inr->n_layers);
   for (int l = 1; l <= H - 1; ++l) {
     ISX_TRY(tensor_map_bf16(&maps[l], inr->W_bf16[l], w, w, 64, w));
     ISX_TRY(tensor_map_bf16(&lomaps[l], inr->Wlo_bf16[l], w, w, 64, w));
+    ISX_TRY(tensor_map_bf16(&pmaps[l], inr->Wperm_bf16[l] ? inr->Wperm_bf16[l] : inr->W_bf16[l], w, w, 64, w));
   }
+  const int sq = mode == ISX_BOUND_CLT ? 1 : 0;
   // chunk size: about kRowBudget G rows per chunk, from the rows per cell the previous chunk needed
   const int64_t kRowBudget = 1 << 24;
   const int64_t kMaxCells = kMaxChunkCells;
@@ -569,6 +649,7 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
     ISX_TRY(ws[WS_GAMMA].ensure(cw, "rows gamma"));
     ISX_TRY(ws[WS_R_I0].ensure(3 * cw, "rows input rows"));
     ISX_TRY(ws[WS_R_I1].ensure(3 * cw, "rows input rows"));
+    ISX_TRY(ws[WS_R_PNEW].ensure(cw, "new-row column sums"));
     ISX_TRY(ws[WS_R_AH].ensure(4 * cw / 2, "split A, high terms"));
     ISX_TRY(ws[WS_R_ALO].ensure(4 * cw / 2, "split A, low terms"));
     for (Slot s : {WS_R_CNT0, WS_R_CNT1}) ISX_TRY(ws[s].ensure((size_t)nc * sizeof(int), "rows counts"));
@@ -613,8 +694,12 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
       ISX_CUDA(cudaStreamSynchronize(st));
       ISX_TRY(ws[xs[nxt]].ensure((size_t)std::max<int64_t>(Rn, 1) * w * 2, "rows"));
       ISX_TRY(ws[rs[nxt]].ensure((size_t)std::max<int64_t>(Rn, 1) * sizeof(int), "row cells"));
+      const int64_t ntiles = (R + kRT - 1) / kRT;
+      ISX_TRY(ws[WS_R_PART].ensure((size_t)(nc + ntiles) * w * sizeof(float), "row GEMM column sums"));
       __nv_bfloat16* Xin = ws[xs[cur]].as<__nv_bfloat16>();
       __nv_bfloat16* Xout = ws[xs[nxt]].as<__nv_bfloat16>();
+      float* part = ws[WS_R_PART].as<float>();
+      float* pnew = ws[WS_R_PNEW].as<float>();
       if (R > 0) {
         rows::RowsGemmArgs ga{};
         ga.xin = Xin;
@@ -624,14 +709,24 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
         ga.alpha = AL;
         ga.R = R;
         ga.xout = Xout;
+        ga.part = part;
+        ga.sq = sq;
         ga.status = status;
+        // bytes: rows in and out, the column sums of every (cell, tile) segment
         prof::Scope ps(K_ROWS_GEMM, st, 2.0 * (double)R * w * w, 4.0 * (double)R * w);
-        ISX_TRY(rows::launch_rows_gemm(inr, ga, maps[j], w, st));
+        ISX_TRY(rows::launch_rows_gemm(inr, ga, pmaps[j], w, st));
       }
       {
-        prof::Scope ps(K_ROWS_NEW, st, 0, 0);
-        k_rows_new<<<(nc + kNewWarps - 1) / kNewWarps, 32 * kNewWarps, 0, st>>>(w, nc, GA, inr->Wt[j], cnt_in, off_out,
-                                                                              cnt_out, Xout, ws[rs[nxt]].as<int>());
+        // bytes: the new rows (bf16) and the row -> cell map written, gamma read, the column sums
+        prof::Scope ps(K_ROWS_NEW, st, 0, 2.0 * (double)(Rn - R) * w + 4.0 * (double)Rn + 8.0 * (double)nc * w);
+        const unsigned nb = (unsigned)((nc + kNewWarps - 1) / kNewWarps);
+        int* rc = ws[rs[nxt]].as<int>();
+        if (w == 256)
+          k_rows_new<8><<<nb, 32 * kNewWarps, 0, st>>>(nc, sq, GA, inr->Wt[j], cnt_in, off_out, cnt_out, Xout, rc, pnew);
+        else if (w == 128)
+          k_rows_new<4><<<nb, 32 * kNewWarps, 0, st>>>(nc, sq, GA, inr->Wt[j], cnt_in, off_out, cnt_out, Xout, rc, pnew);
+        else
+          k_rows_new<2><<<nb, 32 * kNewWarps, 0, st>>>(nc, sq, GA, inr->Wt[j], cnt_in, off_out, cnt_out, Xout, rc, pnew);
         ISX_LAUNCH_CHECK("k_rows_new");
       }
       {
@@ -657,12 +752,25 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
         }
       }
       {
-        // reductions of z_{j+1} and activation j+1; its row count goes to the buffer of X_j's counts
-        prof::Scope ps(K_ROWS_REDUCE, st, 0, 2.0 * (double)Rn * w);
+        // reductions of z_{j+1} and activation j+1; its row count goes to the buffer of X_j's counts.
+        // bytes per cell: the column sums (one vector per input tile the cell spans, and the new
+        // rows'), the three input rows and the centre read; a, alpha, gamma and the split operand
+        // (4 rows, two bf16 terms) written
         const bool last = j == H - 1;
-        k_rows_reduce_act<<<nc, std::min(w / 2, 128), 0, st>>>(w, (int)mode, inr->act, Xout, off_out, cnt_out, I1, C, A,
-                                                              AL, GA, last ? nullptr : cnt_in, last ? nullptr : AH,
-                                                              ALO);
+        const double vecs = (double)(nc + ntiles) + nc + 3.0 * nc + nc + 3.0 * nc + (last ? 0.0 : 4.0 * nc);
+        prof::Scope ps(K_ROWS_REDUCE, st, 0, 4.0 * vecs * w);
+        const unsigned rb = (unsigned)((nc + kRedWarps - 1) / kRedWarps);
+        int* cn = last ? nullptr : cnt_in;
+        __nv_bfloat16* ah = last ? nullptr : AH;
+        if (w == 256)
+          k_rows_reduce_act<8><<<rb, 32 * kRedWarps, 0, st>>>(nc, (int)mode, inr->act, part, pnew, off_in, cnt_in,
+                                                              cnt_out, I1, C, A, AL, GA, cn, ah, ALO);
+        else if (w == 128)
+          k_rows_reduce_act<4><<<rb, 32 * kRedWarps, 0, st>>>(nc, (int)mode, inr->act, part, pnew, off_in, cnt_in,
+                                                              cnt_out, I1, C, A, AL, GA, cn, ah, ALO);
+        else
+          k_rows_reduce_act<2><<<rb, 32 * kRedWarps, 0, st>>>(nc, (int)mode, inr->act, part, pnew, off_in, cnt_in,
+                                                              cnt_out, I1, C, A, AL, GA, cn, ah, ALO);
         ISX_LAUNCH_CHECK("k_rows_reduce_act");
       }
       std::swap(I0, I1);
@@ -670,7 +778,7 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
       R = Rn;
     }
     {
-      prof::Scope ps(K_ROWS_OUT, st, 2.0 * (double)(R + 3.0 * nc) * w, 0);
+      prof::Scope ps(K_ROWS_OUT, st, 2.0 * (double)(R + 3.0 * nc) * w, 2.0 * (double)R * w + 4.0 * 7.0 * nc * w);
       const int L = inr->n_layers - 1;
       k_rows_output<<<nc, 256, 0, st>>>(w, (int)mode, ws[xs[cur]].as<__nv_bfloat16>(), ws[os[cur]].as<int64_t>(),
                                         ws[cs[cur]].as<int>(), I0, A, AL, GA, inr->W[L], inr->hb[L][0], first,

@@ -55,6 +55,7 @@ enum Slot {
   WS_ANC_C_A, WS_ANC_C_B, WS_ANC_S_A, WS_ANC_S_B, WS_ANC_G_A, WS_ANC_G_B, WS_PROP_KEEP, WS_PROP_NEED,
   WS_PROP_IDX, WS_PROP_CODES,
   WS_R_I0, WS_R_I1, WS_R_A, WS_R_CNT0, WS_R_CNT1, WS_R_OFF0, WS_R_OFF1, WS_R_RC0, WS_R_RC1, WS_R_TOT, WS_R_AH, WS_R_ALO,
+  WS_R_PART, WS_R_PNEW,
   WS_N_SLOTS
 };
 
@@ -74,6 +75,7 @@ struct isx_inr_s {
   std::vector<__nv_bfloat16*> Wabs_bf16; // |W[l]| in bfloat16 (row-major)
   std::vector<__nv_bfloat16*> Wsq_bf16;  // W[l]^2 in bfloat16 (row-major)
   std::vector<__nv_bfloat16*> Wlo_bf16;  // W[l] - float(W_bf16[l]) in bfloat16: low part of a two-term split
+  std::vector<__nv_bfloat16*> Wperm_bf16; // W_bf16[l] with its rows in the row GEMM's order (w = 256 only)
   void* tc_net = nullptr;                // device network descriptor of the tensor-core bound kernel
   std::vector<float*> absW_rowsum;       // sum_k |W[l][n][k]| per output neuron
   std::vector<std::vector<float>> hW, hb;  // host copies

@@ -10,8 +10,9 @@
 //
 //  Uncertainty propagation (Eq. 9-10, Table VII, ReLU row) under N(mu, sigma^2):
 //    alpha = (1 - a) / 2, beta = sigma phi(mu / sigma), gamma^2 = (1 - a^2)/4 (mu^2 + sigma^2) + a mu beta
-//    - beta^2, a = erf(-mu / (sqrt 2 sigma)).  Evaluated as Phi = P(X > 0) and Q = 1 - Phi, both from
-//  erfcf (so 1 - a^2 = 4 Phi Q has no cancellation), in units of sigma^2; gamma^2 is clamped at 0.
+//    - beta^2, a = erf(-mu / (sqrt 2 sigma)).  Evaluated as Phi = P(X > 0) and Q = 1 - Phi: the smaller
+//  of the two from erfcf(|t| / sqrt 2) / 2 and the larger as its complement (so 1 - a^2 = 4 Phi Q has no
+//  cancellation), in units of sigma^2; gamma^2 is clamped at 0.
 //  sigma = 0 (or |mu| > 40 sigma): alpha = 1 if mu > 0, 1/2 if mu = 0, else 0; beta = gamma = 0.
 #pragma once
 
@@ -30,8 +31,10 @@ __device__ __forceinline__ Lin relu_clt(float mu, float sigma) {
   Lin r;
   if (sigma > 0.0f && fabsf(mu) < 40.0f * sigma) {
     float t = mu / sigma;
-    float Phi = 0.5f * erfcf(-t * 0.70710678118654752f);
-    float Q = 0.5f * erfcf(t * 0.70710678118654752f);
+    // the smaller of Phi and Q from erfc of |t| (no cancellation), the other as its complement
+    const float tail = 0.5f * erfcf(fabsf(t) * 0.70710678118654752f);
+    const float Phi = t >= 0.0f ? 1.0f - tail : tail;
+    const float Q = t >= 0.0f ? tail : 1.0f - tail;
     float phi = expf(-0.5f * t * t) * 0.39894228040143268f;
     r.alpha = Phi;
     r.beta = sigma * phi;

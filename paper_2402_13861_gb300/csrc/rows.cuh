@@ -22,6 +22,9 @@ struct RowsGemmArgs {
   const float* alpha;                           // [nc][W]
   int64_t R;
   __nv_bfloat16* xout;                          // [R'][W] rows of z_{j+1}
+  float* part;                                  // [nc + ceil(R / 128)][W]: slot cell + tile holds, per
+                                                // neuron, sum f(x) over the cell's rows of that input tile
+  int sq;                                       // f(x) = x^2 (1, Eq. 7) or |x| (0, Eq. 2)
   int* status;
 };
 
@@ -48,9 +51,20 @@ __device__ __forceinline__ bool rwait(uint64_t* b, uint32_t parity, volatile int
   }
 }
 
-// G' = (G diag(alpha_cell)) W_j^T for the R rows of `a` (rows_gemm.cu); w = 64, 128 or 256, `wmap`
-// the tensor map of W_j in bf16 with box {64, w}.
+// G' = (G diag(alpha_cell)) W_j^T for the R rows of `a`, and the per-(cell, tile) column sums of
+// f(G') (rows_gemm.cu); w = 64, 128 or 256, `wmap` the tensor map of W_j in bf16 with box {64, w},
+// its rows in the order of rows_weight_row (the neuron held by MMA row m).
 isx_status launch_rows_gemm(isx_inr inr, const RowsGemmArgs& a, const CUtensorMap& wmap, int w, cudaStream_t st);
+// Row of W_j the row GEMM keeps at position m of its weight operand.  For w = 256 the even neurons
+// come first and the odd ones after them, so that the epilogue thread of MMA row m of the two
+// 128-row halves holds the neuron pair (2m, 2m + 1); otherwise the identity.
+__host__ __device__ __forceinline__ int rows_weight_row(int m, int w) {
+  return w == 256 ? (m < 128 ? 2 * m : 2 * (m - 128) + 1) : m;
+}
+// Slot of the column partials of (cell, input tile) in RowsGemmArgs::part: cell + tile.  Rows of a
+// cell are contiguous, so cell c < c' implies tile <= tile' and the slots of all (cell, tile) pairs
+// that share rows are distinct.
+__host__ __device__ __forceinline__ int64_t rows_part_slot(int64_t cell, int64_t tile) { return cell + tile; }
 // One CTA waits on an mbarrier that nothing completes, with rwait and the given limit, raising
 // ISX_ERR_TIMEOUT in *d_status (rows_gemm.cu).
 isx_status check_bounded_wait(int64_t limit_ns, int* d_status, cudaStream_t st);

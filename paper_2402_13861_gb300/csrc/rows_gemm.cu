@@ -14,37 +14,53 @@ using namespace tc;
 template <int W>
 struct RowsSmem {
   static constexpr int KC = W / 64;
-  static constexpr int NS = (W == 256) ? 5 : 4;            // A ring: one 64-wide K chunk of a tile each
-  static constexpr size_t kWB = (size_t)W * W * 2;         // W_j, KC chunks of [W rows][128 B]
-  static constexpr size_t kAC = (size_t)kRT * 128;         // one A chunk: [128 rows][128 B]
-  static constexpr size_t bytes() { return 1024 + kWB + NS * kAC + (3 * NS + 5) * 8 + 16; }
+  static constexpr int MW = W < 128 ? 128 : W;             // rows of the weight operand (W = 64: zero-padded)
+  static constexpr int NH = MW / 128;                      // 128-row MMA halves of the weight operand
+  static constexpr int NS = (W == 256) ? 5 : 4;            // row ring: one 64-wide K chunk of a tile each
+  static constexpr size_t kWB = (size_t)MW * W * 2;        // W_j, KC chunks of [MW rows][128 B]
+  static constexpr size_t kAC = (size_t)kRT * 128;         // one row chunk: [128 rows][128 B]
+  static constexpr size_t kMeta = 2 * kRT * (8 + 4);       // two tiles' destination rows and cells
+  static constexpr size_t bytes() { return 1024 + kWB + NS * kAC + kMeta + (3 * NS + 5) * 8 + 16; }
 };
 
-// G' = (G diag(alpha_cell)) W^T for all rows: persistent, warp-specialised CTAs over 128-row tiles.
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// G' = (G diag(alpha_cell)) W^T for all rows, computed transposed: D = W_j (G diag(alpha))^T, so that
+// TMEM lane m holds neuron rows_weight_row(m) and column r the tile's row r.  Persistent,
+// warp-specialised CTAs over 128-row tiles:
 //  - warp 5 streams the rows of G by TMA, one 64-wide K chunk of a tile per stage of an NS-stage
-//    ring, already in the 128-byte-swizzled K-major layout of the MMA's A operand;
+//    ring, in the 128-byte-swizzled K-major layout of the MMA's B operand;
 //  - warps 0-3 scale each staged chunk in place: thread t multiplies row t by its cell's alpha
 //    (rows past R stay the TMA's zero fill);
-//  - warp 4 loads W_j (bf16, [out][in] = N x K, K-major) once by TMA, owns TMEM and issues the MMAs;
-//  - warps 6-9 drain the two TMEM accumulators to bf16 rows of G' (lane group = warp mod 4).
+//  - warp 4 loads W_j (bf16, [MW][W], K-major) once by TMA, owns TMEM and issues the MMAs (M = 128
+//    per weight half, N = 128 rows, K = 16 per instruction);
+//  - warps 6-9 drain the two TMEM accumulators.  Thread m owns the neurons of weight row m of each
+//    half and walks the tile's rows in order: it stores each row's bf16 value (a bf16 pair for
+//    W = 256) and adds f(value) to a running sum that it writes to part[cell + tile] whenever the
+//    row's cell changes (f of the float32 accumulator value: within 2^-8 of f of the stored value).
+//    Every thread sees the same rows, so the segment boundaries are uniform; a segment's rows are
+//    consecutive in the output too, so its destination advances by one row per row.
+//    The destination row and cell of every row of the next tile are loaded while this tile drains
+//    and handed over through shared memory.
 // The scalers load the alpha of the next chunk (of this tile, or of the next tile) into registers
-// before they wait for the current one: alpha rows are not L2-resident at chunk scale, so their
-// latency would otherwise sit on every chunk.
-// Loads of tile k + 1 and the epilogue of tile k - 1 overlap the MMAs of tile k.  Every wait is
-// bounded (2 s): on timeout the kernel records ISX_ERR_TIMEOUT, lets the work in flight finish,
-// frees TMEM and returns.
+// before they wait for the current one.  Loads of tile k + 1 and the epilogue of tile k - 1 overlap
+// the MMAs of tile k.  Every wait is bounded (2 s): on timeout the kernel records ISX_ERR_TIMEOUT,
+// lets the work in flight finish, frees TMEM and returns.
 constexpr int kGT = 320;
-template <int W>
+template <int W, bool SQ>
 __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ RowsGemmArgs args,
                                                        const __grid_constant__ CUtensorMap wmap,
                                                        const __grid_constant__ CUtensorMap xmap) {
   using S = RowsSmem<W>;
-  constexpr int KC = S::KC, NS = S::NS;
+  constexpr int KC = S::KC, NS = S::NS, MW = S::MW, NH = S::NH;
+  constexpr uint32_t kCols = 2 * NH * 128;                 // two accumulators of NH x 128 columns
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* Wsm = base;
   uint8_t* Asm = Wsm + S::kWB;
-  uint64_t* araw = reinterpret_cast<uint64_t*>(Asm + NS * S::kAC);
+  long long* mdst = reinterpret_cast<long long*>(Asm + NS * S::kAC);   // [2][128]
+  int* mcell = reinterpret_cast<int*>(mdst + 2 * kRT);                  // [2][128]
+  uint64_t* araw = reinterpret_cast<uint64_t*>(mcell + 2 * kRT);
   uint64_t* afull = araw + NS;
   uint64_t* aempty = afull + NS;
   uint64_t* tfull = aempty + NS;
@@ -55,6 +71,13 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int64_t ntiles = (args.R + kRT - 1) / kRT;
 
+  if (W < 128) {
+    // zero rows W .. 127 of every weight chunk (the MMA reads 128 weight rows)
+    for (int c = 0; c < KC; ++c)
+      for (int i = t; i < (MW - W) * 128 / 16; i += blockDim.x)
+        reinterpret_cast<uint4*>(Wsm + (size_t)c * MW * 128 + (size_t)W * 128)[i] = make_uint4(0, 0, 0, 0);
+    fence_async_shared();
+  }
   if (t == 0) {
     for (int i = 0; i < NS; ++i) {
       mbar_init(&araw[i], 1);
@@ -71,7 +94,7 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
   }
   if (warp == 4) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
-                 "n"(2 * W)
+                 "n"(kCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -86,7 +109,6 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
     bool ok = true;
     int64_t r_next = (int64_t)blockIdx.x * kRT + t;
     int cell_next = (r_next < args.R) ? args.rowcell[r_next] : 0;
-    // alpha of chunk 0 of the first tile
     float4 av[16];
     {
       const float4* al0 = reinterpret_cast<const float4*>(args.alpha + (size_t)cell_next * W);
@@ -97,12 +119,20 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
       const int64_t r = tile * kRT + t;
       const bool valid = r < args.R;
       const int cell = cell_next;
-      // the next tile's row -> cell lookup is in flight while this tile is scaled
       r_next = (tile + gridDim.x) * kRT + t;
       cell_next = (tile + gridDim.x < ntiles && r_next < args.R) ? args.rowcell[r_next] : cell;
+      {
+        // ask L2 for the alpha rows of the cells of this warp's 32 rows of the next tile (a run of
+        // consecutive cells, so one contiguous range), a tile ahead of their use
+        const int cf = __shfl_sync(0xffffffffu, cell_next, 0), cl = __shfl_sync(0xffffffffu, cell_next, 31);
+        if (lane == 0 && tile + gridDim.x < ntiles && cl >= cf) {
+          const uint32_t bytes = (uint32_t)min((cl - cf + 1) * W * 4, 32 * 1024);
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(args.alpha + (size_t)cf * W), "r"(bytes)
+                       : "memory");
+        }
+      }
       for (int c = 0; c < KC; ++c, ++it) {
         const int sidx = it % NS;
-        // alpha of the next chunk: this tile's chunk c + 1, else the next tile's chunk 0
         const float4* aln = (c + 1 < KC) ? reinterpret_cast<const float4*>(args.alpha + (size_t)cell * W) + 16 * (c + 1)
                                          : reinterpret_cast<const float4*>(args.alpha + (size_t)cell_next * W);
         float4 an[16];
@@ -148,64 +178,120 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
       }
     }
   } else if (warp == 4) {
-    // ---- W_j once, then the MMAs ----
+    // ---- W_j once, then the MMAs: D[half h] += W_j[h rows] x chunk^T ----
     if (lane == 0) {
-      mbar_expect_tx(wfull, (uint32_t)S::kWB);
-      for (int c = 0; c < KC; ++c) tma_load_2d(Wsm + (size_t)c * W * 128, &wmap, wfull, c * 64, 0);
-      const uint32_t id = idesc(W);
+      mbar_expect_tx(wfull, (uint32_t)((size_t)W * W * 2));
+      for (int c = 0; c < KC; ++c) tma_load_2d(Wsm + (size_t)c * MW * 128, &wmap, wfull, c * 64, 0);
+      const uint32_t id = idesc(kRT);
       uint32_t it = 0, tt = 0;
       bool ok = rwait(wfull, 0, abort, args.status);
       for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tt) {
         const uint32_t b = tt & 1;
         if (!rwait(&tempty[b], ((tt >> 1) & 1) ^ 1, abort, args.status)) break;
         tc_fence_after();
-        const uint32_t dt = tmem + b * W;
+        const uint32_t dt = tmem + b * (NH * 128);
         for (int c = 0; c < KC; ++c, ++it) {
           const int sidx = it % NS;
           if (!rwait(&afull[sidx], (it / NS) & 1, abort, args.status)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t a0 = su32(Asm + (size_t)sidx * S::kAC), w0 = su32(Wsm + (size_t)c * W * 128);
+          const uint32_t x0 = su32(Asm + (size_t)sidx * S::kAC), w0 = su32(Wsm + (size_t)c * MW * 128);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
-            mma_bf16(dt, sdesc(a0 + kk * 32), sdesc(w0 + kk * 32), id, (c > 0 || kk > 0) ? 1u : 0u);
+#pragma unroll
+            for (int h = 0; h < NH; ++h)
+              mma_bf16(dt + h * 128, sdesc(w0 + h * 128 * 128 + kk * 32), sdesc(x0 + kk * 32), id,
+                       (c > 0 || kk > 0) ? 1u : 0u);
           mma_commit(&aempty[sidx]);
         }
         if (ok) mma_commit(&tfull[b]);
       }
     }
   } else {
-    // ---- epilogue: TMEM -> bf16 rows of G' ----
-    const int row = 32 * (warp & 3) + lane;
+    // ---- epilogue: TMEM -> bf16 rows of G' and the per-(cell, tile) column sums of f(G') ----
+    const int m = 32 * (warp & 3) + lane;                  // weight row (TMEM lane) of this thread
+    const bool own = m < W;                                 // W = 64: rows 64 .. 127 are padding
+    const int n0 = (W == 256) ? 2 * m : m;                  // first neuron of this thread
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+    // metadata of this thread's row of the first tile, and the cell of its row of the second
+    int64_t tile = blockIdx.x;
+    int c_cur = -1, c_nxt = -1;
+    long long d_cur = 0;
+    {
+      const int64_t r = tile * kRT + m;
+      if (tile < ntiles && r < args.R) {
+        c_cur = args.rowcell[r];
+        d_cur = args.off_out[c_cur] + (r - args.off_in[c_cur]);
+      }
+      const int64_t r2 = (tile + gridDim.x) * kRT + m;
+      if (tile + gridDim.x < ntiles && r2 < args.R) c_nxt = args.rowcell[r2];
+    }
     uint32_t tt = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tt) {
+    for (; tile < ntiles; tile += gridDim.x, ++tt) {
       const uint32_t b = tt & 1;
-      // the destination row (a dependent chain of three loads) is resolved while the MMAs run
-      const int64_t r = tile * kRT + row;
-      const bool valid = r < args.R;
-      __nv_bfloat16* dst = nullptr;
-      if (valid) {
-        const int cell = args.rowcell[r];
-        dst = args.xout + (args.off_out[cell] + (r - args.off_in[cell])) * W;
+      int* scell = mcell + b * kRT;
+      long long* sdst = mdst + b * kRT;
+      scell[m] = c_cur;
+      sdst[m] = d_cur;
+      epi_bar();
+      // the next tile's destination rows (its cells came one tile earlier) and the cells of the tile
+      // after it: in flight while this tile drains
+      {
+        const int64_t nt = tile + gridDim.x;
+        const int64_t r1 = nt * kRT + m;
+        c_cur = c_nxt;
+        if (nt < ntiles && r1 < args.R && c_cur >= 0) d_cur = args.off_out[c_cur] + (r1 - args.off_in[c_cur]);
+        const int64_t r2 = (nt + gridDim.x) * kRT + m;
+        c_nxt = (nt + gridDim.x < ntiles && r2 < args.R) ? args.rowcell[r2] : -1;
       }
       const bool got = rwait(&tfull[b], (tt >> 1) & 1, abort, args.status);
       if (!__all_sync(0xffffffffu, got)) break;
       tc_fence_after();
-      const uint32_t trow = tmem + b * W + ((uint32_t)(32 * (warp & 3)) << 16);
+      const int64_t left = args.R - tile * kRT;
+      const int rows = left < kRT ? (int)left : kRT;
+      const uint32_t tb = tmem + b * (NH * 128) + lane_off;
+      // running sums of the current (cell, tile) segment and the destination of its next row
+      float s0 = 0.0f, s1 = 0.0f;
+      int seg = scell[0];
+      __nv_bfloat16* dp = args.xout + (size_t)sdst[0] * W + n0;
 #pragma unroll 1
-      for (int c0 = 0; c0 < W; c0 += 32) {
-        float v[32];
-        tmem_ld32(trow + c0, v);
-        if (valid) {
-          uint32_t pk[16];
+      for (int c0 = 0; c0 < rows; c0 += 32) {
+        // rows c0 .. c0 + 31: which of them start a segment (a ballot over the warp's lanes), and
+        // each lane's row's cell and destination, handed to the row loop by shuffles
+        const int rl = c0 + lane;
+        const int cl = rl < rows ? scell[rl] : -1;
+        const long long dl = rl < rows ? sdst[rl] : 0;
+        const uint32_t starts = __ballot_sync(0xffffffffu, rl < rows && rl > 0 && cl != scell[rl - 1]);
+        float v0[32], v1[32];
+        tmem_ld32(tb + c0, v0);
+        if (NH == 2) tmem_ld32(tb + 128 + c0, v1);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-            pk[i] = *reinterpret_cast<const uint32_t*>(&h);
+        for (int i = 0; i < 32; ++i) {
+          if (c0 + i >= rows) break;
+          if ((starts >> i) & 1u) {                        // uniform: every thread sees the same rows
+            if (own) {
+              float* pp = args.part + (size_t)rows_part_slot(seg, tile) * W + n0;
+              if (NH == 2) *reinterpret_cast<float2*>(pp) = make_float2(s0, s1);
+              else *pp = s0;
+            }
+            s0 = s1 = 0.0f;
+            seg = __shfl_sync(0xffffffffu, cl, i);
+            dp = args.xout + (size_t)__shfl_sync(0xffffffffu, dl, i) * W + n0;
           }
-          uint4* d4 = reinterpret_cast<uint4*>(dst + c0);
-#pragma unroll
-          for (int i = 0; i < 4; ++i) d4[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+          if (NH == 2) {
+            *reinterpret_cast<__nv_bfloat162*>(dp) = __floats2bfloat162_rn(v0[i], v1[i]);
+            s0 = SQ ? fmaf(v0[i], v0[i], s0) : s0 + fabsf(v0[i]);
+            s1 = SQ ? fmaf(v1[i], v1[i], s1) : s1 + fabsf(v1[i]);
+          } else if (own) {
+            *dp = __float2bfloat16_rn(v0[i]);
+            s0 = SQ ? fmaf(v0[i], v0[i], s0) : s0 + fabsf(v0[i]);
+          }
+          dp += W;
         }
+      }
+      if (own) {
+        float* pp = args.part + (size_t)rows_part_slot(seg, tile) * W + n0;
+        if (NH == 2) *reinterpret_cast<float2*>(pp) = make_float2(s0, s1);
+        else *pp = s0;
       }
       tc_fence_before();
       __syncwarp();
@@ -218,24 +304,24 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
     for (int i = 0; i < 1000; ++i) __nanosleep(1000);
   if (warp == 4) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(2 * W) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kCols) : "memory");
   }
 }
 
-template <int W>
+template <int W, bool SQ>
 isx_status launch_rows_gemm_w(isx_inr inr, const RowsGemmArgs& a, const CUtensorMap& map, cudaStream_t st) {
   CUtensorMap xmap;
   ISX_TRY(tensor_map_bf16(&xmap, a.xin, W, (uint64_t)a.R, 64, kRT));
   const size_t smem = RowsSmem<W>::bytes();
-  ISX_CUDA(cudaFuncSetAttribute(k_rows_gemm<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ISX_CUDA(cudaFuncSetAttribute(k_rows_gemm<W, SQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int sms = 148;
   ISX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, inr->device));
   int per_sm = 1;
-  ISX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_gemm<W>, kGT, smem));
-  per_sm = std::max(1, std::min(per_sm, 512 / (2 * W)));   // TMEM: 2 W columns per CTA
+  ISX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_gemm<W, SQ>, kGT, smem));
+  per_sm = std::max(1, std::min(per_sm, 512 / (2 * RowsSmem<W>::NH * 128)));   // TMEM columns per CTA
   const int64_t ntiles = (a.R + kRT - 1) / kRT;
   const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
-  k_rows_gemm<W><<<grid, kGT, smem, st>>>(a, map, xmap);
+  k_rows_gemm<W, SQ><<<grid, kGT, smem, st>>>(a, map, xmap);
   ISX_LAUNCH_CHECK("k_rows_gemm");
   return ISX_OK;
 }
@@ -264,9 +350,14 @@ isx_status check_bounded_wait(int64_t limit_ns, int* d_status, cudaStream_t st) 
 }
 
 isx_status launch_rows_gemm(isx_inr inr, const RowsGemmArgs& a, const CUtensorMap& wmap, int w, cudaStream_t st) {
-  if (w == 256) return launch_rows_gemm_w<256>(inr, a, wmap, st);
-  if (w == 128) return launch_rows_gemm_w<128>(inr, a, wmap, st);
-  return launch_rows_gemm_w<64>(inr, a, wmap, st);
+  if (a.sq) {
+    if (w == 256) return launch_rows_gemm_w<256, true>(inr, a, wmap, st);
+    if (w == 128) return launch_rows_gemm_w<128, true>(inr, a, wmap, st);
+    return launch_rows_gemm_w<64, true>(inr, a, wmap, st);
+  }
+  if (w == 256) return launch_rows_gemm_w<256, false>(inr, a, wmap, st);
+  if (w == 128) return launch_rows_gemm_w<128, false>(inr, a, wmap, st);
+  return launch_rows_gemm_w<64, false>(inr, a, wmap, st);
 }
 
 }  // namespace rows

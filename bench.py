@@ -142,8 +142,8 @@ def extraction_forms(pkg, net, L, isos, plain, plain_ms, mode, k, prec, slow=Fal
     st = torch.cuda.current_stream()
     bufs = {}
 
-    def timed_level(level, **kw):
-        for rep in range(2):
+    def timed_level(level, reps=2, **kw):
+        for rep in range(reps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(st)
             r = net.extract(level, isos, buffers=bufs, active_cap=1 << 27, tri_cap=1 << 25, **kw)
@@ -151,8 +151,8 @@ def extraction_forms(pkg, net, L, isos, plain, plain_ms, mode, k, prec, slow=Fal
             torch.cuda.synchronize()
         return r, a.elapsed_time(b)
 
-    def timed(**kw):
-        return timed_level(L, **kw)
+    def timed(reps=2, **kw):
+        return timed_level(L, reps=reps, **kw)
 
     dense32, ms_d32 = timed(prec="fp32", dense=True)
     # the dense extraction's crossing cells (cells with a triangle, per iso), as the library lists them
@@ -163,10 +163,37 @@ def extraction_forms(pkg, net, L, isos, plain, plain_ms, mode, k, prec, slow=Fal
     mp, tot = missed(plain["codes"], plain["masks"], cross)
     out["plain"] = {"ms": plain_ms, "cells_bounded": int(sum(plain["cells_bounded"])), "missed_pairs": mp,
                     "missed_rate": mp / max(tot, 1)}
-    r, ms = timed(mode=mode, k=k, prec=prec, bound_stop_level=6, eval_prec="bf16")
+    # sound affine arithmetic (row-batched BF16): without inflation, and with the rounding-error
+    # inflation, whose FNR is 0 by construction, so it must miss no crossing pair (timed once: its
+    # error symbols make it the slowest form)
+    r, ms = timed(mode="sound", prec=prec, eval_prec="bf16")
     m, _ = missed(r["codes"], r["masks"], cross)
-    out["bound_to_level6_tc_eval"] = {"ms": ms, "cells_bounded": int(sum(r["cells_bounded"])),
-                                      "n_active": r["n_active"], "missed_pairs": m, "missed_rate": m / max(tot, 1)}
+    out["sound_bf16"] = {"ms": ms, "cells_bounded": int(sum(r["cells_bounded"])),
+                         "cells_per_s": sum(r["cells_bounded"]) / (ms / 1e3), "n_active": r["n_active"],
+                         "missed_pairs": m, "missed_rate": m / max(tot, 1)}
+    r, ms = timed(reps=1, mode="sound", prec=prec, inflate=True, eval_prec="bf16")
+    m, _ = missed(r["codes"], r["masks"], cross)
+    out["sound_bf16_inflated"] = {"ms": ms, "cells_bounded": int(sum(r["cells_bounded"])),
+                                  "cells_per_s": sum(r["cells_bounded"]) / (ms / 1e3), "n_active": r["n_active"],
+                                  "missed_pairs": m, "missed_rate": m / max(tot, 1), "timed_runs": 1}
+    # the confidence multiplier k of the Gaussian read-off (Algorithm 1's t): miss rate against work
+    for kk in (2.0, 4.0):
+        r, ms = timed(mode=mode, k=kk, prec=prec, eval_prec="bf16")
+        m, _ = missed(r["codes"], r["masks"], cross)
+        out[f"{mode}_k{int(kk)}"] = {"ms": ms, "cells_bounded": int(sum(r["cells_bounded"])),
+                                     "n_active": r["n_active"], "missed_pairs": m, "missed_rate": m / max(tot, 1)}
+    # bound_stop_level: bound down to level s, keep every descendant of the survivors, evaluate densely
+    # inside them (tensor-core corner values); s = max_level is the plain form
+    out["stop_level"] = {}
+    for stop in range(4, L):
+        r, ms = timed(mode=mode, k=k, prec=prec, bound_stop_level=stop, eval_prec="bf16")
+        m, _ = missed(r["codes"], r["masks"], cross)
+        out["stop_level"][str(stop)] = {"ms": ms, "cells_bounded": int(sum(r["cells_bounded"])),
+                                        "n_active": r["n_active"], "n_points": r["n_points"], "missed_pairs": m,
+                                        "missed_rate": m / max(tot, 1)}
+    out["stop_level"][str(L)] = {"ms": plain_ms, "cells_bounded": int(sum(plain["cells_bounded"])),
+                                 "missed_rate": out["plain"]["missed_rate"]}
+    out["bound_to_level6_tc_eval"] = dict(out["stop_level"]["6"])
     prop, meta = gp.load(os.path.join(ROOT, "synth", "data", "proposer.npz"))
     r, ms = timed(mode=mode, k=k, prec=prec, eval_prec="bf16", proposer=prop, proposer_level=meta["proposer_level"],
                   tau_lo=meta["tau_lo"], tau_hi=meta["tau_hi"])
@@ -274,11 +301,12 @@ def activation_forms(pkg, k, names=("siren", "sdf_elu")):
     return out
 
 
-def cpu_baseline(layers, mode, k, budget_s=12.0):
-    """Float64 oracle bounding random cells of levels 6-9 of the same workload for ~budget_s."""
-    import numpy as np
+def _oracle_rate(mode, budget_s):
+    """(cells, seconds) of the float64 oracle bounding random cells of levels 6-9 of the scientific
+    network for about budget_s (numpy's matrix products are the only library calls)."""
     from oracle import affine
-    from synth import boxes
+    from synth import boxes, inr
+    layers = inr.load_inr(WORKLOAD)[0]
     ijk, level, lo, hi = boxes.random_cubes(4096, 77, 6, 9)
     done = 0
     t0 = time.perf_counter()
@@ -286,10 +314,55 @@ def cpu_baseline(layers, mode, k, budget_s=12.0):
     while time.perf_counter() - t0 < budget_s and done < 4096:
         affine.bound(layers, lo[done:done + bs], hi[done:done + bs], mode, batch=bs)
         done += bs
-    dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OPENBLAS_NUM_THREADS", os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)))
+    return done, time.perf_counter() - t0
+
+
+def cpu_baseline(layers, mode, k, budget_s=8.0, single_thread=True):
+    """Float64 oracle bounding random cells of levels 6-9 of the same workload: on all host cores (numpy's
+    BLAS threads left at their default, the main value) and, in a child process with one BLAS thread,
+    single-threaded."""
+    done, dt = _oracle_rate(mode, budget_s)
+    cores = os.cpu_count() or 1
+    single = None
+    try:
+        if not single_thread:
+            raise RuntimeError("not measured in this run")
+        env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        code = (f"import sys, json; sys.path.insert(0, {ROOT!r}); import bench; "
+                f"d, t = bench._oracle_rate({mode!r}, {budget_s}); print(json.dumps([d, t]))")
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        d1, t1 = json.loads(out.stdout.strip().splitlines()[-1])
+        single = {"value": d1 / t1, "unit": "cells/s", "cores": 1,
+                  "sample": f"{d1} random cells of levels 6-9 in {t1:.1f} s, one BLAS thread"}
+    except Exception as ex:                       # the single-thread figure never costs the bench line
+        single = {"error": repr(ex)}
     return {"value": done / dt, "unit": "cells/s", "cores": cores, "kind": "oracle",
-            "sample": f"{done} random cells of levels 6-9 bounded by the float64 oracle ({mode}) in {dt:.1f} s"}
+            "blas_threads": os.environ.get("OPENBLAS_NUM_THREADS", "default (all cores)"),
+            "sample": f"{done} random cells of levels 6-9 bounded by the float64 oracle ({mode}) in {dt:.1f} s",
+            "single_thread": single}
+
+
+def precision_sample(net, mode, n=200000):
+    """AA-bounded cells/s of the float32 path against the BF16 row path on the same cells (random cubes
+    of levels 6-9, the levels that hold 99 % of the bounded cells at 512^3): the float32 path keeps
+    every symbol row, so a full 512^3 extraction in float32 would take minutes."""
+    import torch
+    from synth import boxes
+    _, _, lo, hi = boxes.random_cubes(n, 91, 6, 9)
+    lo, hi = torch.tensor(lo, device="cuda"), torch.tensor(hi, device="cuda")
+    st = torch.cuda.current_stream()
+    out = {"cells": n, "sample": f"{n} random cubes of levels 6-9"}
+    for prec in ("bf16", "fp32"):
+        for rep in range(2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            net.bound_cells(lo, hi, mode=mode, prec=prec)
+            b.record(st)
+            torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        out[prec] = {"ms": ms, "cells_per_s": n / (ms / 1e3)}
+    out["bf16_over_fp32"] = out["bf16"]["cells_per_s"] / out["fp32"]["cells_per_s"]
+    return out
 
 
 # kernels whose accounted FLOPs run on the tensor cores
@@ -348,7 +421,7 @@ def run_reference(args):
     per, wall_ms = [], []
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        cb = cpu_baseline(layers, mode, args.k, budget_s=8.0 if s >= args.warmup else 2.0)
+        cb = cpu_baseline(layers, mode, args.k, budget_s=8.0 if s >= args.warmup else 2.0, single_thread=False)
         if s >= args.warmup:
             per.append(cb["value"])
             wall_ms.append(1e3 * (time.perf_counter() - t0))
@@ -520,6 +593,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_forms:
         line["forms"] = extraction_forms(pkg, net, L, isos, res, ms_per_step, args.mode, args.k, prec,
                                          slow=args.all_forms)
+        line["forms"]["fp32_vs_bf16"] = precision_sample(net, args.mode)
         if prec == "bf16":
             if args.all_forms:
                 line["forms"]["batched"] = batched_form(pkg, args.mode, args.k)

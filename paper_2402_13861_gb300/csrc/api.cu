@@ -55,6 +55,18 @@ void Buf::release() {
 
 namespace {
 
+// The smallest bfloat16 >= x, for finite x >= 0.
+__nv_bfloat16 bf16_round_up(float x) {
+  __nv_bfloat16 b = __float2bfloat16_rn(x);
+  if (__bfloat162float(b) < x) {
+    uint16_t bits;
+    std::memcpy(&bits, &b, 2);
+    ++bits;
+    std::memcpy(&b, &bits, 2);
+  }
+  return b;
+}
+
 isx_status check_inr(isx_inr inr) {
   if (!inr) {
     set_error("null INR handle");
@@ -85,7 +97,7 @@ isx_status bound_dispatch(isx_inr inr, const CellSource& src, int64_t n, isx_bou
   if (prec == ISX_PREC_BF16) {
     // one rule, no switch: the row-batched tensor-core path wherever it applies (hidden widths 64,
     // 128, 256), the per-cell tensor-core kernel for the shapes it alone covers
-    if (rows_supported(inr, mode, inflate)) return bound_bf16_rows(inr, src, n, mode, center, spread, st);
+    if (rows_supported(inr, mode, inflate)) return bound_bf16_rows(inr, src, n, mode, inflate, center, spread, st);
     return bound_bf16(inr, src, n, mode, inflate, center, spread, st);
   }
   return bound_fp32(inr, src, n, mode, inflate, center, spread, st);
@@ -290,6 +302,7 @@ isx_status isx_create_inr(const isx_inr_desc* d, isx_inr* out) {
   inr->Wsq_bf16.assign(L, nullptr);
   inr->Wlo_bf16.assign(L, nullptr);
   inr->Wperm_bf16.assign(L, nullptr);
+  inr->Wabsru_bf16.assign(L, nullptr);
   inr->absW_rowsum.assign(L, nullptr);
   inr->hW.resize(L);
   inr->hb.resize(L);
@@ -303,7 +316,7 @@ isx_status isx_create_inr(const isx_inr_desc* d, isx_inr* out) {
     inr->hb[l].assign(d->b[l], d->b[l] + fo);
     std::vector<float> t((size_t)fi * fo);
     std::vector<__nv_bfloat16> tb((size_t)fi * fo), rb((size_t)fi * fo), ab((size_t)fi * fo), sb((size_t)fi * fo),
-        lb((size_t)fi * fo);
+        lb((size_t)fi * fo), ub((size_t)fi * fo);
     for (int o = 0; o < fo; ++o)
       for (int i = 0; i < fi; ++i) {
         const float x = d->W[l][(size_t)o * fi + i];
@@ -312,6 +325,7 @@ isx_status isx_create_inr(const isx_inr_desc* d, isx_inr* out) {
         rb[(size_t)o * fi + i] = __float2bfloat16_rn(x);
         lb[(size_t)o * fi + i] = __float2bfloat16_rn(x - __bfloat162float(rb[(size_t)o * fi + i]));
         ab[(size_t)o * fi + i] = __float2bfloat16_rn(std::fabs(x));
+        ub[(size_t)o * fi + i] = bf16_round_up(std::fabs(x));
         sb[(size_t)o * fi + i] = __float2bfloat16_rn(x * x);
       }
     size_t bytes = (size_t)fi * fo * sizeof(float);
@@ -337,6 +351,9 @@ isx_status isx_create_inr(const isx_inr_desc* d, isx_inr* out) {
           (e = cudaMemcpy(inr->Wperm_bf16[l], pb.data(), (size_t)fi * fo * 2, cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(cuda_fail(e, "permuted W bf16", __FILE__, __LINE__));
     }
+    if ((e = cudaMalloc(&inr->Wabsru_bf16[l], (size_t)fi * fo * 2)) != cudaSuccess ||
+        (e = cudaMemcpy(inr->Wabsru_bf16[l], ub.data(), (size_t)fi * fo * 2, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return fail(cuda_fail(e, "|W| bf16 rounded up", __FILE__, __LINE__));
     if ((e = cudaMalloc(&inr->Wlo_bf16[l], (size_t)fi * fo * 2)) != cudaSuccess ||
         (e = cudaMemcpy(inr->Wlo_bf16[l], lb.data(), (size_t)fi * fo * 2, cudaMemcpyHostToDevice)) != cudaSuccess)
       return fail(cuda_fail(e, "W low bf16", __FILE__, __LINE__));
@@ -375,6 +392,7 @@ isx_status isx_destroy_inr(isx_inr inr) {
   for (auto* p : inr->Wsq_bf16) if (p) cudaFree(p);
   for (auto* p : inr->Wlo_bf16) if (p) cudaFree(p);
   for (auto* p : inr->Wperm_bf16) if (p) cudaFree(p);
+  for (auto* p : inr->Wabsru_bf16) if (p) cudaFree(p);
   if (inr->tc_net) cudaFree(inr->tc_net);
   for (auto* p : inr->absW_rowsum) if (p) cudaFree(p);
   for (auto& buf : inr->ws) buf.release();

@@ -45,6 +45,53 @@ using rows::kRT;
 using rows::roff;
 using rows::rwait;
 
+// Rounding-error inflation of the sound bound (inflate != 0).  The carried form of a pre-activation
+// is exact up to a per-neuron slack d >= |true z - carried form|.  The ReLU interval is widened by it
+// and alpha d goes into the neuron's new symbol together with the linearisation error (relu_sound,
+// as in the float32 path), so after every ReLU the carried form is exact again and the error symbols
+// propagate through W with their signs, like every other symbol.  (Carrying alpha d on as a separate
+// bound through |W| would lose the cancellation of every later layer: on a 256-wide net the bound
+// then grows by the ratio sum |W| |x| / |sum W x| per layer.)  A neuron on the linear side with
+// d > 0 therefore creates a symbol; a dead one (alpha = 0) does not.  A hidden linear layer j makes
+// the slack of the next pre-activation
+//   d' = |W_j| v,  v = alpha (kappa_g r_G + kappa_i r_I) + kappa_c |a|,
+// plus the rounding of the stored result, store * r'_G, and kappa_c |b|.  r_G, r_I are
+// the sums of |x| over the stored symbol rows (bf16) and the three input rows; kappa_g bounds the
+// symbol-row GEMM (the A operand x alpha rounded to float32 and then bf16, W_j in bf16, tensor-core
+// accumulation with unit roundoff u_a), kappa_i the two-term products of the centre and the input
+// rows (3 2^-16 per product, u_a accumulation of 3 K products).  With inflation the centre c' = W_j a
+// + b_j is computed in float32 on the CUDA cores (k_center_fp32), one fused multiply-add chain per
+// output, so its error is kappa_c (sum_k |W_nk a_k| + |b_n|), kappa_c = gamma_{K+1}(u): the tensor
+// cores' accumulation bound would give the centre an error that does not shrink with the cell.
+// Its |a| term rides in v (v = ... + kappa_c |a|), its |b| term is added by the combine.  |W_j| v is
+// itself a tensor-core GEMM
+// with both operands rounded up to bf16 (non-negative, so the exact sum is below the rounded one up
+// to the accumulation error, the factor gemm_slack).  The output layer adds the float32 dot products'
+// errors (see k_rows_output).  Constants as in set_infl; u_a = 2^-17 is a conservative unit roundoff
+// for tensor-core float32 accumulation.
+struct Infl {
+  int on = 0;
+  float kappa_g = 0, kappa_i = 0, kappa_c = 0, store = 0, gemm_slack = 1, sum_g = 1;
+  const float* bias = nullptr;                  // [w] b_j of the layer whose centre the combine reads
+  __nv_bfloat16* V = nullptr;                   // [nc][w] v, rounded up: A operand of the bound GEMM
+  const float* D = nullptr;                     // [nc][w] |W_j| v of the previous layer
+  float* RAD = nullptr;                         // [nc][w] after the last hidden layer: radius bound
+  float* SLK = nullptr;                         // [nc][w] after the last hidden layer: alpha d
+};
+constexpr float kU32 = 5.9604645e-08f;           // 2^-24
+__host__ __device__ __forceinline__ float gamma_u(double k, double u) { return (float)((k * u) / (1.0 - k * u)); }
+void set_infl(Infl& f, int w) {
+  const double ub = 1.0 / 256.0, u = 1.0 / 16777216.0, ua = 1.0 / 131072.0, K = w;
+  f.kappa_g = (float)((1.0 + ub + u) * (1.0 + ub) * (1.0 + gamma_u(K, ua)) - 1.0) * 1.0001f;
+  f.kappa_i = (float)(3.0 / 65536.0 * (1.0 + 2.0 * ub) + gamma_u(3.0 * K, ua) * (1.0 + ub) * (1.0 + ub) * (1.0 + ub) + u)
+              * 1.0001f;
+  f.kappa_c = gamma_u(K + 1.0, u) * 1.0001f;
+  f.store = (float)(ub / (1.0 - ub) + 2.0 * u) * 1.0001f;
+  f.gemm_slack = (float)(1.0 + 2.0 * gamma_u(K, ua)) * 1.0001f;
+  f.sum_g = (float)(1.0 + gamma_u(132.0, u) + 8.0 * u);
+}
+__device__ __forceinline__ __nv_bfloat16 bf16_up(float x) { return __float2bfloat16_ru(x); }
+
 // ---- layer 0 and activation 1: centre c_1, the three input rows I_1 = diag(h) W_0^T (written: the
 //      output layer of a one-hidden-layer net reads them), their reduction, the linearisation, the
 //      split A operand of the first centre / input-row GEMM (when AH is given) and the row count of
@@ -53,7 +100,7 @@ __global__ void __launch_bounds__(256) k_rows_input_act(CellSource src, int64_t 
                                                         int act, const float* __restrict__ W0,
                                                         const float* __restrict__ b0, float* I, float* A, float* AL,
                                                         float* GA, int* cnt_out, __nv_bfloat16* AH,
-                                                        __nv_bfloat16* ALO) {
+                                                        __nv_bfloat16* ALO, Infl infl) {
   __shared__ int mcount[8];
   const int tpc = w / 2, cpb = blockDim.x / tpc;
   const int sub = threadIdx.x / tpc, n = 2 * (threadIdx.x - sub * tpc);
@@ -65,7 +112,7 @@ __global__ void __launch_bounds__(256) k_rows_input_act(CellSource src, int64_t 
   int m = 0;
   if (valid) {
     float xc[3], h[3];
-    cell_box(src, first + cell, 0, xc, h);
+    cell_box(src, first + cell, infl.on, xc, h);
     if (clt)
       for (int d = 0; d < 3; ++d) h[d] *= 0.57735026918962576f;   // uniform on [-h, h] has std h / sqrt 3
     Lin L[2];
@@ -79,7 +126,24 @@ __global__ void __launch_bounds__(256) k_rows_input_act(CellSource src, int64_t 
       iv[e][2] = h[2] * w2;
       const float rad = clt ? sqrtf(iv[e][0] * iv[e][0] + iv[e][1] * iv[e][1] + iv[e][2] * iv[e][2])
                             : fabsf(iv[e][0]) + fabsf(iv[e][1]) + fabsf(iv[e][2]);
-      L[e] = clt ? act_clt(act, c, rad) : relu_sound(c, rad, 0.0f, false);
+      if (infl.on) {
+        // c: three fused multiply-adds; the input rows: one product each
+        const float ru = __fmul_ru(rad, 1.0f + 4.0f * kU32);
+        const float ex = fabsf(w0 * xc[0]) + fabsf(w1 * xc[1]) + fabsf(w2 * xc[2]) + fabsf(b0[nn]);
+        const float dl = __fmul_ru(__fadd_ru(__fmul_ru(5.0f * kU32, ex), __fmul_ru(3.0f * kU32, ru)), 1.0000010f);
+        L[e] = relu_sound(c, ru, dl, true);          // the slack is folded into the new symbol
+        const size_t o = (size_t)cell * w + nn;
+        if (infl.V) {
+          float v = __fmul_ru(infl.kappa_i, __fmul_ru(L[e].alpha, ru));
+          v = __fadd_ru(v, __fmul_ru(infl.kappa_c, fabsf(L[e].center)));
+          infl.V[o] = bf16_up(v);
+        } else {
+          infl.RAD[o] = ru;
+          infl.SLK[o] = 0.0f;
+        }
+      } else {
+        L[e] = clt ? act_clt(act, c, rad) : relu_sound(c, rad, 0.0f, false);
+      }
     }
     const size_t o = (size_t)cell * w + n;
     for (int d = 0; d < 3; ++d)
@@ -254,6 +318,58 @@ __global__ void __launch_bounds__(32 * kNewWarps) k_rows_new(int nc, int sq, con
   for (int c = 0; c < CPL; ++c) pnew[(size_t)cell * w + m0 + c] = acc[c];
 }
 
+// ---- c' = W_j a + b_j for every cell of a chunk in float32 on the CUDA cores (sound mode with
+//      inflation): output (cell, n) is one fused multiply-add chain over k = 0 .. K-1 starting from
+//      b_n, so it errs by at most gamma_{K+1} (sum_k |W_nk a_k| + |b_n|).  64 x 64 output tiles (cells x
+//      neurons), K step 16, 4 x 4 outputs per thread. ----
+__global__ void __launch_bounds__(256) k_center_fp32(int nc, int w, const float* __restrict__ A,
+                                                     const float* __restrict__ Wt, const float* __restrict__ bias,
+                                                     float* __restrict__ C) {
+  __shared__ float As[16][64 + 4];
+  __shared__ float Bs[16][64];
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float bj = (n0 + tx * 4 + j < w) ? bias[n0 + tx * 4 + j] : 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i][j] = bj;
+  }
+  for (int k0 = 0; k0 < w; k0 += 16) {
+    {
+      const int row = tid >> 2, kq = (tid & 3) * 4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (m0 + row < nc) v = *reinterpret_cast<const float4*>(A + (size_t)(m0 + row) * w + k0 + kq);
+      As[kq + 0][row] = v.x; As[kq + 1][row] = v.y; As[kq + 2][row] = v.z; As[kq + 3][row] = v.w;
+      const int kk = tid >> 4, nq = (tid & 15) * 4;
+      float4 bv = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (n0 + nq < w) bv = *reinterpret_cast<const float4*>(Wt + (size_t)(k0 + kk) * w + n0 + nq);
+      Bs[kk][nq + 0] = bv.x; Bs[kk][nq + 1] = bv.y; Bs[kk][nq + 2] = bv.z; Bs[kk][nq + 3] = bv.w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = m0 + ty * 4 + i;
+    const int c = n0 + tx * 4;
+    if (r < nc && c < w) *reinterpret_cast<float4*>(C + (size_t)r * w + c) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+  }
+}
+
 // ---- centre and input rows of z_{j+1}: c' = W a + b, I'_d = (I_d diag(alpha)) W^T, at float32-class
 //      accuracy on the tensor cores: every operand x is carried as x_hi + x_lo (two bf16 terms) and
 //      the product as a_hi w_hi + a_lo w_hi + a_hi w_lo (the dropped a_lo w_lo is below 2^-16 of
@@ -270,6 +386,7 @@ struct RowsSplitArgs {
   const float* bias;                            // [W]
   float* Cout;                                  // [nc][W]
   float* Iout;                                  // [nc][3][W]
+  float* Dout;                                  // one-product mode: [nc][W], row r of A -> row r
   int* status;
 };
 struct RowsSplitMaps {
@@ -286,7 +403,9 @@ struct SplitSmem {
   static constexpr size_t bytes() { return 1024 + 2 * kStage + SB_COUNT * 8 + 16; }
 };
 
-template <int W>
+// ONE = true: the one-product mode, D = A_hi W_hi^T for nc rows of A (no low terms, no bias): the
+// GEMM of the rounding-error bound, whose operands are non-negative and rounded up.
+template <int W, bool ONE>
 __global__ void __launch_bounds__(kST, 1) k_rows_split(const __grid_constant__ RowsSplitArgs args,
                                                         const __grid_constant__ RowsSplitMaps maps) {
   using S = SplitSmem<W>;
@@ -297,7 +416,8 @@ __global__ void __launch_bounds__(kST, 1) k_rows_split(const __grid_constant__ R
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + SB_COUNT);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int64_t ntiles = (4 * args.nc + kRT - 1) / kRT;
+  const int64_t nrows = ONE ? args.nc : 4 * args.nc;
+  const int64_t ntiles = (nrows + kRT - 1) / kRT;
   if (t == 0) {
     for (int i = 0; i < 2; ++i) {
       mbar_init(&bar[SB_FULL + i], 1);
@@ -329,11 +449,11 @@ __global__ void __launch_bounds__(kST, 1) k_rows_split(const __grid_constant__ R
           const int sidx = it & 1;
           if (!rwait(&bar[SB_EMPTY + sidx], ((it >> 1) & 1) ^ 1, abort, args.status)) break;
           uint8_t* sp = stage(sidx);
-          mbar_expect_tx(&bar[SB_FULL + sidx], (uint32_t)S::kStage);
+          mbar_expect_tx(&bar[SB_FULL + sidx], (uint32_t)(ONE ? S::kA + S::kB : S::kStage));
           tma_load_2d(sp, &maps.ahi, &bar[SB_FULL + sidx], c * 64, (int)(tile * kRT));
-          tma_load_2d(sp + S::kA, &maps.alo, &bar[SB_FULL + sidx], c * 64, (int)(tile * kRT));
+          if (!ONE) tma_load_2d(sp + S::kA, &maps.alo, &bar[SB_FULL + sidx], c * 64, (int)(tile * kRT));
           tma_load_2d(sp + 2 * S::kA, &maps.whi, &bar[SB_FULL + sidx], c * 64, 0);
-          tma_load_2d(sp + 2 * S::kA + S::kB, &maps.wlo, &bar[SB_FULL + sidx], c * 64, 0);
+          if (!ONE) tma_load_2d(sp + 2 * S::kA + S::kB, &maps.wlo, &bar[SB_FULL + sidx], c * 64, 0);
         }
         if (*abort) break;
       }
@@ -357,8 +477,10 @@ __global__ void __launch_bounds__(kST, 1) k_rows_split(const __grid_constant__ R
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             mma_bf16(dt, sdesc(ah + kk * 32), sdesc(bh + kk * 32), id, (c > 0 || kk > 0) ? 1u : 0u);
-            mma_bf16(dt, sdesc(al + kk * 32), sdesc(bh + kk * 32), id, 1u);
-            mma_bf16(dt, sdesc(ah + kk * 32), sdesc(bl + kk * 32), id, 1u);
+            if (!ONE) {
+              mma_bf16(dt, sdesc(al + kk * 32), sdesc(bh + kk * 32), id, 1u);
+              mma_bf16(dt, sdesc(ah + kk * 32), sdesc(bl + kk * 32), id, 1u);
+            }
           }
           mma_commit(&bar[SB_EMPTY + sidx]);
         }
@@ -375,11 +497,11 @@ __global__ void __launch_bounds__(kST, 1) k_rows_split(const __grid_constant__ R
       if (!__all_sync(0xffffffffu, got)) break;
       tc_fence_after();
       const int64_t r = tile * kRT + row;
-      const int64_t cell = r >> 2;
-      const int q = (int)(r & 3);
+      const int64_t cell = ONE ? r : r >> 2;
+      const int q = ONE ? 1 : (int)(r & 3);
       const bool valid = cell < args.nc;
       float* dst = nullptr;
-      if (valid) dst = (q == 0) ? args.Cout + cell * W : args.Iout + (cell * 3 + q - 1) * W;
+      if (valid) dst = ONE ? args.Dout + r * W : (q == 0) ? args.Cout + cell * W : args.Iout + (cell * 3 + q - 1) * W;
       const uint32_t trow = tmem + b * W + ((uint32_t)(32 * (warp & 3)) << 16);
 #pragma unroll 1
       for (int c0 = 0; c0 < W; c0 += 32) {
@@ -437,7 +559,7 @@ __global__ void __launch_bounds__(32 * kRedWarps) k_rows_reduce_act(int nc, int 
                                                                     const int* cnt_in, const int* cnt_out,
                                                                     const float* I, const float* C, float* A, float* AL,
                                                                     float* GA, int* cnt_next, __nv_bfloat16* AH,
-                                                                    __nv_bfloat16* ALO) {
+                                                                    __nv_bfloat16* ALO, Infl infl) {
   constexpr int w = 32 * CPL;
   const int lane = threadIdx.x & 31;
   const int cell = blockIdx.x * kRedWarps + (threadIdx.x >> 5);
@@ -452,7 +574,11 @@ __global__ void __launch_bounds__(32 * kRedWarps) k_rows_reduce_act(int nc, int 
   for (int d = 0; d < 3; ++d) ldv<CPL>(I + ((size_t)cell * 3 + d) * w + n0, iv[d]);
   ldv<CPL>(C + (size_t)cell * w + n0, cv);
   ldv<CPL>(pnew + (size_t)cell * w + n0, pv);
-  float s[CPL], e[CPL];
+  float dv[CPL];
+  if (infl.on) ldv<CPL>(infl.D + (size_t)cell * w + n0, dv);
+  // s: the symbol rows' sum (column sums of the row GEMM and of the new rows), compensated; sI: the
+  // three input rows'
+  float s[CPL], e[CPL], sI[CPL];
   auto add = [&](int i, float v) {
     const float y = v - e[i], tt = s[i] + y;
     e[i] = (tt - s[i]) - y;
@@ -461,8 +587,9 @@ __global__ void __launch_bounds__(32 * kRedWarps) k_rows_reduce_act(int nc, int 
 #pragma unroll
   for (int i = 0; i < CPL; ++i) {
     s[i] = e[i] = 0.0f;
+    sI[i] = 0.0f;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) add(i, sq ? iv[d][i] * iv[d][i] : fabsf(iv[d][i]));
+    for (int d = 0; d < 3; ++d) sI[i] += sq ? iv[d][i] * iv[d][i] : fabsf(iv[d][i]);
     add(i, pv[i]);
   }
   if (rows > 0) {
@@ -476,17 +603,38 @@ __global__ void __launch_bounds__(32 * kRedWarps) k_rows_reduce_act(int nc, int 
   }
   float av[CPL], alv[CPL], gv[CPL];
   int m = 0;
+  const size_t o = (size_t)cell * w + n0;
 #pragma unroll
   for (int i = 0; i < CPL; ++i) {
-    const float r = sq ? sqrtf(s[i]) : s[i];
-    const Lin L = sq ? act_clt(act, cv[i], r) : relu_sound(cv[i], r, 0.0f, false);
+    Lin L;
+    if (infl.on) {
+      const float sg = s[i];
+      const float ru = __fmul_ru(__fadd_ru(sg, sI[i]), infl.sum_g);
+      float dl = __fmul_ru(dv[i], infl.gemm_slack);
+      dl = __fadd_ru(dl, __fmul_ru(infl.store, __fmul_ru(sg, infl.sum_g)));
+      dl = __fadd_ru(dl, __fmul_ru(infl.kappa_c, fabsf(infl.bias[n0 + i])));
+      L = relu_sound(cv[i], ru, dl, true);           // the slack is folded into the new symbol
+      if (AH) {
+        float v = __fmul_ru(L.alpha, __fmul_ru(infl.kappa_g, __fmul_ru(sg, infl.sum_g)));
+        v = __fadd_ru(v, __fmul_ru(L.alpha, __fmul_ru(infl.kappa_i, __fmul_ru(sI[i], infl.sum_g))));
+        v = __fadd_ru(v, __fmul_ru(infl.kappa_c, fabsf(L.center)));
+        infl.V[o + i] = bf16_up(v);
+      } else {
+        infl.RAD[o + i] = ru;
+        infl.SLK[o + i] = 0.0f;
+      }
+    } else {
+      const float tot = s[i] + sI[i];
+      const float r = sq ? sqrtf(tot) : tot;
+      L = sq ? act_clt(act, cv[i], r) : relu_sound(cv[i], r, 0.0f, false);
+    }
     av[i] = L.center;
     alv[i] = L.alpha;
     gv[i] = L.gamma;
     m += L.gamma != 0.0f;
   }
-  const size_t o = (size_t)cell * w + n0;
-  if (!AH) stv<CPL>(A + o, av);                   // the centre a is read back only after the last layer
+  // the centre a is read back after the last layer, and by the float32 centre GEMM with inflation
+  if (!AH || infl.on) stv<CPL>(A + o, av);
   stv<CPL>(AL + o, alv);
   stv<CPL>(GA + o, gv);
   if (AH) {
@@ -517,22 +665,35 @@ __global__ void __launch_bounds__(32 * kRedWarps) k_rows_reduce_act(int nc, int 
 
 // ---- output layer and read-off: x0 = w_out . a + b_out; every symbol's output coefficient is its
 //      row . (alpha_H * w_out), or gamma_n w_out,n for the last activation's symbols ----
+// With inflation (sound mode) the radius adds the float32 errors of the output layer and the slack:
+//   (1 + gamma_S) sum |y_i|  +  gamma_{w+1} sum_n |alpha_n w_n| RAD_n  +  (1 + gamma_w) sum_n |w_n| SLK_n
+//   + gamma_{w+1} (sum_n |w_n a_n| + |b|)  +  u sum_n |gamma_n w_n|,
+// S the number of symbols: each y_i = row_i . (alpha o w) errs by gamma_{w+1} sum_n |x_in| |alpha_n w_n|
+// (summed over i: RAD_n bounds sum_i |x_in|), the centre's dot product by gamma_{w+1} of its terms, the
+// last activation's symbols gamma_n w_n by one rounding, and the slack alpha d passes through |w|.
 __global__ void __launch_bounds__(256) k_rows_output(int w, int mode, const __nv_bfloat16* X, const int64_t* off,
                                                      const int* cnt, const float* I, const float* A,
                                                      const float* AL, const float* GA,
                                                      const float* __restrict__ wout, float bout, int64_t first,
-                                                     float* center, float* spread) {
+                                                     float* center, float* spread, Infl infl) {
   __shared__ float v[kMaxW];
-  __shared__ float red[2][8];
+  __shared__ float red[3][8];
   const int cell = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const bool sq = mode != ISX_BOUND_SOUND;
-  float x0 = 0.0f, s = 0.0f;
+  float x0 = 0.0f, s = 0.0f, ex = 0.0f;
+  const float gw = gamma_u((double)w + 1.0, 5.9604644775390625e-08);
   for (int n = t; n < w; n += blockDim.x) {
     const size_t o = (size_t)cell * w + n;
     v[n] = AL[o] * wout[n];
     x0 = fmaf(wout[n], A[o], x0);
     const float y = GA[o] * wout[n];
     s += sq ? y * y : fabsf(y);
+    if (infl.on) {
+      ex = __fadd_ru(ex, __fmul_ru(gw, __fmul_ru(fabsf(v[n]), infl.RAD[o])));
+      ex = __fadd_ru(ex, __fmul_ru(1.0f + gw, __fmul_ru(fabsf(wout[n]), infl.SLK[o])));
+      ex = __fadd_ru(ex, __fmul_ru(gw, fabsf(wout[n] * A[o])));
+      ex = __fadd_ru(ex, __fmul_ru(kU32, fabsf(y)));
+    }
   }
   __syncthreads();
   // three input rows and the G rows: one warp per row
@@ -571,54 +732,75 @@ __global__ void __launch_bounds__(256) k_rows_output(int w, int mode, const __nv
   for (int o = 16; o > 0; o >>= 1) {
     x0 += __shfl_xor_sync(0xffffffffu, x0, o);
     s += __shfl_xor_sync(0xffffffffu, s, o);
+    ex += __shfl_xor_sync(0xffffffffu, ex, o);
   }
   if (lane == 0) {
     red[0][warp] = x0;
     red[1][warp] = s;
+    red[2][warp] = ex;
   }
   __syncthreads();
   if (t == 0) {
-    float a = 0.0f, b = 0.0f;
+    float a = 0.0f, b = 0.0f, e = 0.0f;
     for (int i = 0; i < 8; ++i) {
       a += red[0][i];
       b += red[1][i];
+      e += red[2][i];
     }
     center[first + cell] = a + bout;
-    spread[first + cell] = (mode == ISX_BOUND_SOUND) ? b : sqrtf(mode == ISX_BOUND_RAUA ? b / 3.0f : b);
+    if (infl.on) {
+      // S symbols summed in float32: a factor 1 + gamma_S, S = rows + 3 + w; the partial sums of the
+      // error terms are rounded up and their float32 additions covered by the 1 + 2^-20 factor
+      const float gS = gamma_u((double)(cnt[cell] + 3 + w), 5.9604644775390625e-08);
+      e = __fadd_ru(e, __fmul_ru(gw, fabsf(bout)));
+      e = __fadd_ru(e, 2.0f * kU32 * (fabsf(a) + fabsf(bout)));      // the final add of the centre
+      e = __fmul_ru(e, 1.0000050f);
+      spread[first + cell] = __fadd_ru(__fmul_ru(b, 1.0f + 2.0f * gS), e);
+    } else {
+      spread[first + cell] = (mode == ISX_BOUND_SOUND) ? b : sqrtf(mode == ISX_BOUND_RAUA ? b / 3.0f : b);
+    }
   }
 }
 
-template <int W>
+template <int W, bool ONE>
 isx_status launch_rows_split(isx_inr inr, const RowsSplitArgs& a, const RowsSplitMaps& maps, cudaStream_t st) {
   const size_t smem = SplitSmem<W>::bytes();
-  ISX_CUDA(cudaFuncSetAttribute(k_rows_split<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ISX_CUDA(cudaFuncSetAttribute(k_rows_split<W, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int sms = 148;
   ISX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, inr->device));
   int per_sm = 1;
-  ISX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_split<W>, kST, smem));
+  ISX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_split<W, ONE>, kST, smem));
   per_sm = std::max(1, std::min(per_sm, 512 / (2 * W)));
-  const int64_t ntiles = (4 * a.nc + kRT - 1) / kRT;
+  const int64_t ntiles = ((ONE ? 1 : 4) * a.nc + kRT - 1) / kRT;
   const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
-  k_rows_split<W><<<grid, kST, smem, st>>>(a, maps);
+  k_rows_split<W, ONE><<<grid, kST, smem, st>>>(a, maps);
   ISX_LAUNCH_CHECK("k_rows_split");
   return ISX_OK;
+}
+template <bool ONE>
+isx_status launch_rows_split_w(isx_inr inr, int w, const RowsSplitArgs& a, const RowsSplitMaps& maps,
+                               cudaStream_t st) {
+  if (w == 256) return launch_rows_split<256, ONE>(inr, a, maps, st);
+  if (w == 128) return launch_rows_split<128, ONE>(inr, a, maps, st);
+  return launch_rows_split<64, ONE>(inr, a, maps, st);
 }
 
 }  // namespace
 
 bool rows_supported(isx_inr inr, isx_bound_mode mode, int inflate) {
+  (void)inflate;
   if (!(inr->w == 64 || inr->w == 128 || inr->w == 256) || inr->H < 1) return false;
-  if (mode == ISX_BOUND_SOUND && inflate) return false;
   return mode == ISX_BOUND_SOUND || mode == ISX_BOUND_CLT || mode == ISX_BOUND_RAUA;
 }
 
-isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bound_mode mode, float* d_center,
-                           float* d_spread, cudaStream_t st) {
+isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bound_mode mode, int inflate,
+                           float* d_center, float* d_spread, cudaStream_t st) {
   if (n <= 0) return ISX_OK;
-  if (!rows_supported(inr, mode, 0)) {
-    set_error("row-batched tensor-core bounds need hidden width 64, 128 or 256 and no inflation");
+  if (!rows_supported(inr, mode, inflate)) {
+    set_error("row-batched tensor-core bounds need hidden width 64, 128 or 256");
     return ISX_ERR_UNSUPPORTED;
   }
+  if (mode != ISX_BOUND_SOUND) inflate = 0;
   const int w = inr->w, H = inr->H;
   auto& ws = inr->ws;
   ISX_TRY(ws[WS_TC_STATUS].ensure(64, "tc status"));
@@ -634,6 +816,9 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
     ISX_TRY(tensor_map_bf16(&pmaps[l], inr->Wperm_bf16[l] ? inr->Wperm_bf16[l] : inr->W_bf16[l], w, w, 64, w));
   }
   const int sq = mode == ISX_BOUND_CLT ? 1 : 0;
+  std::vector<CUtensorMap> absmaps(inr->n_layers);
+  if (inflate)
+    for (int l = 1; l <= H - 1; ++l) ISX_TRY(tensor_map_bf16(&absmaps[l], inr->Wabsru_bf16[l], w, w, 64, w));
   // chunk size: about kRowBudget G rows per chunk, from the rows per cell the previous chunk needed
   const int64_t kRowBudget = 1 << 24;
   const int64_t kMaxCells = kMaxChunkCells;
@@ -650,6 +835,15 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
     ISX_TRY(ws[WS_R_I0].ensure(3 * cw, "rows input rows"));
     ISX_TRY(ws[WS_R_I1].ensure(3 * cw, "rows input rows"));
     ISX_TRY(ws[WS_R_PNEW].ensure(cw, "new-row column sums"));
+    Infl infl;
+    if (inflate) {
+      ISX_TRY(ws[WS_R_V].ensure(cw / 2, "rounding-bound operand"));
+      ISX_TRY(ws[WS_R_D].ensure(cw, "rounding-bound GEMM result"));
+      ISX_TRY(ws[WS_RAD].ensure(cw, "last radius bound"));
+      ISX_TRY(ws[WS_DELTA].ensure(cw, "last slack"));
+      infl.on = 1;
+      set_infl(infl, w);
+    }
     ISX_TRY(ws[WS_R_AH].ensure(4 * cw / 2, "split A, high terms"));
     ISX_TRY(ws[WS_R_ALO].ensure(4 * cw / 2, "split A, low terms"));
     for (Slot s : {WS_R_CNT0, WS_R_CNT1}) ISX_TRY(ws[s].ensure((size_t)nc * sizeof(int), "rows counts"));
@@ -669,8 +863,14 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
     const int act_blocks = (int)((nc + (512 / w) - 1) / (512 / w));   // 512 / w cells per block
     {
       prof::Scope ps(K_ROWS_ACT, st, 2.0 * nc * 3 * w, 0);
+      Infl fi = infl;
+      if (inflate) {
+        fi.V = H > 1 ? ws[WS_R_V].as<__nv_bfloat16>() : nullptr;
+        fi.RAD = ws[WS_RAD].as<float>();
+        fi.SLK = ws[WS_DELTA].as<float>();
+      }
       k_rows_input_act<<<act_blocks, 256, 0, st>>>(src, first, nc, w, (int)mode, inr->act, inr->W[0], inr->b[0], I0,
-                                                   A, AL, GA, ws[cs[1]].as<int>(), H > 1 ? AH : nullptr, ALO);
+                                                   A, AL, GA, ws[cs[1]].as<int>(), H > 1 ? AH : nullptr, ALO, fi);
       ISX_LAUNCH_CHECK("k_rows_input_act");
     }
     ISX_CUDA(cudaMemsetAsync(ws[cs[0]].ptr, 0, (size_t)nc * sizeof(int), st));
@@ -743,13 +943,27 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
         sm.whi = maps[j];
         sm.wlo = lomaps[j];
         prof::Scope ps(K_ROWS_SPLIT, st, 2.0 * nc * 4.0 * w * w, 0);
-        if (w == 256) {
-          ISX_TRY(launch_rows_split<256>(inr, sa, sm, st));
-        } else if (w == 128) {
-          ISX_TRY(launch_rows_split<128>(inr, sa, sm, st));
-        } else {
-          ISX_TRY(launch_rows_split<64>(inr, sa, sm, st));
-        }
+        ISX_TRY(launch_rows_split_w<false>(inr, w, sa, sm, st));
+      }
+      if (inflate) {
+        // the centre in float32 on the CUDA cores, over the tensor cores' two-term one
+        prof::Scope pc(K_GEMM_FP32, st, 2.0 * nc * w * w, 0);
+        k_center_fp32<<<dim3((unsigned)((w + 63) / 64), (unsigned)((nc + 63) / 64)), 256, 0, st>>>(nc, w, A, inr->Wt[j],
+                                                                                                  inr->b[j], C);
+        ISX_LAUNCH_CHECK("k_center_fp32");
+      }
+      if (inflate) {
+        // the rounding-error bound's GEMM: D = |W_j| v, operands rounded up
+        RowsSplitArgs da{};
+        da.nc = nc;
+        da.Dout = ws[WS_R_D].as<float>();
+        da.status = status;
+        RowsSplitMaps dm;
+        std::memset(&dm, 0, sizeof(dm));
+        ISX_TRY(tensor_map_bf16(&dm.ahi, ws[WS_R_V].ptr, w, (uint64_t)nc, 64, kRT));
+        dm.whi = absmaps[j];
+        prof::Scope ps(K_ROWS_AUX, st, 2.0 * nc * w * w, 0);
+        ISX_TRY(launch_rows_split_w<true>(inr, w, da, dm, st));
       }
       {
         // reductions of z_{j+1} and activation j+1; its row count goes to the buffer of X_j's counts.
@@ -762,15 +976,23 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
         const unsigned rb = (unsigned)((nc + kRedWarps - 1) / kRedWarps);
         int* cn = last ? nullptr : cnt_in;
         __nv_bfloat16* ah = last ? nullptr : AH;
+        Infl fi = infl;
+        if (inflate) {
+          fi.bias = inr->b[j];
+          fi.D = ws[WS_R_D].as<float>();
+          fi.V = last ? nullptr : ws[WS_R_V].as<__nv_bfloat16>();
+          fi.RAD = ws[WS_RAD].as<float>();
+          fi.SLK = ws[WS_DELTA].as<float>();
+        }
         if (w == 256)
           k_rows_reduce_act<8><<<rb, 32 * kRedWarps, 0, st>>>(nc, (int)mode, inr->act, part, pnew, off_in, cnt_in,
-                                                              cnt_out, I1, C, A, AL, GA, cn, ah, ALO);
+                                                              cnt_out, I1, C, A, AL, GA, cn, ah, ALO, fi);
         else if (w == 128)
           k_rows_reduce_act<4><<<rb, 32 * kRedWarps, 0, st>>>(nc, (int)mode, inr->act, part, pnew, off_in, cnt_in,
-                                                              cnt_out, I1, C, A, AL, GA, cn, ah, ALO);
+                                                              cnt_out, I1, C, A, AL, GA, cn, ah, ALO, fi);
         else
           k_rows_reduce_act<2><<<rb, 32 * kRedWarps, 0, st>>>(nc, (int)mode, inr->act, part, pnew, off_in, cnt_in,
-                                                              cnt_out, I1, C, A, AL, GA, cn, ah, ALO);
+                                                              cnt_out, I1, C, A, AL, GA, cn, ah, ALO, fi);
         ISX_LAUNCH_CHECK("k_rows_reduce_act");
       }
       std::swap(I0, I1);
@@ -780,9 +1002,14 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
     {
       prof::Scope ps(K_ROWS_OUT, st, 2.0 * (double)(R + 3.0 * nc) * w, 2.0 * (double)R * w + 4.0 * 7.0 * nc * w);
       const int L = inr->n_layers - 1;
+      Infl fi = infl;
+      if (inflate) {
+        fi.RAD = ws[WS_RAD].as<float>();
+        fi.SLK = ws[WS_DELTA].as<float>();
+      }
       k_rows_output<<<nc, 256, 0, st>>>(w, (int)mode, ws[xs[cur]].as<__nv_bfloat16>(), ws[os[cur]].as<int64_t>(),
                                         ws[cs[cur]].as<int>(), I0, A, AL, GA, inr->W[L], inr->hb[L][0], first,
-                                        d_center, d_spread);
+                                        d_center, d_spread, fi);
       ISX_LAUNCH_CHECK("k_rows_output");
     }
     rows_per_cell = std::max(1.0, (double)R / nc);

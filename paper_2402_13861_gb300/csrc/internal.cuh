@@ -55,7 +55,7 @@ enum Slot {
   WS_ANC_C_A, WS_ANC_C_B, WS_ANC_S_A, WS_ANC_S_B, WS_ANC_G_A, WS_ANC_G_B, WS_PROP_KEEP, WS_PROP_NEED,
   WS_PROP_IDX, WS_PROP_CODES,
   WS_R_I0, WS_R_I1, WS_R_A, WS_R_CNT0, WS_R_CNT1, WS_R_OFF0, WS_R_OFF1, WS_R_RC0, WS_R_RC1, WS_R_TOT, WS_R_AH, WS_R_ALO,
-  WS_R_PART, WS_R_PNEW,
+  WS_R_PART, WS_R_PNEW, WS_R_V, WS_R_D,
   WS_N_SLOTS
 };
 
@@ -76,6 +76,8 @@ struct isx_inr_s {
   std::vector<__nv_bfloat16*> Wsq_bf16;  // W[l]^2 in bfloat16 (row-major)
   std::vector<__nv_bfloat16*> Wlo_bf16;  // W[l] - float(W_bf16[l]) in bfloat16: low part of a two-term split
   std::vector<__nv_bfloat16*> Wperm_bf16; // W_bf16[l] with its rows in the row GEMM's order (w = 256 only)
+  std::vector<__nv_bfloat16*> Wabsru_bf16; // |W[l]| rounded up to bfloat16 (row-major): the rounding-error
+                                           // bound's GEMM, whose result must not fall below |W| v
   void* tc_net = nullptr;                // device network descriptor of the tensor-core bound kernel
   std::vector<float*> absW_rowsum;       // sum_k |W[l][n][k]| per output neuron
   std::vector<std::vector<float>> hW, hb;  // host copies
@@ -135,9 +137,9 @@ __host__ __device__ __forceinline__ bool sound_readout(int mode) {
 
 // Row-batched tensor-core path: layer-synchronous over a chunk of cells, noise-symbol rows with a
 // zero coefficient dropped, alpha applied on the A side so that one weight operand serves all
-// cells (bound_rows.cu).  Hidden widths 64, 128 and 256, no inflation.
-isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bound_mode mode, float* d_center,
-                           float* d_spread, cudaStream_t st);
+// cells (bound_rows.cu).  Hidden widths 64, 128 and 256; sound bounds with or without inflation.
+isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bound_mode mode, int inflate,
+                           float* d_center, float* d_spread, cudaStream_t st);
 bool rows_supported(isx_inr inr, isx_bound_mode mode, int inflate);
 
 // Tensor-core (tcgen05, bfloat16) path; ISX_ERR_UNSUPPORTED for shapes it does not cover.

@@ -37,7 +37,8 @@ __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: 
 //  - warps 6-9 drain the two TMEM accumulators.  Thread m owns the neurons of weight row m of each
 //    half and walks the tile's rows in order: it stores each row's bf16 value (a bf16 pair for
 //    W = 256) and adds f(value) to a running sum that it writes to part[cell + tile] whenever the
-//    row's cell changes (f of the float32 accumulator value: within 2^-8 of f of the stored value).
+//    row's cell changes (|stored bf16 value| for the radius, which the rounding-error bound needs;
+//    the square of the float32 accumulator value for sigma, within 2^-7 of the stored value's).
 //    Every thread sees the same rows, so the segment boundaries are uniform; a segment's rows are
 //    consecutive in the output too, so its destination advances by one row per row.
 //    The destination row and cell of every row of the next tile are loaded while this tile drains
@@ -278,12 +279,20 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
             dp = args.xout + (size_t)__shfl_sync(0xffffffffu, dl, i) * W + n0;
           }
           if (NH == 2) {
-            *reinterpret_cast<__nv_bfloat162*>(dp) = __floats2bfloat162_rn(v0[i], v1[i]);
-            s0 = SQ ? fmaf(v0[i], v0[i], s0) : s0 + fabsf(v0[i]);
-            s1 = SQ ? fmaf(v1[i], v1[i], s1) : s1 + fabsf(v1[i]);
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v0[i], v1[i]);
+            *reinterpret_cast<__nv_bfloat162*>(dp) = h;
+            if (SQ) {
+              s0 = fmaf(v0[i], v0[i], s0);
+              s1 = fmaf(v1[i], v1[i], s1);
+            } else {                                       // the radius sums the stored values
+              const float2 f = __bfloat1622float2(h);
+              s0 += fabsf(f.x);
+              s1 += fabsf(f.y);
+            }
           } else if (own) {
-            *dp = __float2bfloat16_rn(v0[i]);
-            s0 = SQ ? fmaf(v0[i], v0[i], s0) : s0 + fabsf(v0[i]);
+            const __nv_bfloat16 h = __float2bfloat16_rn(v0[i]);
+            *dp = h;
+            s0 = SQ ? fmaf(v0[i], v0[i], s0) : s0 + fabsf(__bfloat162float(h));
           }
           dp += W;
         }

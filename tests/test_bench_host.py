@@ -88,7 +88,7 @@ def test_job_totals_single_rank():
 def test_reference_line_shape(monkeypatch, capsys):
     """The oracle arm prints one JSON line with the contract's keys (the oracle itself is replaced
     by a stub sample here so that the test takes no CPU time)."""
-    monkeypatch.setattr(bench, "cpu_baseline", lambda layers, mode, k, budget_s=12.0: {
+    monkeypatch.setattr(bench, "cpu_baseline", lambda layers, mode, k, budget_s=12.0, single_thread=True: {
         "value": 100.0, "unit": "cells/s", "cores": 2, "kind": "oracle", "sample": "stub"})
     monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "2", "--warmup", "0"])
     args = bench.parse()

@@ -68,7 +68,7 @@ def test_bf16_bounds_match_oracle(pkg, dims, mode):
     net.close()
 
 
-@pytest.mark.parametrize("dims", [[3, 128, 128, 128, 1], "scientific"])
+@pytest.mark.parametrize("dims", [[3, 64, 64, 64, 64, 1], [3, 128, 128, 128, 1], [3] + [256] * 5 + [1], "scientific"])
 def test_bf16_inflated_sound_bounds_contain_samples(pkg, dims):
     layers = inr.load_inr(dims)[0] if isinstance(dims, str) else inr.random_inr(dims, 5)
     net = pkg.Inr(layers)
@@ -149,15 +149,28 @@ def test_bf16_extraction_small_matches_oracle(pkg, mode):
     net.close()
 
 
-def test_bf16_sound_inflated_extraction_misses_nothing(pkg):
-    """Sound bf16 bounds with inflation keep every cell whose float32 corner values straddle the
-    iso-value: hierarchical triangles equal the dense ones."""
-    layers = inr.random_inr([3, 128, 128, 128, 1], 32)
+@pytest.mark.parametrize("name,L", [("random128x3", 5), ("small", 6), ("scientific", 6), ("scientific", 7)])
+def test_bf16_sound_inflated_extraction_misses_nothing(pkg, name, L):
+    """Sound bf16 bounds with inflation (row-batched path) keep every cell whose float32 corner values
+    straddle an iso-value: the hierarchical triangles are exactly the dense ones (FNR = 0)."""
+    if name == "random128x3":
+        layers = inr.random_inr([3, 128, 128, 128, 1], 32)
+        vals = mlp.mlp_forward(layers, octree.lattice_points(1 << L))
+        isos = np.quantile(vals, [0.4, 0.7]).astype(np.float32)
+    else:
+        layers, isos, _ = inr.load_inr(name)
     net = pkg.Inr(layers)
-    L = 5
-    vals = mlp.mlp_forward(layers, octree.lattice_points(1 << L))
-    isos = np.quantile(vals, [0.4, 0.7]).astype(np.float32)
-    h = net.extract(L, isos, mode="sound", prec="bf16", inflate=True)
-    d = net.extract(L, isos, prec="fp32", dense=True)
-    assert h["n_tris"] == d["n_tris"] and d["n_tris"] > 0
+    from paper_2402_13861_gb300 import _lib
+    _lib.profile_reset()
+    h = net.extract(L, isos, mode="sound", prec="bf16", inflate=True, active_cap=1 << 20, tri_cap=1 << 22)
+    launches = _lib.profile_read()
+    d = net.extract(L, isos, prec="fp32", dense=True, active_cap=1 << 20, tri_cap=1 << 22)
+    assert launches.get("rows_gemm", {"launches": 0})["launches"] > 0 or len(layers) < 4
+    assert launches.get("bound_tc", {"launches": 0})["launches"] == 0
+    gh = set(zip((to_np(h["tri_cell"]).astype(np.int64) & 0xFFFFFFFF).tolist(), to_np(h["tri_iso"]).tolist()))
+    gd = set(zip((to_np(d["tri_cell"]).astype(np.int64) & 0xFFFFFFFF).tolist(), to_np(d["tri_iso"]).tolist()))
+    print(f"{name} {1 << L}^3: {h['n_tris']} hierarchical vs {d['n_tris']} dense triangles, "
+          f"{sum(h['cells_bounded'])} cells bounded, {h['n_active']} active")
+    assert gd <= gh and h["n_tris"] == d["n_tris"] and d["n_tris"] > 0
+    assert torch.equal(torch.sort(h["tri_edge"].reshape(-1))[0], torch.sort(d["tri_edge"].reshape(-1))[0])
     net.close()

@@ -47,8 +47,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--all-forms", action="store_true",
-                    help="also the slow forms: the per-cell kernel, RA-Fixed, the batched form (fits 8 nets) and "
-                         "the SIREN workload (fits a SIREN); the default run keeps the quick ones")
+                    help="also the slow forms: RA-Fixed and the SIREN workload (fits a SIREN); the default run "
+                         "keeps the quick ones")
     return ap.parse_args()
 
 
@@ -217,23 +217,27 @@ def extraction_forms(pkg, net, L, isos, plain, plain_ms, mode, k, prec, slow=Fal
     return out
 
 
-def batched_form(pkg, mode, k):
-    """The batched form: 8 INRs of mixed shape (hidden widths 128 / 256, 3-5 hidden layers), each fitted
-    for 300 Adam steps to its own field of the scientific kind (32-256 anisotropic Gaussians + sine),
-    16 iso-values over the 10-90 % quantiles, octrees to 64^3 or 128^3.  Reports the time of running
-    the 8 extractions one after another and as one batch replayed from its CUDA graph (after a
-    sizing run and a capture run)."""
+def batched_form(pkg, mode, k, workers=8):
+    """The batched form: 32 extractions of mixed shape in flight together.  8 networks (hidden widths
+    64 / 128 / 256, 3-6 hidden layers), each fitted for 300 Adam steps to its own field of the
+    scientific kind (32-256 anisotropic Gaussians + sine), give 4 entries each (own INR handle): octrees
+    to 128^3 and 256^3, 16 iso-values over the 10-90 % or 20-80 % quantiles.  Reports the 32 extractions
+    run one after another and as one isx_batch_run on `workers` worker streams, and checks that every
+    entry's mesh is the same."""
     import torch
     from synth import fields, inr
-    specs = [(128, 3, 7, 32), (256, 4, 6, 64), (128, 5, 7, 128), (256, 3, 7, 256), (128, 4, 6, 48),
-             (256, 5, 6, 96), (128, 3, 7, 192), (256, 4, 7, 160)]
-    nets, params = [], []
-    for i, (w, H, L, nb) in enumerate(specs):
+    specs = [(64, 3, 32), (128, 3, 64), (256, 3, 128), (64, 5, 48), (128, 4, 96), (256, 4, 160), (128, 6, 192),
+             (256, 5, 256)]
+    nets, params, shapes = [], [], []
+    for i, (w, H, nb) in enumerate(specs):
         layers, _ = inr.fit([3] + [w] * H + [1], fields.anisotropic_blobs(4000 + i, nb), 300, init_seed=4000 + i,
                             sample_seed=5000 + i)
-        isos = inr.quantile_isos(layers, 16, grid=64)
-        nets.append(pkg.Inr(layers))
-        params.append(dict(max_level=L, isos=isos, mode=mode, k=k, prec="bf16"))
+        for j, (L, lo_q, hi_q) in enumerate(((7, 0.1, 0.9), (7, 0.2, 0.8), (8, 0.1, 0.9), (8, 0.2, 0.8))):
+            isos = inr.quantile_isos(layers, 16, lo_q=lo_q, hi_q=hi_q, grid=64)
+            nets.append(pkg.Inr(layers))
+            params.append(dict(max_level=L, isos=isos, mode=mode, k=k, prec="bf16",
+                               eval_prec="bf16" if w in (128, 256) else "fp32"))
+            shapes.append(f"w{w}xH{H}@{1 << L}^3")
     st = torch.cuda.current_stream()
 
     def ev_ms(fn):
@@ -246,19 +250,20 @@ def batched_form(pkg, mode, k):
 
     bufs = [dict() for _ in nets]
     for net, p, bf in zip(nets, params, bufs):
-        net.extract(buffers=bf, **p)                            # warm-up, sizes the buffers
-    singles, seq_rows_ms = ev_ms(lambda: [net.extract(buffers=bf, **p) for net, p, bf in zip(nets, params, bufs)])
-    batch = pkg.Batch(nets, params, use_graph=True)
-    batch.run()                                                 # sized run
-    batch.run()                                                 # capture and first replay
-    res, batch_ms = ev_ms(batch.run)
+        net.extract(buffers=bf, active_cap=1 << 21, tri_cap=1 << 23, **p)      # warm-up, sizes every workspace
+    singles, seq_ms = ev_ms(lambda: [net.extract(buffers=bf, **p) for net, p, bf in zip(nets, params, bufs)])
+    singles = [(s["n_active"], s["n_tris"]) for s in singles]
+    batch = pkg.Batch(nets, params, workers=workers)
+    batch.run(active_cap=1 << 21, tri_cap=1 << 23)                            # sizes the batch's buffers
+    res, batch_ms = ev_ms(lambda: batch.run(active_cap=1 << 21, tri_cap=1 << 23))
+    same = all((r["n_active"], r["n_tris"]) == s for r, s in zip(res, singles))
+    cells = int(sum(sum(r["cells_bounded"]) for r in res))
     batch.close()
     for net in nets:
         net.close()
-    return {"entries": len(specs), "shapes": [f"w{w}xH{H}@{1 << L}^3" for w, H, L, _ in specs], "isos_each": 16,
-            "batched_graph_ms": batch_ms, "sequential_row_batched_ms": seq_rows_ms,
-            "n_active_batch": [r["n_active"] for r in res], "n_active_sequential": [s["n_active"] for s in singles],
-            "cells_bounded_sequential": int(sum(sum(s["cells_bounded"]) for s in singles))}
+    return {"entries": len(nets), "shapes": shapes, "isos_each": 16, "workers": workers,
+            "sequential_ms": seq_ms, "batch_ms": batch_ms, "speedup": seq_ms / batch_ms, "same_meshes": bool(same),
+            "cells_bounded": cells, "batch_cells_per_s": cells / (batch_ms / 1e3)}
 
 
 def activation_forms(pkg, k, names=("siren", "sdf_elu")):
@@ -593,12 +598,17 @@ def main():
     if rank == 0 and world == 1 and not args.no_forms:
         line["forms"] = extraction_forms(pkg, net, L, isos, res, ms_per_step, args.mode, args.k, prec,
                                          slow=args.all_forms)
-        line["forms"]["fp32_vs_bf16"] = precision_sample(net, args.mode)
+        # every further form is measured on its own: one that fails records its error, never the line
+        extra = [("fp32_vs_bf16", lambda: precision_sample(net, args.mode))]
         if prec == "bf16":
-            if args.all_forms:
-                line["forms"]["batched"] = batched_form(pkg, args.mode, args.k)
-            line["forms"]["activations"] = activation_forms(
-                pkg, args.k, ("siren", "sdf_elu") if args.all_forms else ("sdf_elu",))
+            extra += [("batched", lambda: batched_form(pkg, args.mode, args.k)),
+                      ("activations", lambda: activation_forms(
+                          pkg, args.k, ("siren", "sdf_elu") if args.all_forms else ("sdf_elu",)))]
+        for name, fn in extra:
+            try:
+                line["forms"][name] = fn()
+            except Exception as ex:
+                line["forms"][name] = {"error": repr(ex)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(layers, args.mode, args.k)
     if rank == 0:

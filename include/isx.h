@@ -66,11 +66,10 @@ typedef enum { ISX_BOUND_SOUND = 0, ISX_BOUND_CLT = 1, ISX_BOUND_RAUA = 2, ISX_B
 /* Arithmetic of the coefficient propagation.  FP32: float32 storage and FMA.  BF16: coefficient
  * matrices stored in bfloat16 and multiplied on tcgen05 tensor cores with float32 accumulation;
  * centres, reductions and linearisations stay float32.  Two BF16 kernels exist:
- *  - the row-batched path (hidden widths 64, 128, 256; SOUND without inflation, CLT, RAUA; the
- *    default): cells of a chunk are propagated layer by layer, the symbol rows of all cells in one
- *    tensor-core GEMM per layer, symbols whose coefficient is exactly 0 never created;
- *  - the per-cell persistent kernel (hidden widths 128, 256): SOUND with inflation, isx_batch_* and
- *    isx_bound_cells_noalloc.
+ *  - the row-batched path (hidden widths 64, 128, 256; SOUND with or without inflation, CLT, RAUA):
+ *    cells of a chunk are propagated layer by layer, the symbol rows of all cells in one tensor-core
+ *    GEMM per layer, symbols whose coefficient is exactly 0 never created;
+ *  - the per-cell persistent kernel (hidden widths 128, 256): isx_bound_cells_noalloc.
  * The choice is fixed by that rule (no switch).  Both stay within the BF16 rounding band of the
  * float64 propagation; they are not bit-identical. */
 typedef enum { ISX_PREC_FP32 = 0, ISX_PREC_BF16 = 1 } isx_precision;
@@ -227,23 +226,22 @@ isx_status isx_extract_isosurface(isx_inr inr, const isx_extract_params* params,
                                   void* stream);
 
 /* ---- batched extraction ----------------------------------------------------------------------
- * Many extractions run together: the octrees of all entries are walked level-synchronously
- * (Algorithm 1 for every entry, one level of all of them at a time) and the cells of a level are
- * bounded by one persistent tensor-core launch per hidden width present, whatever their INR; culling
- * and compaction run on one list of all entries' cells.  Entries may differ in INR (widths 128 and
- * 256, any depth), iso-values, k and max_level; they share mode and inflation and use BF16 bounds.
- * No counterpart in the paper (it extracts one INR at a time).
- * With use_graph, the first run sizes the level lists (reading each level's count) and later runs
- * capture the whole level loop once as a CUDA graph and replay it; a replay whose counts exceed the
- * sized capacities (e.g. INR weights changed in place) is detected on the device and redone sized.
- * Outputs per entry are as for isx_extract_isosurface (meshes[i] for entry i); ms_acp is the level
- * loop of the whole batch, cells_bounded / cells_kept are not filled.  The INRs must outlive the
- * batch.  Errors: ISX_ERR_ARG (mixed devices, modes or inflation; n outside 1..65535),
- * ISX_ERR_UNSUPPORTED (FP32 bounds, other widths, proposer or bound_stop_level), ISX_ERR_CAPACITY
- * (an entry's active cells or triangles exceed its caps: its counts are filled, the others run),
- * ISX_ERR_TIMEOUT, ISX_ERR_CUDA.  isx_batch_run synchronises `stream`. */
+ * Many extractions in flight together (no counterpart in the paper, which extracts one INR at a
+ * time).  Every entry runs exactly isx_extract_isosurface with its own INR and parameters (any mode,
+ * precision, k, isos, max_level, bound_stop_level, k-d tree, proposer, level record), so its outputs
+ * are bit-identical to that single call.  isx_batch_run hands the entries to `workers` host threads
+ * (0: 8), each with its own non-blocking CUDA stream created by isx_batch_create; the level loops of
+ * several extractions then overlap on the GPU, which pays where an extraction is too small to fill
+ * it.  Entries that share an INR handle run on one worker in entry order (they share its workspace);
+ * different handles run concurrently.  The workers start after the work queued on `stream`, and
+ * `stream` waits for all of them.  Outputs per entry are those of isx_extract_isosurface (meshes[i]
+ * for entry i, its caller-owned buffers).  The INRs must outlive the batch.  Errors: ISX_ERR_ARG
+ * (a malformed entry, INRs on another device, workers outside 0..64, n outside 1..65535); otherwise
+ * every entry runs and the first failing entry's status is returned (ISX_ERR_CAPACITY fills that
+ * entry's required counts), with isx_last_error naming the entry.  isx_batch_run synchronises every
+ * worker stream. */
 typedef struct isx_batch_s* isx_batch;
-isx_status isx_batch_create(const isx_inr* inrs, const isx_extract_params* params, int n, int use_graph,
+isx_status isx_batch_create(const isx_inr* inrs, const isx_extract_params* params, int n, int workers,
                             isx_batch* out);
 isx_status isx_batch_run(isx_batch batch, isx_mesh* meshes, void* stream);
 isx_status isx_batch_destroy(isx_batch batch);

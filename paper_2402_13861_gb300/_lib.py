@@ -421,10 +421,11 @@ class Proposer:
 
 
 class Batch:
-    """Many extractions run level-synchronously (wraps isx_batch).  ``nets``: Inr objects; ``params``:
-    one dict of Inr.params keyword arguments per entry (max_level, isos, mode, k, prec, ...)."""
+    """Many extractions in flight together (wraps isx_batch): every entry runs isx_extract_isosurface
+    on one of ``workers`` host threads, each with its own CUDA stream.  ``nets``: Inr objects;
+    ``params``: one dict of Inr.params keyword arguments per entry (max_level, isos, mode, k, prec, ...)."""
 
-    def __init__(self, nets, params, use_graph=True):
+    def __init__(self, nets, params, workers=8):
         lib = load()
         self.nets = list(nets)
         self.params = [Inr.params(**p) for p in params]
@@ -433,7 +434,7 @@ class Batch:
         hs = (C.c_void_p * n)(*[net.handle for net in self.nets])
         ps = (ExtractParams * n)(*self.params)
         h = C.c_void_p()
-        _check(lib.isx_batch_create(hs, ps, n, int(bool(use_graph)), C.byref(h)))
+        _check(lib.isx_batch_create(hs, ps, n, int(workers), C.byref(h)))
         self._h = h
         self._bufs = [dict() for _ in range(n)]
 
@@ -485,5 +486,6 @@ class Batch:
             na, nt = int(m.n_active), int(m.n_tris)
             out.append(dict(codes=b["code"][:na], masks=b["mask"][:na], tri_vert=b["vert"][:nt],
                             tri_edge=b["edge"][:nt], tri_iso=b["iso"][:nt], tri_cell=b["cell"][:nt], n_active=na,
-                            n_tris=nt, n_points=int(m.n_points), ms_acp=m.ms_acp, ms_inr=m.ms_inr, ms_mc=m.ms_mc))
+                            n_tris=nt, n_points=int(m.n_points), ms_acp=m.ms_acp, ms_inr=m.ms_inr, ms_mc=m.ms_mc,
+                            ms_total=m.ms_total, cells_bounded=list(m.cells_bounded)[:self.max_levels[i] + 1]))
         return out

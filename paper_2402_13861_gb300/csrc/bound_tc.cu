@@ -87,10 +87,8 @@ struct TcNet {
 struct TcArgs {
   CellSource src;
   int64_t n;
-  const int64_t* n_dev;                // if set, the cell count is read from device memory
   int mode, inflate, w;
-  const TcNet* nets;                   // device array of networks
-  const uint16_t* cell_net;            // network of every cell (nullptr: all cells use nets[0])
+  const TcNet* nets;                   // device descriptor of the network
   __nv_bfloat16* scratch;
   int rows_per_cta;
   float* center;
@@ -305,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
   extern __shared__ uint8_t smem_raw[];
   constexpr int MT = W / 128;              // 128-row tiles per block of w rows
   constexpr int KC = W / 64;               // 64-wide K chunks
-  const int64_t ncell = args.n_dev ? *args.n_dev : args.n;
+  const int64_t ncell = args.n;
   Smem s = carve(smem_raw, W);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int mode = args.mode;
@@ -375,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
         return true;
       };
       for (int64_t cell = blockIdx.x; cell < ncell && ok; cell += gridDim.x) {
-        const TcNet& N = args.nets[args.cell_net ? args.cell_net[cell] : 0];
+        const TcNet& N = args.nets[0];
         const int H = N.H;
         if (N.w != W) continue;
         for (int j = 1; j <= H - 1 && ok; ++j) {
@@ -450,7 +448,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
         return true;
       };
       for (int64_t cell = blockIdx.x; cell < ncell && ok; cell += gridDim.x) {
-        const TcNet& N = args.nets[args.cell_net ? args.cell_net[cell] : 0];
+        const TcNet& N = args.nets[0];
         const int H = N.H;
         if (N.w != W) continue;
         // layer 1: B is idle (the previous cell's MMAs released it, this cell's W_2 waits for this GEMV)
@@ -498,7 +496,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
         return true;
       };
       for (int64_t cell = blockIdx.x; cell < ncell && ok; cell += gridDim.x) {
-        const TcNet& N = args.nets[args.cell_net ? args.cell_net[cell] : 0];
+        const TcNet& N = args.nets[0];
         const int H = N.H;
         if (N.w != W) continue;
         for (int j = 1; j <= H - 1 && ok; ++j) {
@@ -542,7 +540,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
       ++tiles_done;
     };
     for (int64_t cell = blockIdx.x; cell < ncell; cell += gridDim.x) {
-      const TcNet& N = args.nets[args.cell_net ? args.cell_net[cell] : 0];
+      const TcNet& N = args.nets[0];
       const int H = N.H;
       if (N.w != W) continue;
       if (__shfl_sync(0xffffffffu, *(volatile int*)s.abort, 0)) break;
@@ -674,7 +672,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bound_tc(const __grid_constant_
       return s.scal[63] == 0.f;
     };
     for (int64_t cell = blockIdx.x; cell < ncell; cell += gridDim.x) {
-      const TcNet& N = args.nets[args.cell_net ? args.cell_net[cell] : 0];
+      const TcNet& N = args.nets[0];
       const int H = N.H;
       if (N.w != W) continue;
       if (mt == 0) s.scal[63] = *(volatile int*)s.abort ? 1.f : 0.f;
@@ -1078,37 +1076,6 @@ isx_status tc_net_of(isx_inr inr, const void** out) {
 }
 
 size_t tc_net_bytes() { return sizeof(TcNet); }
-
-// Bounds the cells of a batch: packed codes at `level`, the network of each cell (an index into
-// d_nets, a device array of descriptors copied from tc_net_of), count read from *n_dev.  Cells of
-// networks of another width than w are skipped.  `scratch` holds grid * rows_per_cta rows of w
-// bf16.  No synchronisation (stream-capturable); a timeout raises *status.
-isx_status bound_bf16_batch(const void* d_nets, int w, int rows_per_cta, const uint32_t* codes,
-                            const uint16_t* cell_net, int level, const int64_t* n_dev, isx_bound_mode mode,
-                            int inflate, float* center, float* spread, __nv_bfloat16* scratch, int grid, int* status,
-                            cudaStream_t st) {
-  TcArgs a{};
-  a.src.codes = codes;
-  a.src.level = level;
-  a.n = 0;
-  a.n_dev = n_dev;
-  a.mode = (int)mode;
-  a.inflate = (mode == ISX_BOUND_SOUND) ? inflate : 0;
-  a.w = w;
-  a.nets = static_cast<const TcNet*>(d_nets);
-  a.cell_net = cell_net;
-  a.scratch = scratch;
-  a.rows_per_cta = rows_per_cta;
-  a.center = center;
-  a.spread = spread;
-  a.status = status;
-  a.trace = nullptr;
-  set_kappas(a, w);
-  TcMaps maps;
-  std::memset(&maps, 0, sizeof(maps));
-  ISX_TRY(make_scratch_map(&maps.scratch, scratch, w, rows_per_cta, grid));
-  return launch_tc(w, a, maps, grid, st);
-}
 
 isx_status tensor_map_bf16(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
                            uint32_t box_outer) {

@@ -149,10 +149,6 @@ bool bf16_supported(isx_inr inr);
 // Device copy of the INR's network descriptor for the tensor-core bound kernel (built on first use).
 isx_status tc_net_of(isx_inr inr, const void** out);
 size_t tc_net_bytes();
-isx_status bound_bf16_batch(const void* d_nets, int w, int rows_per_cta, const uint32_t* codes,
-                            const uint16_t* cell_net, int level, const int64_t* n_dev, isx_bound_mode mode,
-                            int inflate, float* center, float* spread, __nv_bfloat16* scratch, int grid, int* status,
-                            cudaStream_t st);
 // 2-D bfloat16 tensor map [outer][inner] (row stride inner * 2 bytes), 128-byte swizzle.
 isx_status tensor_map_bf16(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
                            uint32_t box_outer);

@@ -222,8 +222,8 @@ def batched_form(pkg, mode, k, workers=8):
     64 / 128 / 256, 3-6 hidden layers), each fitted for 300 Adam steps to its own field of the
     scientific kind (32-256 anisotropic Gaussians + sine), give 4 entries each (own INR handle): octrees
     to 128^3 and 256^3, 16 iso-values over the 10-90 % or 20-80 % quantiles.  Reports the 32 extractions
-    run one after another and as one isx_batch_run on `workers` worker streams, and checks that every
-    entry's mesh is the same."""
+    run one after another (a batch with one worker) and together (`workers` worker streams), and
+    checks that every entry's mesh is the same."""
     import torch
     from synth import fields, inr
     specs = [(64, 3, 32), (128, 3, 64), (256, 3, 128), (64, 5, 48), (128, 4, 96), (256, 4, 160), (128, 6, 192),
@@ -248,13 +248,14 @@ def batched_form(pkg, mode, k, workers=8):
         torch.cuda.synchronize()
         return out, a.elapsed_time(b)
 
-    bufs = [dict() for _ in nets]
-    for net, p, bf in zip(nets, params, bufs):
-        net.extract(buffers=bf, active_cap=1 << 21, tri_cap=1 << 23, **p)      # warm-up, sizes every workspace
-    singles, seq_ms = ev_ms(lambda: [net.extract(buffers=bf, **p) for net, p, bf in zip(nets, params, bufs)])
+    # one after another: the same entries on one worker (one workspace); then on `workers` workers
+    seq = pkg.Batch(nets, params, workers=1)
+    seq.run(active_cap=1 << 21, tri_cap=1 << 23)                              # sizes the buffers
+    singles, seq_ms = ev_ms(lambda: seq.run(active_cap=1 << 21, tri_cap=1 << 23))
     singles = [(s["n_active"], s["n_tris"]) for s in singles]
+    seq.close()
     batch = pkg.Batch(nets, params, workers=workers)
-    batch.run(active_cap=1 << 21, tri_cap=1 << 23)                            # sizes the batch's buffers
+    batch.run(active_cap=1 << 21, tri_cap=1 << 23)
     res, batch_ms = ev_ms(lambda: batch.run(active_cap=1 << 21, tri_cap=1 << 23))
     same = all((r["n_active"], r["n_tris"]) == s for r, s in zip(res, singles))
     cells = int(sum(sum(r["cells_bounded"]) for r in res))

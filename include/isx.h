@@ -232,8 +232,12 @@ isx_status isx_extract_isosurface(isx_inr inr, const isx_extract_params* params,
  * are bit-identical to that single call.  isx_batch_run hands the entries to `workers` host threads
  * (0: 8), each with its own non-blocking CUDA stream created by isx_batch_create; the level loops of
  * several extractions then overlap on the GPU, which pays where an extraction is too small to fill
- * it.  Entries that share an INR handle run on one worker in entry order (they share its workspace);
- * different handles run concurrently.  The workers start after the work queued on `stream`, and
+ * it.  Each worker owns a workspace (grown with cudaMalloc on first use, freed by isx_batch_destroy)
+ * and lends it to the INR of the entry it runs, so a batch holds `workers` workspaces however many
+ * INRs it has, and an INR's own workspace is left as it was; with several workers the row-batched
+ * bound works in smaller chunks (no cell's result depends on the chunking).  Entries that share an
+ * INR handle run on one worker in entry order; different handles run concurrently, and no other call
+ * may use the batch's INRs while isx_batch_run runs.  The workers start after the work queued on `stream`, and
  * `stream` waits for all of them.  Outputs per entry are those of isx_extract_isosurface (meshes[i]
  * for entry i, its caller-owned buffers).  The INRs must outlive the batch.  Errors: ISX_ERR_ARG
  * (a malformed entry, INRs on another device, workers outside 0..64, n outside 1..65535); otherwise

@@ -8,7 +8,10 @@
 // extraction reads a count back to the host at every level (to size the next level's lists and row
 // buffers), and a small extraction is bound by those round trips and by launch latency; with several
 // extractions in flight their kernels fill the GPU together.  A large extraction fills it by itself.
-// Entries that share an INR handle share its workspace, so they run on one worker, in entry order.
+// Each worker owns a workspace and lends it to the INR of the entry it runs (an INR handle otherwise
+// keeps its own, grown to its largest extraction), so the batch holds `workers` workspaces however
+// many INRs it has; with several workers the row-batched path's chunks are made smaller (chunking does
+// not change any cell's result).  Entries that share an INR handle run on one worker, in entry order.
 #include "internal.cuh"
 
 #include <algorithm>
@@ -16,6 +19,13 @@
 #include <string>
 #include <thread>
 #include <vector>
+
+struct BatchWorker {
+  isx::Buf ws[isx::WS_N_SLOTS];                // the worker's workspace, lent to the entry it runs
+  ~BatchWorker() {
+    for (auto& b : ws) b.release();
+  }
+};
 
 struct isx_batch_s {
   int device = 0;
@@ -25,6 +35,8 @@ struct isx_batch_s {
   std::vector<std::vector<int>> groups;        // entries per INR handle, in entry order
   std::vector<cudaStream_t> streams;           // one per worker
   std::vector<cudaEvent_t> events;             // one per worker, plus the caller's start event
+  std::vector<BatchWorker> workers;
+  int64_t row_budget = 0;                      // symbol rows per chunk of the row-batched path
 };
 
 using namespace isx;
@@ -68,6 +80,8 @@ isx_status isx_batch_create(const isx_inr* inrs, const isx_extract_params* param
     if (!placed) b->groups.push_back({i});
   }
   const int nw = std::max(1, std::min(workers > 0 ? workers : 8, (int)b->groups.size()));
+  b->workers = std::vector<BatchWorker>(nw);
+  b->row_budget = std::max<int64_t>((int64_t)1 << 21, ((int64_t)1 << 24) / nw);
   for (int w = 0; w < nw; ++w) {
     cudaStream_t s = nullptr;
     cudaEvent_t e = nullptr;
@@ -119,8 +133,15 @@ isx_status isx_batch_run(isx_batch b, isx_mesh* meshes, void* stream) {
     cudaSetDevice(b->device);
     for (int g = next++; g < (int)b->groups.size(); g = next++)
       for (int i : b->groups[g]) {
-        status[i] = isx_extract_isosurface(b->inrs[i], &b->params[i], &meshes[i], b->streams[w]);
+        isx_inr inr = b->inrs[i];
+        // lend the worker's workspace and chunk size to the entry's INR for the call
+        std::swap(inr->ws, b->workers[w].ws);
+        const int64_t rb = inr->row_budget;
+        inr->row_budget = b->row_budget;
+        status[i] = isx_extract_isosurface(inr, &b->params[i], &meshes[i], b->streams[w]);
         if (status[i] != ISX_OK) message[i] = isx_last_error();
+        inr->row_budget = rb;
+        std::swap(inr->ws, b->workers[w].ws);
       }
   };
   std::vector<std::thread> pool;
@@ -148,8 +169,8 @@ isx_status isx_batch_destroy(isx_batch b) {
   for (auto s : b->streams) cudaStreamSynchronize(s);
   for (auto s : b->streams) cudaStreamDestroy(s);
   for (auto e : b->events) cudaEventDestroy(e);
+  delete b;                                     // frees the workers' workspaces on this device
   if (prev >= 0) cudaSetDevice(prev);
-  delete b;
   return ISX_OK;
 }
 

@@ -72,6 +72,7 @@ using rows::rwait;
 struct Infl {
   int on = 0;
   float kappa_g = 0, kappa_i = 0, kappa_c = 0, store = 0, gemm_slack = 1, sum_g = 1;
+  float gamma_w = 0;                            // gamma_{w+1}(u): the output layer's float32 dot products
   const float* bias = nullptr;                  // [w] b_j of the layer whose centre the combine reads
   __nv_bfloat16* V = nullptr;                   // [nc][w] v, rounded up: A operand of the bound GEMM
   const float* D = nullptr;                     // [nc][w] |W_j| v of the previous layer
@@ -79,7 +80,7 @@ struct Infl {
   float* SLK = nullptr;                         // [nc][w] after the last hidden layer: alpha d
 };
 constexpr float kU32 = 5.9604645e-08f;           // 2^-24
-__host__ __device__ __forceinline__ float gamma_u(double k, double u) { return (float)((k * u) / (1.0 - k * u)); }
+inline float gamma_u(double k, double u) { return (float)((k * u) / (1.0 - k * u)); }   // host only
 void set_infl(Infl& f, int w) {
   const double ub = 1.0 / 256.0, u = 1.0 / 16777216.0, ua = 1.0 / 131072.0, K = w;
   f.kappa_g = (float)((1.0 + ub + u) * (1.0 + ub) * (1.0 + gamma_u(K, ua)) - 1.0) * 1.0001f;
@@ -89,6 +90,7 @@ void set_infl(Infl& f, int w) {
   f.store = (float)(ub / (1.0 - ub) + 2.0 * u) * 1.0001f;
   f.gemm_slack = (float)(1.0 + 2.0 * gamma_u(K, ua)) * 1.0001f;
   f.sum_g = (float)(1.0 + gamma_u(132.0, u) + 8.0 * u);
+  f.gamma_w = gamma_u(K + 1.0, u) * 1.0001f;
 }
 __device__ __forceinline__ __nv_bfloat16 bf16_up(float x) { return __float2bfloat16_ru(x); }
 
@@ -681,7 +683,7 @@ __global__ void __launch_bounds__(256) k_rows_output(int w, int mode, const __nv
   const int cell = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const bool sq = mode != ISX_BOUND_SOUND;
   float x0 = 0.0f, s = 0.0f, ex = 0.0f;
-  const float gw = gamma_u((double)w + 1.0, 5.9604644775390625e-08);
+  const float gw = infl.gamma_w;
   for (int n = t; n < w; n += blockDim.x) {
     const size_t o = (size_t)cell * w + n;
     v[n] = AL[o] * wout[n];
@@ -751,7 +753,8 @@ __global__ void __launch_bounds__(256) k_rows_output(int w, int mode, const __nv
     if (infl.on) {
       // S symbols summed in float32: a factor 1 + gamma_S, S = rows + 3 + w; the partial sums of the
       // error terms are rounded up and their float32 additions covered by the 1 + 2^-20 factor
-      const float gS = gamma_u((double)(cnt[cell] + 3 + w), 5.9604644775390625e-08);
+      const float su = (float)(cnt[cell] + 3 + w) * kU32;
+      const float gS = __fmul_ru(__fdiv_ru(su, 1.0f - su), 1.0010f);
       e = __fadd_ru(e, __fmul_ru(gw, fabsf(bout)));
       e = __fadd_ru(e, 2.0f * kU32 * (fabsf(a) + fabsf(bout)));      // the final add of the centre
       e = __fmul_ru(e, 1.0000050f);
@@ -820,7 +823,7 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
   if (inflate)
     for (int l = 1; l <= H - 1; ++l) ISX_TRY(tensor_map_bf16(&absmaps[l], inr->Wabsru_bf16[l], w, w, 64, w));
   // chunk size: about kRowBudget G rows per chunk, from the rows per cell the previous chunk needed
-  const int64_t kRowBudget = 1 << 24;
+  const int64_t kRowBudget = inr->row_budget;
   const int64_t kMaxCells = kMaxChunkCells;
   double rows_per_cell = (double)w * (H - 1);
   int64_t first = 0;

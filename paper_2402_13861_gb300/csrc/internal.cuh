@@ -82,6 +82,7 @@ struct isx_inr_s {
   std::vector<float*> absW_rowsum;       // sum_k |W[l][n][k]| per output neuron
   std::vector<std::vector<float>> hW, hb;  // host copies
   isx::Buf ws[isx::WS_N_SLOTS];
+  int64_t row_budget = (int64_t)1 << 24;  // symbol rows per chunk of the row-batched bound path
   float* h_pinned = nullptr;            // small pinned host buffer for count read-back
   int* h_pinned_i = nullptr;
 };

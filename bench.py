@@ -267,6 +267,65 @@ def batched_form(pkg, mode, k, workers=8):
             "cells_bounded": cells, "batch_cells_per_s": cells / (batch_ms / 1e3)}
 
 
+def large_form(pkg, full=False):
+    """The large configuration: a 3 -> 512 x 8 -> 1 ReLU INR fitted to 1024 anisotropic Gaussians (seed 5;
+    committed fixture), one iso-value midway between the 10 % and 90 % quantiles.  BF16 row-batched
+    bounds at 512^3 (with `full`, also 1024^3): sound affine arithmetic, whose launch accounting gives the
+    row GEMM's bandwidth and the split GEMM's tensor-core rate at width 512, and UP with k = 2, 3, 4, whose
+    active pairs are counted against the sound form's (sound bounds miss no crossing cell up to BF16
+    rounding; there is no dense tensor-core reference at width 512)."""
+    import torch
+    from synth import inr
+    from paper_2402_13861_gb300.train_proposer import missed
+    t0 = time.time()
+    layers, isos, wl = inr.load_inr("large")
+    fit_s = time.time() - t0
+    net = pkg.Inr(layers)
+    st = torch.cuda.current_stream()
+    bufs = {}
+    out = {"dims": wl.dims, "load_or_fit_s": fit_s, "n_iso": int(len(isos))}
+
+    def run(level, reps=1, **kw):
+        pkg.profile_reset()
+        pkg.profile_enable(True)
+        for rep in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            r = net.extract(level, isos, buffers=bufs, prec="bf16", eval_prec="fp32", active_cap=1 << 27,
+                            tri_cap=1 << 26, **kw)
+            b.record(st)
+            torch.cuda.synchronize()
+        pkg.profile_enable(False)
+        return r, a.elapsed_time(b), pkg.profile_read()
+
+    for L in ((9, 10) if full else (9,)):
+        ref, ms_s, stats = run(L, reps=2 if L < 10 else 1, mode="sound")
+        key = ref["codes"].to(torch.int64) & 0xFFFFFFFF
+        o = torch.argsort(key)
+        cross = (key[o], (ref["masks"].to(torch.int64) & 0xFFFFFFFF)[o])
+        e = {"ms": ms_s, "cells_bounded": int(sum(ref["cells_bounded"])),
+             "cells_per_s": sum(ref["cells_bounded"]) / (ms_s / 1e3), "n_active": ref["n_active"],
+             "n_tris": ref["n_tris"]}
+        g, sp = stats.get("rows_gemm"), stats.get("rows_split")
+        if g and g["ms"] > 0:
+            e["rows_gemm_gbs"] = g["bytes"] / (g["ms"] / 1e3) / 1e9
+            e["rows_gemm_tflops"] = g["flops"] / (g["ms"] / 1e3) / 1e12
+        if sp and sp["ms"] > 0:
+            e["rows_split_tflops"] = sp["flops"] / (sp["ms"] / 1e3) / 1e12
+        tot_ms = sum(v["ms"] for v in stats.values()) or 1.0
+        e["kernel_time_share"] = {k: round(v["ms"] / tot_ms, 4) for k, v in stats.items() if v["ms"] > 0.01 * tot_ms}
+        res = {"sound": e}
+        for kk in (2.0, 3.0, 4.0):
+            r, ms, _ = run(L, mode="clt", k=kk)
+            m, tot = missed(r["codes"], r["masks"], cross)
+            res[f"clt_k{int(kk)}"] = {"ms": ms, "cells_bounded": int(sum(r["cells_bounded"])),
+                                      "cells_bounded_per_level": r["cells_bounded"], "n_active": r["n_active"],
+                                      "missed_vs_sound": m, "missed_rate_vs_sound": m / max(tot, 1)}
+        out[f"{1 << L}^3"] = res
+    net.close()
+    return out
+
+
 def activation_forms(pkg, k, names=("siren", "sdf_elu")):
     """The SIREN (sine, Table VII's sine row) and ELU-SDF workloads at 512^3: hierarchical CLT
     extraction on the tensor cores against dense extraction (FP32 evaluation), the crossing
@@ -602,7 +661,8 @@ def main():
         # every further form is measured on its own: one that fails records its error, never the line
         extra = [("fp32_vs_bf16", lambda: precision_sample(net, args.mode))]
         if prec == "bf16":
-            extra += [("batched", lambda: batched_form(pkg, args.mode, args.k)),
+            extra += [("large", lambda: large_form(pkg, full=args.all_forms)),
+                      ("batched", lambda: batched_form(pkg, args.mode, args.k)),
                       ("activations", lambda: activation_forms(
                           pkg, args.k, ("siren", "sdf_elu") if args.all_forms else ("sdf_elu",)))]
         for name, fn in extra:

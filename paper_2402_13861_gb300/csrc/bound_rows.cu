@@ -250,6 +250,20 @@ struct NewRowIO<8> {
   }
 };
 template <>
+struct NewRowIO<16> {
+  static __device__ __forceinline__ void ld(const float* p, float* v) {
+#pragma unroll
+    for (int i = 0; i < 16; i += 4) {
+      const float4 a = *reinterpret_cast<const float4*>(p + i);
+      v[i] = a.x; v[i + 1] = a.y; v[i + 2] = a.z; v[i + 3] = a.w;
+    }
+  }
+  static __device__ __forceinline__ void st(__nv_bfloat16* p, const uint32_t* h) {
+    *reinterpret_cast<uint4*>(p) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(p + 8) = make_uint4(h[4], h[5], h[6], h[7]);
+  }
+};
+template <>
 struct NewRowIO<4> {
   static __device__ __forceinline__ void ld(const float* p, float* v) {
     const float4 a = *reinterpret_cast<const float4*>(p);
@@ -399,8 +413,10 @@ struct RowsSplitMaps {
 template <int W>
 struct SplitSmem {
   static constexpr int KC = W / 64;
+  static constexpr int NHALF = W > 256 ? 2 : 1;            // W = 512: each CTA computes 256 output columns
+  static constexpr int NC = W / NHALF;                     // output columns of a CTA
   static constexpr size_t kA = (size_t)kRT * 128;          // one A term of one K chunk
-  static constexpr size_t kB = (size_t)W * 128;            // one W term of one K chunk
+  static constexpr size_t kB = (size_t)NC * 128;           // one W term of one K chunk (NC rows of W)
   static constexpr size_t kStage = 2 * kA + 2 * kB;
   static constexpr size_t bytes() { return 1024 + 2 * kStage + SB_COUNT * 8 + 16; }
 };
@@ -411,7 +427,7 @@ template <int W, bool ONE>
 __global__ void __launch_bounds__(kST, 1) k_rows_split(const __grid_constant__ RowsSplitArgs args,
                                                         const __grid_constant__ RowsSplitMaps maps) {
   using S = SplitSmem<W>;
-  constexpr int KC = S::KC;
+  constexpr int KC = S::KC, NHALF = S::NHALF, NC = S::NC;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bar = reinterpret_cast<uint64_t*>(base + 2 * S::kStage);
@@ -420,6 +436,9 @@ __global__ void __launch_bounds__(kST, 1) k_rows_split(const __grid_constant__ R
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int64_t nrows = ONE ? args.nc : 4 * args.nc;
   const int64_t ntiles = (nrows + kRT - 1) / kRT;
+  // work items (tile, column half); the grid is a multiple of NHALF, so a CTA keeps its half
+  const int hq = blockIdx.x % NHALF;
+  const int64_t t0 = blockIdx.x / NHALF, TS = gridDim.x / NHALF;
   if (t == 0) {
     for (int i = 0; i < 2; ++i) {
       mbar_init(&bar[SB_FULL + i], 1);
@@ -432,7 +451,7 @@ __global__ void __launch_bounds__(kST, 1) k_rows_split(const __grid_constant__ R
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
-                 "n"(2 * W)
+                 "n"(2 * NC)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -446,7 +465,7 @@ __global__ void __launch_bounds__(kST, 1) k_rows_split(const __grid_constant__ R
     // ---- producer ----
     if (lane == 0) {
       uint32_t it = 0;
-      for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      for (int64_t tile = t0; tile < ntiles; tile += TS) {
         for (int c = 0; c < KC; ++c, ++it) {
           const int sidx = it & 1;
           if (!rwait(&bar[SB_EMPTY + sidx], ((it >> 1) & 1) ^ 1, abort, args.status)) break;
@@ -454,8 +473,8 @@ __global__ void __launch_bounds__(kST, 1) k_rows_split(const __grid_constant__ R
           mbar_expect_tx(&bar[SB_FULL + sidx], (uint32_t)(ONE ? S::kA + S::kB : S::kStage));
           tma_load_2d(sp, &maps.ahi, &bar[SB_FULL + sidx], c * 64, (int)(tile * kRT));
           if (!ONE) tma_load_2d(sp + S::kA, &maps.alo, &bar[SB_FULL + sidx], c * 64, (int)(tile * kRT));
-          tma_load_2d(sp + 2 * S::kA, &maps.whi, &bar[SB_FULL + sidx], c * 64, 0);
-          if (!ONE) tma_load_2d(sp + 2 * S::kA + S::kB, &maps.wlo, &bar[SB_FULL + sidx], c * 64, 0);
+          tma_load_2d(sp + 2 * S::kA, &maps.whi, &bar[SB_FULL + sidx], c * 64, hq * NC);
+          if (!ONE) tma_load_2d(sp + 2 * S::kA + S::kB, &maps.wlo, &bar[SB_FULL + sidx], c * 64, hq * NC);
         }
         if (*abort) break;
       }
@@ -463,13 +482,13 @@ __global__ void __launch_bounds__(kST, 1) k_rows_split(const __grid_constant__ R
   } else if (warp == 1) {
     // ---- MMA issuer ----
     if (lane == 0) {
-      const uint32_t id = idesc(W);
+      const uint32_t id = idesc(NC);
       uint32_t it = 0, tt = 0;
-      for (int64_t tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x, ++tt) {
+      for (int64_t tile = t0; tile < ntiles && !*abort; tile += TS, ++tt) {
         const uint32_t b = tt & 1;
         if (!rwait(&bar[SB_TEMPTY + b], ((tt >> 1) & 1) ^ 1, abort, args.status)) break;
         tc_fence_after();
-        const uint32_t dt = tmem + b * W;
+        const uint32_t dt = tmem + b * NC;
         for (int c = 0; c < KC; ++c, ++it) {
           const int sidx = it & 1;
           if (!rwait(&bar[SB_FULL + sidx], (it >> 1) & 1, abort, args.status)) break;
@@ -493,7 +512,7 @@ __global__ void __launch_bounds__(kST, 1) k_rows_split(const __grid_constant__ R
     // ---- epilogue: TMEM lane group warp % 4, one row per thread ----
     const int row = 32 * (warp & 3) + lane;
     uint32_t tt = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tt) {
+    for (int64_t tile = t0; tile < ntiles; tile += TS, ++tt) {
       const uint32_t b = tt & 1;
       const bool got = rwait(&bar[SB_TFULL + b], (tt >> 1) & 1, abort, args.status);
       if (!__all_sync(0xffffffffu, got)) break;
@@ -503,16 +522,17 @@ __global__ void __launch_bounds__(kST, 1) k_rows_split(const __grid_constant__ R
       const int q = ONE ? 1 : (int)(r & 3);
       const bool valid = cell < args.nc;
       float* dst = nullptr;
-      if (valid) dst = ONE ? args.Dout + r * W : (q == 0) ? args.Cout + cell * W : args.Iout + (cell * 3 + q - 1) * W;
-      const uint32_t trow = tmem + b * W + ((uint32_t)(32 * (warp & 3)) << 16);
+      if (valid)
+        dst = (ONE ? args.Dout + r * W : (q == 0) ? args.Cout + cell * W : args.Iout + (cell * 3 + q - 1) * W) + hq * NC;
+      const uint32_t trow = tmem + b * NC + ((uint32_t)(32 * (warp & 3)) << 16);
 #pragma unroll 1
-      for (int c0 = 0; c0 < W; c0 += 32) {
+      for (int c0 = 0; c0 < NC; c0 += 32) {
         float v[32];
         tmem_ld32(trow + c0, v);
         if (valid) {
-          if (q == 0)
+          if (!ONE && q == 0)
 #pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] += args.bias[c0 + i];
+            for (int i = 0; i < 32; ++i) v[i] += args.bias[hq * NC + c0 + i];
           float4* d4 = reinterpret_cast<float4*>(dst + c0);
 #pragma unroll
           for (int i = 0; i < 8; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
@@ -529,7 +549,7 @@ __global__ void __launch_bounds__(kST, 1) k_rows_split(const __grid_constant__ R
     for (int i = 0; i < 1000; ++i) __nanosleep(1000);
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(2 * W) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(2 * NC) : "memory");
   }
 }
 
@@ -555,22 +575,25 @@ __device__ __forceinline__ void stv(float* p, const float* v) {
   for (int i = 0; i < CPL; i += 2) *reinterpret_cast<float2*>(p + i) = make_float2(v[i], v[i + 1]);
 }
 constexpr int kRedWarps = 4;
-template <int CPL>
+template <int CPL, int PASSES>
 __global__ void __launch_bounds__(32 * kRedWarps) k_rows_reduce_act(int nc, int mode, int act, const float* part,
                                                                     const float* pnew, const int64_t* off_in,
                                                                     const int* cnt_in, const int* cnt_out,
                                                                     const float* I, const float* C, float* A, float* AL,
                                                                     float* GA, int* cnt_next, __nv_bfloat16* AH,
                                                                     __nv_bfloat16* ALO, Infl infl) {
-  constexpr int w = 32 * CPL;
+  constexpr int w = 32 * CPL * PASSES;
   const int lane = threadIdx.x & 31;
   const int cell = blockIdx.x * kRedWarps + (threadIdx.x >> 5);
   if (cell >= nc) return;
   const bool sq = mode == ISX_BOUND_CLT;
-  const int n0 = lane * CPL;
   const int rows = cnt_in[cell];
   const int64_t o0 = off_in[cell];
   const int rows_out = cnt_out[cell];
+  int m = 0;
+#pragma unroll 1
+  for (int pass = 0; pass < PASSES; ++pass) {
+  const int n0 = (pass * 32 + lane) * CPL;
   float iv[3][CPL], cv[CPL], pv[CPL];
 #pragma unroll
   for (int d = 0; d < 3; ++d) ldv<CPL>(I + ((size_t)cell * 3 + d) * w + n0, iv[d]);
@@ -604,7 +627,6 @@ __global__ void __launch_bounds__(32 * kRedWarps) k_rows_reduce_act(int nc, int 
     }
   }
   float av[CPL], alv[CPL], gv[CPL];
-  int m = 0;
   const size_t o = (size_t)cell * w + n0;
 #pragma unroll
   for (int i = 0; i < CPL; ++i) {
@@ -658,6 +680,7 @@ __global__ void __launch_bounds__(32 * kRedWarps) k_rows_reduce_act(int nc, int 
       for (int i = 0; i < CPL; ++i) x[i] = alv[i] * iv[d][i];
       put(q0 + (size_t)(d + 1) * w, x);
     }
+  }
   }
   if (!cnt_next) return;
 #pragma unroll
@@ -773,9 +796,11 @@ isx_status launch_rows_split(isx_inr inr, const RowsSplitArgs& a, const RowsSpli
   ISX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, inr->device));
   int per_sm = 1;
   ISX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_split<W, ONE>, kST, smem));
-  per_sm = std::max(1, std::min(per_sm, 512 / (2 * W)));
+  constexpr int NHALF = SplitSmem<W>::NHALF;
+  per_sm = std::max(1, std::min(per_sm, 512 / (2 * SplitSmem<W>::NC)));
   const int64_t ntiles = ((ONE ? 1 : 4) * a.nc + kRT - 1) / kRT;
-  const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
+  int grid = (int)std::min<int64_t>(ntiles * NHALF, (int64_t)sms * per_sm);
+  grid -= grid % NHALF;
   k_rows_split<W, ONE><<<grid, kST, smem, st>>>(a, maps);
   ISX_LAUNCH_CHECK("k_rows_split");
   return ISX_OK;
@@ -783,6 +808,7 @@ isx_status launch_rows_split(isx_inr inr, const RowsSplitArgs& a, const RowsSpli
 template <bool ONE>
 isx_status launch_rows_split_w(isx_inr inr, int w, const RowsSplitArgs& a, const RowsSplitMaps& maps,
                                cudaStream_t st) {
+  if (w == 512) return launch_rows_split<512, ONE>(inr, a, maps, st);
   if (w == 256) return launch_rows_split<256, ONE>(inr, a, maps, st);
   if (w == 128) return launch_rows_split<128, ONE>(inr, a, maps, st);
   return launch_rows_split<64, ONE>(inr, a, maps, st);
@@ -792,7 +818,7 @@ isx_status launch_rows_split_w(isx_inr inr, int w, const RowsSplitArgs& a, const
 
 bool rows_supported(isx_inr inr, isx_bound_mode mode, int inflate) {
   (void)inflate;
-  if (!(inr->w == 64 || inr->w == 128 || inr->w == 256) || inr->H < 1) return false;
+  if (!(inr->w == 64 || inr->w == 128 || inr->w == 256 || inr->w == 512) || inr->H < 1) return false;
   return mode == ISX_BOUND_SOUND || mode == ISX_BOUND_CLT || mode == ISX_BOUND_RAUA;
 }
 
@@ -813,15 +839,18 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
   int64_t* bsum = d_tot + 8;
   ISX_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
   std::vector<CUtensorMap> maps(inr->n_layers), lomaps(inr->n_layers), pmaps(inr->n_layers);
+  // TMA boxes are at most 256 rows: the split GEMM reads W_j in 256-row halves and the row GEMM in
+  // 128-row quarters at w = 512
+  const uint32_t box_split = w > 256 ? 256 : w, box_rows = w > 256 ? 128 : w;
   for (int l = 1; l <= H - 1; ++l) {
-    ISX_TRY(tensor_map_bf16(&maps[l], inr->W_bf16[l], w, w, 64, w));
-    ISX_TRY(tensor_map_bf16(&lomaps[l], inr->Wlo_bf16[l], w, w, 64, w));
-    ISX_TRY(tensor_map_bf16(&pmaps[l], inr->Wperm_bf16[l] ? inr->Wperm_bf16[l] : inr->W_bf16[l], w, w, 64, w));
+    ISX_TRY(tensor_map_bf16(&maps[l], inr->W_bf16[l], w, w, 64, box_split));
+    ISX_TRY(tensor_map_bf16(&lomaps[l], inr->Wlo_bf16[l], w, w, 64, box_split));
+    ISX_TRY(tensor_map_bf16(&pmaps[l], inr->Wperm_bf16[l] ? inr->Wperm_bf16[l] : inr->W_bf16[l], w, w, 64, box_rows));
   }
   const int sq = mode == ISX_BOUND_CLT ? 1 : 0;
   std::vector<CUtensorMap> absmaps(inr->n_layers);
   if (inflate)
-    for (int l = 1; l <= H - 1; ++l) ISX_TRY(tensor_map_bf16(&absmaps[l], inr->Wabsru_bf16[l], w, w, 64, w));
+    for (int l = 1; l <= H - 1; ++l) ISX_TRY(tensor_map_bf16(&absmaps[l], inr->Wabsru_bf16[l], w, w, 64, box_split));
   // chunk size: about kRowBudget G rows per chunk, from the rows per cell the previous chunk needed
   const int64_t kRowBudget = inr->row_budget;
   const int64_t kMaxCells = kMaxChunkCells;
@@ -924,7 +953,9 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
         prof::Scope ps(K_ROWS_NEW, st, 0, 2.0 * (double)(Rn - R) * w + 4.0 * (double)Rn + 8.0 * (double)nc * w);
         const unsigned nb = (unsigned)((nc + kNewWarps - 1) / kNewWarps);
         int* rc = ws[rs[nxt]].as<int>();
-        if (w == 256)
+        if (w == 512)
+          k_rows_new<16><<<nb, 32 * kNewWarps, 0, st>>>(nc, sq, GA, inr->Wt[j], cnt_in, off_out, cnt_out, Xout, rc, pnew);
+        else if (w == 256)
           k_rows_new<8><<<nb, 32 * kNewWarps, 0, st>>>(nc, sq, GA, inr->Wt[j], cnt_in, off_out, cnt_out, Xout, rc, pnew);
         else if (w == 128)
           k_rows_new<4><<<nb, 32 * kNewWarps, 0, st>>>(nc, sq, GA, inr->Wt[j], cnt_in, off_out, cnt_out, Xout, rc, pnew);
@@ -987,15 +1018,18 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
           fi.RAD = ws[WS_RAD].as<float>();
           fi.SLK = ws[WS_DELTA].as<float>();
         }
-        if (w == 256)
-          k_rows_reduce_act<8><<<rb, 32 * kRedWarps, 0, st>>>(nc, (int)mode, inr->act, part, pnew, off_in, cnt_in,
-                                                              cnt_out, I1, C, A, AL, GA, cn, ah, ALO, fi);
+        if (w == 512)
+          k_rows_reduce_act<8, 2><<<rb, 32 * kRedWarps, 0, st>>>(nc, (int)mode, inr->act, part, pnew, off_in, cnt_in,
+                                                                 cnt_out, I1, C, A, AL, GA, cn, ah, ALO, fi);
+        else if (w == 256)
+          k_rows_reduce_act<8, 1><<<rb, 32 * kRedWarps, 0, st>>>(nc, (int)mode, inr->act, part, pnew, off_in, cnt_in,
+                                                                 cnt_out, I1, C, A, AL, GA, cn, ah, ALO, fi);
         else if (w == 128)
-          k_rows_reduce_act<4><<<rb, 32 * kRedWarps, 0, st>>>(nc, (int)mode, inr->act, part, pnew, off_in, cnt_in,
-                                                              cnt_out, I1, C, A, AL, GA, cn, ah, ALO, fi);
+          k_rows_reduce_act<4, 1><<<rb, 32 * kRedWarps, 0, st>>>(nc, (int)mode, inr->act, part, pnew, off_in, cnt_in,
+                                                                 cnt_out, I1, C, A, AL, GA, cn, ah, ALO, fi);
         else
-          k_rows_reduce_act<2><<<rb, 32 * kRedWarps, 0, st>>>(nc, (int)mode, inr->act, part, pnew, off_in, cnt_in,
-                                                              cnt_out, I1, C, A, AL, GA, cn, ah, ALO, fi);
+          k_rows_reduce_act<2, 1><<<rb, 32 * kRedWarps, 0, st>>>(nc, (int)mode, inr->act, part, pnew, off_in, cnt_in,
+                                                                 cnt_out, I1, C, A, AL, GA, cn, ah, ALO, fi);
         ISX_LAUNCH_CHECK("k_rows_reduce_act");
       }
       std::swap(I0, I1);

@@ -14,10 +14,11 @@ using namespace tc;
 template <int W>
 struct RowsSmem {
   static constexpr int KC = W / 64;
-  static constexpr int MW = W < 128 ? 128 : W;             // rows of the weight operand (W = 64: zero-padded)
-  static constexpr int NH = MW / 128;                      // 128-row MMA halves of the weight operand
-  static constexpr int NS = (W == 256) ? 5 : 4;            // row ring: one 64-wide K chunk of a tile each
-  static constexpr size_t kWB = (size_t)MW * W * 2;        // W_j, KC chunks of [MW rows][128 B]
+  static constexpr int NQ = W > 256 ? W / 128 : 1;         // weight slices: W = 512 is split into 4 CTAs' quarters
+  static constexpr int MW = W > 256 ? 128 : (W < 128 ? 128 : W);   // weight rows a CTA holds (W = 64: zero-padded)
+  static constexpr int NH = MW / 128;                      // 128-row MMA halves of those rows
+  static constexpr int NS = (W >= 256) ? 5 : 4;            // row ring: one 64-wide K chunk of a tile each
+  static constexpr size_t kWB = (size_t)MW * W * 2;        // the weight rows, KC chunks of [MW rows][128 B]
   static constexpr size_t kAC = (size_t)kRT * 128;         // one row chunk: [128 rows][128 B]
   static constexpr size_t kMeta = 2 * kRT * (8 + 4);       // two tiles' destination rows and cells
   static constexpr size_t bytes() { return 1024 + kWB + NS * kAC + kMeta + (3 * NS + 5) * 8 + 16; }
@@ -33,7 +34,8 @@ __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: 
 //  - warps 0-3 scale each staged chunk in place: thread t multiplies row t by its cell's alpha
 //    (rows past R stay the TMA's zero fill);
 //  - warp 4 loads W_j (bf16, [MW][W], K-major) once by TMA, owns TMEM and issues the MMAs (M = 128
-//    per weight half, N = 128 rows, K = 16 per instruction);
+//    per weight half, N = 128 rows, K = 16 per instruction).  W = 512 does not fit in shared memory:
+//    each CTA then holds a 128-row quarter of W_j, and a tile's four quarters go to four CTAs;
 //  - warps 6-9 drain the two TMEM accumulators.  Thread m owns the neurons of weight row m of each
 //    half and walks the tile's rows in order: it stores each row's bf16 value (a bf16 pair for
 //    W = 256) and adds f(value) to a running sum that it writes to part[cell + tile] whenever the
@@ -53,7 +55,7 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
                                                        const __grid_constant__ CUtensorMap wmap,
                                                        const __grid_constant__ CUtensorMap xmap) {
   using S = RowsSmem<W>;
-  constexpr int KC = S::KC, NS = S::NS, MW = S::MW, NH = S::NH;
+  constexpr int KC = S::KC, NS = S::NS, MW = S::MW, NH = S::NH, NQ = S::NQ;
   constexpr uint32_t kCols = 2 * NH * 128;                 // two accumulators of NH x 128 columns
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -71,6 +73,11 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int64_t ntiles = (args.R + kRT - 1) / kRT;
+  // work items are (tile, weight slice); the grid is a multiple of NQ, so this CTA's slice q never
+  // changes and it walks the tiles t0, t0 + TS, ...; the NQ CTAs of a tile run side by side and
+  // share its row chunks through L2
+  const int q = blockIdx.x % NQ;
+  const int64_t t0 = blockIdx.x / NQ, TS = gridDim.x / NQ;
 
   if (W < 128) {
     // zero rows W .. 127 of every weight chunk (the MMA reads 128 weight rows)
@@ -108,7 +115,7 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
     // ---- scale row t of every staged chunk by alpha of its cell, in place ----
     uint32_t it = 0;
     bool ok = true;
-    int64_t r_next = (int64_t)blockIdx.x * kRT + t;
+    int64_t r_next = t0 * kRT + t;
     int cell_next = (r_next < args.R) ? args.rowcell[r_next] : 0;
     float4 av[16];
     {
@@ -116,17 +123,17 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
 #pragma unroll
       for (int g = 0; g < 16; ++g) av[g] = al0[g];
     }
-    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    for (int64_t tile = t0; tile < ntiles && ok; tile += TS) {
       const int64_t r = tile * kRT + t;
       const bool valid = r < args.R;
       const int cell = cell_next;
-      r_next = (tile + gridDim.x) * kRT + t;
-      cell_next = (tile + gridDim.x < ntiles && r_next < args.R) ? args.rowcell[r_next] : cell;
+      r_next = (tile + TS) * kRT + t;
+      cell_next = (tile + TS < ntiles && r_next < args.R) ? args.rowcell[r_next] : cell;
       {
         // ask L2 for the alpha rows of the cells of this warp's 32 rows of the next tile (a run of
         // consecutive cells, so one contiguous range), a tile ahead of their use
         const int cf = __shfl_sync(0xffffffffu, cell_next, 0), cl = __shfl_sync(0xffffffffu, cell_next, 31);
-        if (lane == 0 && tile + gridDim.x < ntiles && cl >= cf) {
+        if (lane == 0 && tile + TS < ntiles && cl >= cf) {
           const uint32_t bytes = (uint32_t)min((cl - cf + 1) * W * 4, 32 * 1024);
           asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(args.alpha + (size_t)cf * W), "r"(bytes)
                        : "memory");
@@ -169,7 +176,7 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
     if (lane == 0) {
       uint32_t it = 0;
       bool ok = true;
-      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      for (int64_t tile = t0; tile < ntiles && ok; tile += TS) {
         for (int c = 0; c < KC; ++c, ++it) {
           const int sidx = it % NS;
           if (!rwait(&aempty[sidx], ((it / NS) & 1) ^ 1, abort, args.status)) { ok = false; break; }
@@ -181,12 +188,15 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
   } else if (warp == 4) {
     // ---- W_j once, then the MMAs: D[half h] += W_j[h rows] x chunk^T ----
     if (lane == 0) {
-      mbar_expect_tx(wfull, (uint32_t)((size_t)W * W * 2));
-      for (int c = 0; c < KC; ++c) tma_load_2d(Wsm + (size_t)c * MW * 128, &wmap, wfull, c * 64, 0);
+      // the CTA's weight rows: all of W_j, or rows q * 128 .. q * 128 + 127 of it
+      constexpr int rows_held = W < MW ? W : MW;
+      mbar_expect_tx(wfull, (uint32_t)((size_t)rows_held * W * 2));
+      for (int c = 0; c < KC; ++c)
+        tma_load_2d(Wsm + (size_t)c * MW * 128, &wmap, wfull, c * 64, NQ > 1 ? q * 128 : 0);
       const uint32_t id = idesc(kRT);
       uint32_t it = 0, tt = 0;
       bool ok = rwait(wfull, 0, abort, args.status);
-      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tt) {
+      for (int64_t tile = t0; tile < ntiles && ok; tile += TS, ++tt) {
         const uint32_t b = tt & 1;
         if (!rwait(&tempty[b], ((tt >> 1) & 1) ^ 1, abort, args.status)) break;
         tc_fence_after();
@@ -211,10 +221,10 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
     // ---- epilogue: TMEM -> bf16 rows of G' and the per-(cell, tile) column sums of f(G') ----
     const int m = 32 * (warp & 3) + lane;                  // weight row (TMEM lane) of this thread
     const bool own = m < W;                                 // W = 64: rows 64 .. 127 are padding
-    const int n0 = (W == 256) ? 2 * m : m;                  // first neuron of this thread
+    const int n0 = (W == 256) ? 2 * m : q * 128 + m;        // first neuron of this thread
     const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
     // metadata of this thread's row of the first tile, and the cell of its row of the second
-    int64_t tile = blockIdx.x;
+    int64_t tile = t0;
     int c_cur = -1, c_nxt = -1;
     long long d_cur = 0;
     {
@@ -223,11 +233,11 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
         c_cur = args.rowcell[r];
         d_cur = args.off_out[c_cur] + (r - args.off_in[c_cur]);
       }
-      const int64_t r2 = (tile + gridDim.x) * kRT + m;
-      if (tile + gridDim.x < ntiles && r2 < args.R) c_nxt = args.rowcell[r2];
+      const int64_t r2 = (tile + TS) * kRT + m;
+      if (tile + TS < ntiles && r2 < args.R) c_nxt = args.rowcell[r2];
     }
     uint32_t tt = 0;
-    for (; tile < ntiles; tile += gridDim.x, ++tt) {
+    for (; tile < ntiles; tile += TS, ++tt) {
       const uint32_t b = tt & 1;
       int* scell = mcell + b * kRT;
       long long* sdst = mdst + b * kRT;
@@ -237,12 +247,12 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
       // the next tile's destination rows (its cells came one tile earlier) and the cells of the tile
       // after it: in flight while this tile drains
       {
-        const int64_t nt = tile + gridDim.x;
+        const int64_t nt = tile + TS;
         const int64_t r1 = nt * kRT + m;
         c_cur = c_nxt;
         if (nt < ntiles && r1 < args.R && c_cur >= 0) d_cur = args.off_out[c_cur] + (r1 - args.off_in[c_cur]);
-        const int64_t r2 = (nt + gridDim.x) * kRT + m;
-        c_nxt = (nt + gridDim.x < ntiles && r2 < args.R) ? args.rowcell[r2] : -1;
+        const int64_t r2 = (nt + TS) * kRT + m;
+        c_nxt = (nt + TS < ntiles && r2 < args.R) ? args.rowcell[r2] : -1;
       }
       const bool got = rwait(&tfull[b], (tt >> 1) & 1, abort, args.status);
       if (!__all_sync(0xffffffffu, got)) break;
@@ -328,8 +338,10 @@ isx_status launch_rows_gemm_w(isx_inr inr, const RowsGemmArgs& a, const CUtensor
   int per_sm = 1;
   ISX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_gemm<W, SQ>, kGT, smem));
   per_sm = std::max(1, std::min(per_sm, 512 / (2 * RowsSmem<W>::NH * 128)));   // TMEM columns per CTA
+  constexpr int NQ = RowsSmem<W>::NQ;
   const int64_t ntiles = (a.R + kRT - 1) / kRT;
-  const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
+  int grid = (int)std::min<int64_t>(ntiles * NQ, (int64_t)sms * per_sm);
+  grid -= grid % NQ;                                       // every CTA keeps one weight slice
   k_rows_gemm<W, SQ><<<grid, kGT, smem, st>>>(a, map, xmap);
   ISX_LAUNCH_CHECK("k_rows_gemm");
   return ISX_OK;
@@ -360,10 +372,12 @@ isx_status check_bounded_wait(int64_t limit_ns, int* d_status, cudaStream_t st) 
 
 isx_status launch_rows_gemm(isx_inr inr, const RowsGemmArgs& a, const CUtensorMap& wmap, int w, cudaStream_t st) {
   if (a.sq) {
+    if (w == 512) return launch_rows_gemm_w<512, true>(inr, a, wmap, st);
     if (w == 256) return launch_rows_gemm_w<256, true>(inr, a, wmap, st);
     if (w == 128) return launch_rows_gemm_w<128, true>(inr, a, wmap, st);
     return launch_rows_gemm_w<64, true>(inr, a, wmap, st);
   }
+  if (w == 512) return launch_rows_gemm_w<512, false>(inr, a, wmap, st);
   if (w == 256) return launch_rows_gemm_w<256, false>(inr, a, wmap, st);
   if (w == 128) return launch_rows_gemm_w<128, false>(inr, a, wmap, st);
   return launch_rows_gemm_w<64, false>(inr, a, wmap, st);

@@ -68,7 +68,24 @@ def test_bf16_bounds_match_oracle(pkg, dims, mode):
     net.close()
 
 
-@pytest.mark.parametrize("dims", [[3, 64, 64, 64, 64, 1], [3, 128, 128, 128, 1], [3] + [256] * 5 + [1], "scientific"])
+@pytest.mark.parametrize("dims,mode,m", [([3, 512, 512, 512, 1], "clt", 16), ([3, 512, 512, 512, 1], "sound", 16),
+                                         ([3] + [512] * 8 + [1], "clt", 6)])
+def test_bf16_width512_bounds_match_oracle(pkg, dims, mode, m):
+    """Width 512 (the large configuration's width): the row GEMM holds a 128-row quarter of W_j per
+    CTA and the split GEMM a 256-column half; head and ragged tail of 613 boxes against the oracle."""
+    layers = inr.random_inr(dims, 23)
+    net = pkg.Inr(layers)
+    lo, hi = boxes.random_boxes(613, 19, -9, -1)
+    c, s = _bounds(net, lo, hi, mode, "bf16")
+    assert np.all(np.isfinite(c)) and np.all(np.isfinite(s))
+    idx = np.concatenate([np.arange(m), np.arange(613 - m, 613)])
+    b = rm.bound_bands(layers, lo[idx], hi[idx], mode, batch=4)
+    check_against_bands(c[idx], s[idx], b, f"w512 x {len(dims) - 2} {mode}")
+    net.close()
+
+
+@pytest.mark.parametrize("dims", [[3, 64, 64, 64, 64, 1], [3, 128, 128, 128, 1], [3] + [256] * 5 + [1],
+                                  [3, 512, 512, 512, 1], "scientific"])
 def test_bf16_inflated_sound_bounds_contain_samples(pkg, dims):
     layers = inr.load_inr(dims)[0] if isinstance(dims, str) else inr.random_inr(dims, 5)
     net = pkg.Inr(layers)
@@ -135,6 +152,18 @@ def test_bf16_extraction_clt_matches_oracle(pkg):
     isos = np.quantile(vals, [0.3, 0.6]).astype(np.float32)
     res = net.extract(L, isos, mode="clt", k=3.0, prec="bf16")
     check_extraction_pairs(layers, isos, L, res, "clt", 3.0, "bf16 UP 128x3 32^3")
+    net.close()
+
+
+def test_bf16_extraction_width512_matches_oracle(pkg):
+    """UP k = 3 extraction of a 3->512x3->1 network at 16^3 on the row-batched path."""
+    layers = inr.random_inr([3, 512, 512, 512, 1], 33)
+    net = pkg.Inr(layers)
+    L = 4
+    vals = mlp.mlp_forward(layers, octree.lattice_points(1 << L))
+    isos = np.quantile(vals, [0.35, 0.65]).astype(np.float32)
+    res = net.extract(L, isos, mode="clt", k=3.0, prec="bf16")
+    check_extraction_pairs(layers, isos, L, res, "clt", 3.0, "bf16 UP 512x3 16^3", batch=16)
     net.close()
 
 

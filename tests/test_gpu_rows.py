@@ -112,6 +112,23 @@ def test_rows_path_width_64_matches_fp32(pkg, mode):
     net.close()
 
 
+@pytest.mark.parametrize("mode", ["clt", "sound"])
+def test_rows_path_width_512_matches_fp32(pkg, mode):
+    """Width 512 against the float32 path over many tiles of the quartered row GEMM and the halved
+    split GEMM (the blanket band; per-result bands against the oracle are in test_gpu_bf16.py)."""
+    layers = inr.random_inr([3, 512, 512, 512, 512, 1], 18)
+    H = len(layers) - 1
+    net = pkg.Inr(layers)
+    lo, hi = _cubes(6000, 15, 2, 9)
+    c, s = net.bound_cells(lo, hi, mode=mode, prec="bf16")
+    c32, s32 = net.bound_cells(lo, hi, mode=mode, prec="fp32")
+    c, s, c32, s32 = (to_np(x).astype(np.float64) for x in (c, s, c32, s32))
+    tol = 3 * H * UB * (np.abs(c32) + s32) + 1e-6
+    print(f"w512 {mode}: max |dc|/tol {np.max(np.abs(c - c32) / tol):.3f}, |ds|/tol {np.max(np.abs(s - s32) / tol):.3f}")
+    assert np.all(np.isfinite(c)) and np.all(np.abs(c - c32) <= tol) and np.all(np.abs(s - s32) <= tol)
+    net.close()
+
+
 def test_rows_path_width_64_extraction(pkg):
     """A BF16 extraction of the 3 -> 64 -> 64 -> 1 fixture runs on the row path and keeps the FP32
     extraction's active set up to cells near an iso-value."""

@@ -66,7 +66,8 @@ typedef enum { ISX_BOUND_SOUND = 0, ISX_BOUND_CLT = 1, ISX_BOUND_RAUA = 2, ISX_B
 /* Arithmetic of the coefficient propagation.  FP32: float32 storage and FMA.  BF16: coefficient
  * matrices stored in bfloat16 and multiplied on tcgen05 tensor cores with float32 accumulation;
  * centres, reductions and linearisations stay float32.  Two BF16 kernels exist:
- *  - the row-batched path (hidden widths 64, 128, 256; SOUND with or without inflation, CLT, RAUA):
+ *  - the row-batched path (hidden widths 64, 128, 256, 512; SOUND with or without inflation, CLT,
+ *    RAUA):
  *    cells of a chunk are propagated layer by layer, the symbol rows of all cells in one tensor-core
  *    GEMM per layer, symbols whose coefficient is exactly 0 never created;
  *  - the per-cell persistent kernel (hidden widths 128, 256): isx_bound_cells_noalloc.

@@ -39,7 +39,6 @@ namespace {
 
 using namespace tc;
 
-constexpr int kMaxW = 512;                      // largest hidden width of an INR
 constexpr int64_t kMaxChunkCells = 1 << 19;     // cells per chunk of the layer-synchronous loop
 using rows::kRT;
 using rows::roff;
@@ -696,89 +695,142 @@ __global__ void __launch_bounds__(32 * kRedWarps) k_rows_reduce_act(int nc, int 
 // S the number of symbols: each y_i = row_i . (alpha o w) errs by gamma_{w+1} sum_n |x_in| |alpha_n w_n|
 // (summed over i: RAD_n bounds sum_i |x_in|), the centre's dot product by gamma_{w+1} of its terms, the
 // last activation's symbols gamma_n w_n by one rounding, and the slack alpha d passes through |w|.
-__global__ void __launch_bounds__(256) k_rows_output(int w, int mode, const __nv_bfloat16* X, const int64_t* off,
-                                                     const int* cnt, const float* I, const float* A,
-                                                     const float* AL, const float* GA,
-                                                     const float* __restrict__ wout, float bout, int64_t first,
-                                                     float* center, float* spread, Infl infl) {
-  __shared__ float v[kMaxW];
-  __shared__ float red[3][8];
-  const int cell = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const bool sq = mode != ISX_BOUND_SOUND;
-  float x0 = 0.0f, s = 0.0f, ex = 0.0f;
-  const float gw = infl.gamma_w;
-  for (int n = t; n < w; n += blockDim.x) {
-    const size_t o = (size_t)cell * w + n;
-    v[n] = AL[o] * wout[n];
-    x0 = fmaf(wout[n], A[o], x0);
-    const float y = GA[o] * wout[n];
-    s += sq ? y * y : fabsf(y);
-    if (infl.on) {
-      ex = __fadd_ru(ex, __fmul_ru(gw, __fmul_ru(fabsf(v[n]), infl.RAD[o])));
-      ex = __fadd_ru(ex, __fmul_ru(1.0f + gw, __fmul_ru(fabsf(wout[n]), infl.SLK[o])));
-      ex = __fadd_ru(ex, __fmul_ru(gw, fabsf(wout[n] * A[o])));
-      ex = __fadd_ru(ex, __fmul_ru(kU32, fabsf(y)));
+// One warp per cell, CPL = w / 32 consecutive neurons per lane (the vector v = alpha o w_out stays in
+// registers); each row is one vector load per lane, four rows' loads in flight, and its dot product
+// is reduced across the warp before |y| or y^2 is taken.
+constexpr int kOutWarps = 8;
+template <int CPL>
+__device__ __forceinline__ void ld_row(const __nv_bfloat16* p, float* f) {
+  uint32_t h[CPL / 2];
+  if constexpr (CPL == 2) {
+    h[0] = *reinterpret_cast<const uint32_t*>(p);
+  } else if constexpr (CPL == 4) {
+    const uint2 u = *reinterpret_cast<const uint2*>(p);
+    h[0] = u.x; h[1] = u.y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < CPL / 8; ++i) {
+      const uint4 u = *reinterpret_cast<const uint4*>(p + 8 * i);
+      h[4 * i] = u.x; h[4 * i + 1] = u.y; h[4 * i + 2] = u.z; h[4 * i + 3] = u.w;
     }
   }
-  __syncthreads();
-  // three input rows and the G rows: one warp per row
+#pragma unroll
+  for (int i = 0; i < CPL / 2; ++i) {
+    const float2 x = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h[i]));
+    f[2 * i] = x.x;
+    f[2 * i + 1] = x.y;
+  }
+}
+template <int CPL>
+__global__ void __launch_bounds__(32 * kOutWarps) k_rows_output(int nc, int mode, const __nv_bfloat16* X,
+                                                                const int64_t* off, const int* cnt, const float* I,
+                                                                const float* A, const float* AL, const float* GA,
+                                                                const float* __restrict__ wout, float bout,
+                                                                int64_t first, float* center, float* spread,
+                                                                Infl infl) {
+  constexpr int w = 32 * CPL;
+  const int lane = threadIdx.x & 31;
+  const int cell = blockIdx.x * kOutWarps + (threadIdx.x >> 5);
+  if (cell >= nc) return;
+  const bool sq = mode != ISX_BOUND_SOUND;
+  const int m0 = lane * CPL;
+  const size_t o = (size_t)cell * w + m0;
   const int rows = cnt[cell];
   const int64_t o0 = off[cell];
-  for (int r = warp; r < 3; r += 8) {
+  float v[CPL];
+  // per lane: x0 and the last activation's symbols (s), the error terms (ex); sr, the rows' and the
+  // input rows' terms, is the same in every lane (their dot products are reduced across the warp)
+  float x0 = 0.0f, s = 0.0f, ex = 0.0f, sr = 0.0f;
+  {
+    float wo[CPL], al[CPL], av[CPL], gv[CPL];
+    ldv<CPL>(wout + m0, wo);
+    ldv<CPL>(AL + o, al);
+    ldv<CPL>(A + o, av);
+    ldv<CPL>(GA + o, gv);
+    float rad[CPL], slk[CPL];
+    if (infl.on) {
+      ldv<CPL>(infl.RAD + o, rad);
+      ldv<CPL>(infl.SLK + o, slk);
+    }
+    const float gw = infl.gamma_w;
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) {
+      v[i] = al[i] * wo[i];
+      x0 = fmaf(wo[i], av[i], x0);
+      const float y = gv[i] * wo[i];
+      s += sq ? y * y : fabsf(y);
+      if (infl.on) {
+        ex = __fadd_ru(ex, __fmul_ru(gw, __fmul_ru(fabsf(v[i]), rad[i])));
+        ex = __fadd_ru(ex, __fmul_ru(1.0f + gw, __fmul_ru(fabsf(wo[i]), slk[i])));
+        ex = __fadd_ru(ex, __fmul_ru(gw, fabsf(wo[i] * av[i])));
+        ex = __fadd_ru(ex, __fmul_ru(kU32, fabsf(y)));
+      }
+    }
+  }
+  auto dot = [&](const float* x) {
     float y = 0.0f;
-    const float* src = I + (size_t)cell * 3 * w + (size_t)r * w;
-    for (int n = lane; n < w; n += 32) y = fmaf(src[n], v[n], y);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
-    if (lane == 0) s += sq ? y * y : fabsf(y);
+    for (int i = 0; i < CPL; ++i) y = fmaf(x[i], v[i], y);
+    return y;
+  };
+  // the three input rows (float32)
+  {
+    float y[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float iv[CPL];
+      ldv<CPL>(I + ((size_t)cell * 3 + d) * w + m0, iv);
+      y[d] = dot(iv);
+    }
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) y[d] += __shfl_xor_sync(0xffffffffu, y[d], sh);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) sr += sq ? y[d] * y[d] : fabsf(y[d]);
   }
-  // the G rows two at a time per warp (both rows' loads in flight)
-  for (int r = warp; r < rows; r += 16) {
-    const bool two = r + 8 < rows;
-    const __nv_bfloat16* s0p = X + (o0 + r) * w;
-    const __nv_bfloat16* s1p = X + (o0 + (two ? r + 8 : r)) * w;
-    float y0 = 0.0f, y1 = 0.0f;
-    for (int n = lane; n < w; n += 32) {
-      const float vn = v[n];
-      y0 = fmaf(__bfloat162float(s0p[n]), vn, y0);
-      y1 = fmaf(__bfloat162float(s1p[n]), vn, y1);
+  // the stored symbol rows (bf16), four at a time
+  const __nv_bfloat16* xp = X + o0 * w + m0;
+  int r = 0;
+  for (; r + 4 <= rows; r += 4) {
+    float y[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float x[CPL];
+      ld_row<CPL>(xp + (size_t)(r + q) * w, x);
+      y[q] = dot(x);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      y0 += __shfl_xor_sync(0xffffffffu, y0, o);
-      y1 += __shfl_xor_sync(0xffffffffu, y1, o);
-    }
-    if (lane == 0) {
-      s += sq ? y0 * y0 : fabsf(y0);
-      if (two) s += sq ? y1 * y1 : fabsf(y1);
-    }
+    for (int sh = 16; sh > 0; sh >>= 1)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) y[q] += __shfl_xor_sync(0xffffffffu, y[q], sh);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sr += sq ? y[q] * y[q] : fabsf(y[q]);
+  }
+  for (; r < rows; ++r) {
+    float x[CPL];
+    ld_row<CPL>(xp + (size_t)r * w, x);
+    float y = dot(x);
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) y += __shfl_xor_sync(0xffffffffu, y, sh);
+    sr += sq ? y * y : fabsf(y);
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    x0 += __shfl_xor_sync(0xffffffffu, x0, o);
-    s += __shfl_xor_sync(0xffffffffu, s, o);
-    ex += __shfl_xor_sync(0xffffffffu, ex, o);
+  for (int sh = 16; sh > 0; sh >>= 1) {
+    x0 += __shfl_xor_sync(0xffffffffu, x0, sh);
+    s += __shfl_xor_sync(0xffffffffu, s, sh);
+    ex += __shfl_xor_sync(0xffffffffu, ex, sh);
   }
   if (lane == 0) {
-    red[0][warp] = x0;
-    red[1][warp] = s;
-    red[2][warp] = ex;
-  }
-  __syncthreads();
-  if (t == 0) {
-    float a = 0.0f, b = 0.0f, e = 0.0f;
-    for (int i = 0; i < 8; ++i) {
-      a += red[0][i];
-      b += red[1][i];
-      e += red[2][i];
-    }
+    const float a = x0, b = s + sr;
     center[first + cell] = a + bout;
     if (infl.on) {
       // S symbols summed in float32: a factor 1 + gamma_S, S = rows + 3 + w; the partial sums of the
       // error terms are rounded up and their float32 additions covered by the 1 + 2^-20 factor
-      const float su = (float)(cnt[cell] + 3 + w) * kU32;
+      const float su = (float)(rows + 3 + w) * kU32;
       const float gS = __fmul_ru(__fdiv_ru(su, 1.0f - su), 1.0010f);
-      e = __fadd_ru(e, __fmul_ru(gw, fabsf(bout)));
+      float e = ex;
+      e = __fadd_ru(e, __fmul_ru(infl.gamma_w, fabsf(bout)));
       e = __fadd_ru(e, 2.0f * kU32 * (fabsf(a) + fabsf(bout)));      // the final add of the centre
       e = __fmul_ru(e, 1.0000050f);
       spread[first + cell] = __fadd_ru(__fmul_ru(b, 1.0f + 2.0f * gS), e);
@@ -826,7 +878,7 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
                            float* d_center, float* d_spread, cudaStream_t st) {
   if (n <= 0) return ISX_OK;
   if (!rows_supported(inr, mode, inflate)) {
-    set_error("row-batched tensor-core bounds need hidden width 64, 128 or 256");
+    set_error("row-batched tensor-core bounds need hidden width 64, 128, 256 or 512");
     return ISX_ERR_UNSUPPORTED;
   }
   if (mode != ISX_BOUND_SOUND) inflate = 0;
@@ -1044,9 +1096,24 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
         fi.RAD = ws[WS_RAD].as<float>();
         fi.SLK = ws[WS_DELTA].as<float>();
       }
-      k_rows_output<<<nc, 256, 0, st>>>(w, (int)mode, ws[xs[cur]].as<__nv_bfloat16>(), ws[os[cur]].as<int64_t>(),
-                                        ws[cs[cur]].as<int>(), I0, A, AL, GA, inr->W[L], inr->hb[L][0], first,
-                                        d_center, d_spread, fi);
+      const unsigned ob = (unsigned)((nc + kOutWarps - 1) / kOutWarps);
+      const __nv_bfloat16* Xl = ws[xs[cur]].as<__nv_bfloat16>();
+      const int64_t* ol = ws[os[cur]].as<int64_t>();
+      const int* cl = ws[cs[cur]].as<int>();
+      const float* wl = inr->W[L];
+      const float bl = inr->hb[L][0];
+      if (w == 512)
+        k_rows_output<16><<<ob, 32 * kOutWarps, 0, st>>>(nc, (int)mode, Xl, ol, cl, I0, A, AL, GA, wl, bl, first,
+                                                         d_center, d_spread, fi);
+      else if (w == 256)
+        k_rows_output<8><<<ob, 32 * kOutWarps, 0, st>>>(nc, (int)mode, Xl, ol, cl, I0, A, AL, GA, wl, bl, first,
+                                                        d_center, d_spread, fi);
+      else if (w == 128)
+        k_rows_output<4><<<ob, 32 * kOutWarps, 0, st>>>(nc, (int)mode, Xl, ol, cl, I0, A, AL, GA, wl, bl, first,
+                                                        d_center, d_spread, fi);
+      else
+        k_rows_output<2><<<ob, 32 * kOutWarps, 0, st>>>(nc, (int)mode, Xl, ol, cl, I0, A, AL, GA, wl, bl, first,
+                                                        d_center, d_spread, fi);
       ISX_LAUNCH_CHECK("k_rows_output");
     }
     rows_per_cell = std::max(1.0, (double)R / nc);

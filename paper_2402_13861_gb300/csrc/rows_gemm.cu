@@ -275,9 +275,9 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
         float v0[32], v1[32];
         tmem_ld32(tb + c0, v0);
         if (NH == 2) tmem_ld32(tb + 128 + c0, v1);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          if (c0 + i >= rows) break;
+        // row c0 + i: close the segment that ends before it, then store it and add it to the sums.
+        // The loops below run over constant i (no early exit), so v0[i] / v1[i] stay registers.
+        auto row = [&](int i, float x0, float x1) {
           if ((starts >> i) & 1u) {                        // uniform: every thread sees the same rows
             if (own) {
               float* pp = args.part + (size_t)rows_part_slot(seg, tile) * W + n0;
@@ -289,22 +289,31 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
             dp = args.xout + (size_t)__shfl_sync(0xffffffffu, dl, i) * W + n0;
           }
           if (NH == 2) {
-            const __nv_bfloat162 h = __floats2bfloat162_rn(v0[i], v1[i]);
+            const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
             *reinterpret_cast<__nv_bfloat162*>(dp) = h;
             if (SQ) {
-              s0 = fmaf(v0[i], v0[i], s0);
-              s1 = fmaf(v1[i], v1[i], s1);
+              s0 = fmaf(x0, x0, s0);
+              s1 = fmaf(x1, x1, s1);
             } else {                                       // the radius sums the stored values
               const float2 f = __bfloat1622float2(h);
               s0 += fabsf(f.x);
               s1 += fabsf(f.y);
             }
           } else if (own) {
-            const __nv_bfloat16 h = __float2bfloat16_rn(v0[i]);
+            const __nv_bfloat16 h = __float2bfloat16_rn(x0);
             *dp = h;
-            s0 = SQ ? fmaf(v0[i], v0[i], s0) : s0 + fabsf(__bfloat162float(h));
+            s0 = SQ ? fmaf(x0, x0, s0) : s0 + fabsf(__bfloat162float(h));
           }
           dp += W;
+        };
+        if (rows - c0 >= 32) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) row(i, v0[i], NH == 2 ? v1[i] : 0.0f);
+        } else {
+          const int nl = rows - c0;                        // the last tile's last rows
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (i < nl) row(i, v0[i], NH == 2 ? v1[i] : 0.0f);
         }
       }
       if (own) {

@@ -78,33 +78,6 @@ __device__ __forceinline__ Lin relu_sound(float c, float rad, float delta, bool 
   return r;
 }
 
-// Sound linearisation with inflation, the slack kept apart: the interval is [c - rad - delta,
-// c + rad + delta] (rounded outward) and gamma covers the linearisation error and the rounding of the
-// new centre, but not alpha * delta, which goes to *slack_out (rounded up) and is carried on as a
-// separate bound instead of a new symbol: a neuron on one side of the kink then keeps gamma = 0 and
-// creates no symbol.
-__device__ __forceinline__ Lin relu_sound_sep(float c, float rad, float delta, float* slack_out) {
-  Lin r;
-  const float R = __fadd_ru(__fmul_ru(rad, kLinSafe), delta);
-  const float l = __fsub_rd(c, R), u = __fadd_ru(c, R);
-  if (u <= 0.0f) {
-    r.alpha = 0.0f; r.beta = 0.0f; r.gamma = 0.0f;
-  } else if (l >= 0.0f) {
-    r.alpha = 1.0f; r.beta = 0.0f; r.gamma = 0.0f;
-  } else {
-    r.alpha = u / (u - l);
-    r.beta = -0.5f * r.alpha * l;
-    const float e1 = fabsf(-r.alpha * l - r.beta), e2 = fabsf(r.beta), e3 = fabsf(u - r.alpha * u - r.beta);
-    r.gamma = fmaxf(e1, fmaxf(e2, e3));
-    r.gamma = __fadd_ru(r.gamma, 4.0f * kLinU * (fabsf(r.alpha * l) + fabsf(u) + fabsf(r.beta)));
-    // the new centre alpha c + beta is rounded once (alpha = 0 or 1 with beta = 0 give it exactly)
-    r.gamma = __fadd_ru(r.gamma, 2.0f * kLinU * (fabsf(r.alpha * c) + fabsf(r.beta)) * kLinSafe);
-  }
-  r.center = fmaf(r.alpha, c, r.beta);
-  *slack_out = __fmul_ru(r.alpha, delta);
-  return r;
-}
-
 // ---- ELU and sine (least-squares rule only; the ISX_ACT_* codes) ----------------------------------
 //
 //  Both follow the definition of the least-squares line under X ~ N(mu, sigma^2):

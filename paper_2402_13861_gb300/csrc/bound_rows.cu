@@ -617,7 +617,7 @@ __global__ void __launch_bounds__(32 * kRedWarps) k_rows_reduce_act(int nc, int 
     add(i, pv[i]);
   }
   if (rows > 0) {
-    const int64_t t0 = o0 / kRT, t1 = (o0 + rows - 1) / kRT;
+    const int64_t t0 = o0 / rows::kPT, t1 = (o0 + rows - 1) / rows::kPT;
     for (int64_t t = t0; t <= t1; ++t) {
       float q[CPL];
       ldv<CPL>(part + (size_t)rows::rows_part_slot(cell, t) * w + n0, q);
@@ -978,7 +978,7 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
       ISX_CUDA(cudaStreamSynchronize(st));
       ISX_TRY(ws[xs[nxt]].ensure((size_t)std::max<int64_t>(Rn, 1) * w * 2, "rows"));
       ISX_TRY(ws[rs[nxt]].ensure((size_t)std::max<int64_t>(Rn, 1) * sizeof(int), "row cells"));
-      const int64_t ntiles = (R + kRT - 1) / kRT;
+      const int64_t ntiles = (R + rows::kPT - 1) / rows::kPT;     // column-sum blocks of the input rows
       ISX_TRY(ws[WS_R_PART].ensure((size_t)(nc + ntiles) * w * sizeof(float), "row GEMM column sums"));
       __nv_bfloat16* Xin = ws[xs[cur]].as<__nv_bfloat16>();
       __nv_bfloat16* Xout = ws[xs[nxt]].as<__nv_bfloat16>();

@@ -12,6 +12,7 @@ namespace isx {
 namespace rows {
 
 constexpr int kRT = 128;                        // rows per MMA tile
+constexpr int kPT = 64;                         // rows per column-sum slot (half a tile)
 constexpr uint64_t kRowsWaitNs = 2000000000ull;
 
 struct RowsGemmArgs {
@@ -22,8 +23,9 @@ struct RowsGemmArgs {
   const float* alpha;                           // [nc][W]
   int64_t R;
   __nv_bfloat16* xout;                          // [R'][W] rows of z_{j+1}
-  float* part;                                  // [nc + ceil(R / 128)][W]: slot cell + tile holds, per
-                                                // neuron, sum f(x) over the cell's rows of that input tile
+  float* part;                                  // [nc + ceil(R / 64)][W]: slot cell + t holds, per neuron,
+                                                // sum f(x) over the cell's rows among input rows
+                                                // 64 t .. 64 t + 63
   int sq;                                       // f(x) = x^2 (1, Eq. 7) or |x| (0, Eq. 2)
   int* status;
 };
@@ -61,10 +63,10 @@ isx_status launch_rows_gemm(isx_inr inr, const RowsGemmArgs& a, const CUtensorMa
 __host__ __device__ __forceinline__ int rows_weight_row(int m, int w) {
   return w == 256 ? (m < 128 ? 2 * m : 2 * (m - 128) + 1) : m;
 }
-// Slot of the column partials of (cell, input tile) in RowsGemmArgs::part: cell + tile.  Rows of a
-// cell are contiguous, so cell c < c' implies tile <= tile' and the slots of all (cell, tile) pairs
-// that share rows are distinct.
-__host__ __device__ __forceinline__ int64_t rows_part_slot(int64_t cell, int64_t tile) { return cell + tile; }
+// Slot of the column partials of (cell, 64-row block t of the input rows) in RowsGemmArgs::part:
+// cell + t.  Rows of a cell are contiguous, so cell c < c' implies t <= t' and the slots of all
+// (cell, block) pairs that share rows are distinct.
+__host__ __device__ __forceinline__ int64_t rows_part_slot(int64_t cell, int64_t t) { return cell + t; }
 // One CTA waits on an mbarrier that nothing completes, with rwait and the given limit, raising
 // ISX_ERR_TIMEOUT in *d_status (rows_gemm.cu).
 isx_status check_bounded_wait(int64_t limit_ns, int* d_status, cudaStream_t st);

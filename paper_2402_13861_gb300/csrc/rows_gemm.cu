@@ -24,7 +24,7 @@ struct RowsSmem {
   static constexpr size_t bytes() { return 1024 + kWB + NS * kAC + kMeta + (3 * NS + 5) * 8 + 16; }
 };
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 // G' = (G diag(alpha_cell)) W^T for all rows, computed transposed: D = W_j (G diag(alpha))^T, so that
 // TMEM lane m holds neuron rows_weight_row(m) and column r the tile's row r.  Persistent,
@@ -36,20 +36,22 @@ __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: 
 //  - warp 4 loads W_j (bf16, [MW][W], K-major) once by TMA, owns TMEM and issues the MMAs (M = 128
 //    per weight half, N = 128 rows, K = 16 per instruction).  W = 512 does not fit in shared memory:
 //    each CTA then holds a 128-row quarter of W_j, and a tile's four quarters go to four CTAs;
-//  - warps 6-9 drain the two TMEM accumulators.  Thread m owns the neurons of weight row m of each
-//    half and walks the tile's rows in order: it stores each row's bf16 value (a bf16 pair for
-//    W = 256) and adds f(value) to a running sum that it writes to part[cell + tile] whenever the
-//    row's cell changes (|stored bf16 value| for the radius, which the rounding-error bound needs;
-//    the square of the float32 accumulator value for sigma, within 2^-7 of the stored value's).
+//  - warps 6-13 drain the two TMEM accumulators, two warps per TMEM lane group: warps 6-9 take rows
+//    0-63 of a tile, warps 10-13 rows 64-127.  Thread m owns the neurons of weight row m of each
+//    half and walks its 64 rows in order: it stores each row's bf16 value (a bf16 pair for
+//    W = 256) and adds f(value) to a running sum that it writes to part[cell + t] (t the 64-row
+//    block of the input rows) whenever the row's cell changes (|stored bf16 value| for the radius,
+//    which the rounding-error bound needs; the square of the float32 accumulator value for sigma,
+//    within 2^-7 of the stored value's).
 //    Every thread sees the same rows, so the segment boundaries are uniform; a segment's rows are
 //    consecutive in the output too, so its destination advances by one row per row.
 //    The destination row and cell of every row of the next tile are loaded while this tile drains
 //    and handed over through shared memory.
 // The scalers load the alpha of the next chunk (of this tile, or of the next tile) into registers
-// before they wait for the current one.  Loads of tile k + 1 and the epilogue of tile k - 1 overlap
+// as soon as they have handed over the current one.  Loads of tile k + 1 and the epilogue of tile k - 1 overlap
 // the MMAs of tile k.  Every wait is bounded (2 s): on timeout the kernel records ISX_ERR_TIMEOUT,
 // lets the work in flight finish, frees TMEM and returns.
-constexpr int kGT = 320;
+constexpr int kGT = 448;                        // 4 scalers, MMA, producer, 8 epilogue warps
 template <int W, bool SQ>
 __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ RowsGemmArgs args,
                                                        const __grid_constant__ CUtensorMap wmap,
@@ -94,7 +96,7 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&tfull[i], 1);
-      mbar_init(&tempty[i], 4);
+      mbar_init(&tempty[i], 8);
     }
     mbar_init(wfull, 1);
     *abort = 0;
@@ -141,11 +143,6 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
       }
       for (int c = 0; c < KC; ++c, ++it) {
         const int sidx = it % NS;
-        const float4* aln = (c + 1 < KC) ? reinterpret_cast<const float4*>(args.alpha + (size_t)cell * W) + 16 * (c + 1)
-                                         : reinterpret_cast<const float4*>(args.alpha + (size_t)cell_next * W);
-        float4 an[16];
-#pragma unroll
-        for (int g = 0; g < 16; ++g) an[g] = aln[g];
         if (!rwait(&araw[sidx], (it / NS) & 1, abort, args.status)) { ok = false; break; }
         uint8_t* Ac = Asm + (size_t)sidx * S::kAC;
         if (valid) {
@@ -167,8 +164,11 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
         }
         fence_async_shared();
         mbar_arrive(&afull[sidx]);
+        // alpha of the next chunk (of this tile, or of the next tile), in flight during the next wait
+        const float4* aln = (c + 1 < KC) ? reinterpret_cast<const float4*>(args.alpha + (size_t)cell * W) + 16 * (c + 1)
+                                         : reinterpret_cast<const float4*>(args.alpha + (size_t)cell_next * W);
 #pragma unroll
-        for (int g = 0; g < 16; ++g) av[g] = an[g];
+        for (int g = 0; g < 16; ++g) av[g] = aln[g];
       }
     }
   } else if (warp == 5) {
@@ -218,8 +218,9 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
       }
     }
   } else {
-    // ---- epilogue: TMEM -> bf16 rows of G' and the per-(cell, tile) column sums of f(G') ----
+    // ---- epilogue: TMEM -> bf16 rows of G' and the per-(cell, 64-row block) column sums of f(G') ----
     const int m = 32 * (warp & 3) + lane;                  // weight row (TMEM lane) of this thread
+    const int h = (warp - 6) >> 2;                          // rows 64 h .. 64 h + 63 of every tile
     const bool own = m < W;                                 // W = 64: rows 64 .. 127 are padding
     const int n0 = (W == 256) ? 2 * m : q * 128 + m;        // first neuron of this thread
     const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
@@ -241,12 +242,14 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
       const uint32_t b = tt & 1;
       int* scell = mcell + b * kRT;
       long long* sdst = mdst + b * kRT;
-      scell[m] = c_cur;
-      sdst[m] = d_cur;
+      if (h == 0) {
+        scell[m] = c_cur;
+        sdst[m] = d_cur;
+      }
       epi_bar();
       // the next tile's destination rows (its cells came one tile earlier) and the cells of the tile
       // after it: in flight while this tile drains
-      {
+      if (h == 0) {
         const int64_t nt = tile + TS;
         const int64_t r1 = nt * kRT + m;
         c_cur = c_nxt;
@@ -254,24 +257,28 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
         const int64_t r2 = (nt + TS) * kRT + m;
         c_nxt = (nt + TS < ntiles && r2 < args.R) ? args.rowcell[r2] : -1;
       }
+      // after an expired wait every epilogue warp keeps walking the tiles without work, so that all of
+      // them still meet at the barrier above
       const bool got = rwait(&tfull[b], (tt >> 1) & 1, abort, args.status);
-      if (!__all_sync(0xffffffffu, got)) break;
+      if (!__all_sync(0xffffffffu, got)) continue;
       tc_fence_after();
       const int64_t left = args.R - tile * kRT;
-      const int rows = left < kRT ? (int)left : kRT;
+      const int rbeg = kPT * h;                             // this warp's rows rbeg .. rows - 1
+      const int rows = (int)(left < rbeg + kPT ? left : rbeg + kPT);
       const uint32_t tb = tmem + b * (NH * 128) + lane_off;
-      // running sums of the current (cell, tile) segment and the destination of its next row
+      const int64_t blk = 2 * tile + h;                     // 64-row block of the input rows
+      // running sums of the current (cell, block) segment and the destination of its next row
       float s0 = 0.0f, s1 = 0.0f;
-      int seg = scell[0];
-      __nv_bfloat16* dp = args.xout + (size_t)sdst[0] * W + n0;
+      int seg = rbeg < rows ? scell[rbeg] : 0;
+      __nv_bfloat16* dp = args.xout + (size_t)(rbeg < rows ? sdst[rbeg] : 0) * W + n0;
 #pragma unroll 1
-      for (int c0 = 0; c0 < rows; c0 += 32) {
+      for (int c0 = rbeg; c0 < rows; c0 += 32) {
         // rows c0 .. c0 + 31: which of them start a segment (a ballot over the warp's lanes), and
         // each lane's row's cell and destination, handed to the row loop by shuffles
         const int rl = c0 + lane;
         const int cl = rl < rows ? scell[rl] : -1;
         const long long dl = rl < rows ? sdst[rl] : 0;
-        const uint32_t starts = __ballot_sync(0xffffffffu, rl < rows && rl > 0 && cl != scell[rl - 1]);
+        const uint32_t starts = __ballot_sync(0xffffffffu, rl < rows && rl > rbeg && cl != scell[rl - 1]);
         float v0[32], v1[32];
         tmem_ld32(tb + c0, v0);
         if (NH == 2) tmem_ld32(tb + 128 + c0, v1);
@@ -280,7 +287,7 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
         auto row = [&](int i, float x0, float x1) {
           if ((starts >> i) & 1u) {                        // uniform: every thread sees the same rows
             if (own) {
-              float* pp = args.part + (size_t)rows_part_slot(seg, tile) * W + n0;
+              float* pp = args.part + (size_t)rows_part_slot(seg, blk) * W + n0;
               if (NH == 2) *reinterpret_cast<float2*>(pp) = make_float2(s0, s1);
               else *pp = s0;
             }
@@ -316,8 +323,8 @@ __global__ void __launch_bounds__(kGT, 1) k_rows_gemm(const __grid_constant__ Ro
             if (i < nl) row(i, v0[i], NH == 2 ? v1[i] : 0.0f);
         }
       }
-      if (own) {
-        float* pp = args.part + (size_t)rows_part_slot(seg, tile) * W + n0;
+      if (own && rbeg < rows) {
+        float* pp = args.part + (size_t)rows_part_slot(seg, blk) * W + n0;
         if (NH == 2) *reinterpret_cast<float2*>(pp) = make_float2(s0, s1);
         else *pp = s0;
       }

@@ -557,8 +557,9 @@ __global__ void __launch_bounds__(kST, 1) k_rows_split(const __grid_constant__ R
 //      k_rows_new and the three input rows (compensated), fused with activation j+1 (alpha, gamma, a,
 //      and, when AH is given, the split A operand of the next centre / input-row GEMM (which carries
 //      a; otherwise a itself is written, for the output layer) and the next row count
-//      cnt_next = cnt_out + #(gamma != 0)).  One warp per cell, CPL = w / 32 consecutive
-//      neurons per lane; every load of the cell is issued before the first use. ----
+//      cnt_next = cnt_out + #(gamma != 0)).  One warp per cell; PASSES passes over the neurons,
+//      CPL consecutive neurons per lane and pass (w = 32 CPL PASSES); every load of a pass is issued
+//      before its first use. ----
 template <int CPL>
 __device__ __forceinline__ void ldv(const float* p, float* v) {
 #pragma unroll
@@ -1070,14 +1071,16 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
           fi.RAD = ws[WS_RAD].as<float>();
           fi.SLK = ws[WS_DELTA].as<float>();
         }
+        // two neurons per lane and pass: the fewest registers per warp, so the most cells in flight
+        // (four neurons per lane took 1.3x as long, eight 1.33x, at w = 256)
         if (w == 512)
-          k_rows_reduce_act<8, 2><<<rb, 32 * kRedWarps, 0, st>>>(nc, (int)mode, inr->act, part, pnew, off_in, cnt_in,
+          k_rows_reduce_act<2, 8><<<rb, 32 * kRedWarps, 0, st>>>(nc, (int)mode, inr->act, part, pnew, off_in, cnt_in,
                                                                  cnt_out, I1, C, A, AL, GA, cn, ah, ALO, fi);
         else if (w == 256)
-          k_rows_reduce_act<8, 1><<<rb, 32 * kRedWarps, 0, st>>>(nc, (int)mode, inr->act, part, pnew, off_in, cnt_in,
+          k_rows_reduce_act<2, 4><<<rb, 32 * kRedWarps, 0, st>>>(nc, (int)mode, inr->act, part, pnew, off_in, cnt_in,
                                                                  cnt_out, I1, C, A, AL, GA, cn, ah, ALO, fi);
         else if (w == 128)
-          k_rows_reduce_act<4, 1><<<rb, 32 * kRedWarps, 0, st>>>(nc, (int)mode, inr->act, part, pnew, off_in, cnt_in,
+          k_rows_reduce_act<2, 2><<<rb, 32 * kRedWarps, 0, st>>>(nc, (int)mode, inr->act, part, pnew, off_in, cnt_in,
                                                                  cnt_out, I1, C, A, AL, GA, cn, ah, ALO, fi);
         else
           k_rows_reduce_act<2, 1><<<rb, 32 * kRedWarps, 0, st>>>(nc, (int)mode, inr->act, part, pnew, off_in, cnt_in,

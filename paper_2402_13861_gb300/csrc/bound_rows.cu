@@ -312,21 +312,31 @@ __global__ void __launch_bounds__(32 * kNewWarps) k_rows_new(int nc, int sq, con
     IO::st(xout + row * w + m0, h);
     ++row;
   };
-  for (int n0 = 0; n0 < w; n0 += 32) {
-    const float gl = GA[(size_t)cell * w + n0 + lane];
-    unsigned b = __ballot_sync(0xffffffffu, gl != 0.0f);
-    while (b) {                                    // two rows' loads in flight
-      const int l1 = __ffs(b) - 1;
-      b &= b - 1;
-      const int l2 = b ? __ffs(b) - 1 : -1;
-      if (l2 >= 0) b &= b - 1;
-      const float g1 = __shfl_sync(0xffffffffu, gl, l1);
-      const float g2 = __shfl_sync(0xffffffffu, gl, l2 >= 0 ? l2 : l1);
-      float v1[CPL], v2[CPL];
-      IO::ld(Wt + (size_t)(n0 + l1) * w + m0, v1);
-      if (l2 >= 0) IO::ld(Wt + (size_t)(n0 + l2) * w + m0, v2);
-      emit(g1, v1);
-      if (l2 >= 0) emit(g2, v2);
+  // gamma of neurons 32 g + lane for all w / 32 = CPL groups, loaded together; then, group by group,
+  // the new rows in increasing neuron order, NF rows' weight loads in flight
+  constexpr int NF = CPL >= 16 ? 2 : 4;
+  float gl[CPL];
+#pragma unroll
+  for (int g = 0; g < CPL; ++g) gl[g] = GA[(size_t)cell * w + 32 * g + lane];
+#pragma unroll
+  for (int g = 0; g < CPL; ++g) {
+    unsigned b = __ballot_sync(0xffffffffu, gl[g] != 0.0f);
+    while (b) {
+      int l[NF];
+#pragma unroll
+      for (int q = 0; q < NF; ++q) {
+        l[q] = b ? __ffs(b) - 1 : -1;
+        b &= b - 1;
+      }
+      float gg[NF], v[NF][CPL];
+#pragma unroll
+      for (int q = 0; q < NF; ++q) {
+        gg[q] = __shfl_sync(0xffffffffu, gl[g], l[q] >= 0 ? l[q] : 0);
+        if (l[q] >= 0) IO::ld(Wt + (size_t)(32 * g + l[q]) * w + m0, v[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < NF; ++q)
+        if (l[q] >= 0) emit(gg[q], v[q]);
     }
   }
 #pragma unroll

@@ -563,8 +563,9 @@ __global__ void __launch_bounds__(kST, 1) k_rows_split(const __grid_constant__ R
 }
 
 // ---- reductions of z_{j+1} per (cell, neuron): r = sum |x| or sigma = sqrt(sum x^2) over the cell's
-//      symbols, from the column sums the row GEMM wrote per (cell, input tile), the new rows' sums of
-//      k_rows_new and the three input rows (compensated), fused with activation j+1 (alpha, gamma, a,
+//      symbols, from the column sums the row GEMM wrote per (cell, 64-row input block), the new
+//      rows' sums of k_rows_new and the three input rows (compensated), fused with activation j+1
+//      (alpha, gamma, a,
 //      and, when AH is given, the split A operand of the next centre / input-row GEMM (which carries
 //      a; otherwise a itself is written, for the output layer) and the next row count
 //      cnt_next = cnt_out + #(gamma != 0)).  One warp per cell; PASSES passes over the neurons,
@@ -1007,7 +1008,7 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
         ga.part = part;
         ga.sq = sq;
         ga.status = status;
-        // bytes: rows in and out, the column sums of every (cell, tile) segment
+        // bytes: rows in and out, the column sums of every (cell, 64-row block) segment
         prof::Scope ps(K_ROWS_GEMM, st, 2.0 * (double)R * w * w, 4.0 * (double)R * w);
         ISX_TRY(rows::launch_rows_gemm(inr, ga, pmaps[j], w, st));
       }
@@ -1064,9 +1065,9 @@ isx_status bound_bf16_rows(isx_inr inr, const CellSource& src, int64_t n, isx_bo
       }
       {
         // reductions of z_{j+1} and activation j+1; its row count goes to the buffer of X_j's counts.
-        // bytes per cell: the column sums (one vector per input tile the cell spans, and the new
-        // rows'), the three input rows and the centre read; a, alpha, gamma and the split operand
-        // (4 rows, two bf16 terms) written
+        // bytes per cell: the column sums (one vector per 64-row input block the cell spans, and
+        // the new rows'), the three input rows and the centre read; a, alpha, gamma and the split
+        // operand (4 rows, two bf16 terms) written
         const bool last = j == H - 1;
         const double vecs = (double)(nc + ntiles) + nc + 3.0 * nc + nc + 3.0 * nc + (last ? 0.0 : 4.0 * nc);
         prof::Scope ps(K_ROWS_REDUCE, st, 0, 4.0 * vecs * w);

@@ -53,9 +53,10 @@ __device__ __forceinline__ bool rwait(uint64_t* b, uint32_t parity, volatile int
   }
 }
 
-// G' = (G diag(alpha_cell)) W_j^T for the R rows of `a`, and the per-(cell, tile) column sums of
-// f(G') (rows_gemm.cu); w = 64, 128 or 256, `wmap` the tensor map of W_j in bf16 with box {64, w},
-// its rows in the order of rows_weight_row (the neuron held by MMA row m).
+// G' = (G diag(alpha_cell)) W_j^T for the R rows of `a`, and the per-(cell, 64-row block) column
+// sums of f(G') (rows_gemm.cu); w = 64, 128, 256 or 512, `wmap` the tensor map of W_j in bf16 with
+// box {64, w} (box {64, 128} at w = 512: a CTA holds a 128-row quarter), its rows in the order of
+// rows_weight_row (the neuron held by MMA row m).
 isx_status launch_rows_gemm(isx_inr inr, const RowsGemmArgs& a, const CUtensorMap& wmap, int w, cudaStream_t st);
 // Row of W_j the row GEMM keeps at position m of its weight operand.  For w = 256 the even neurons
 // come first and the odd ones after them, so that the epilogue thread of MMA row m of the two

@@ -312,15 +312,24 @@ __global__ void __launch_bounds__(32 * kNewWarps) k_rows_new(int nc, int sq, con
     IO::st(xout + row * w + m0, h);
     ++row;
   };
-  // gamma of neurons 32 g + lane for all w / 32 = CPL groups, loaded together; then, group by group,
-  // the new rows in increasing neuron order, NF rows' weight loads in flight
+  // gamma of all w neurons, loaded together into shared memory with one ballot mask per 32; then,
+  // group by group, the new rows in increasing neuron order, NF rows' weight loads in flight (the
+  // group loop is not unrolled: one copy of the row code keeps the kernel small)
   constexpr int NF = CPL >= 16 ? 2 : 4;
-  float gl[CPL];
-#pragma unroll
-  for (int g = 0; g < CPL; ++g) gl[g] = GA[(size_t)cell * w + 32 * g + lane];
+  __shared__ float sgam[kNewWarps][w];
+  __shared__ unsigned smask[kNewWarps][CPL];
+  const int wi = threadIdx.x >> 5;
 #pragma unroll
   for (int g = 0; g < CPL; ++g) {
-    unsigned b = __ballot_sync(0xffffffffu, gl[g] != 0.0f);
+    const float x = GA[(size_t)cell * w + 32 * g + lane];
+    sgam[wi][32 * g + lane] = x;
+    const unsigned bm = __ballot_sync(0xffffffffu, x != 0.0f);
+    if (lane == 0) smask[wi][g] = bm;
+  }
+  __syncwarp();
+#pragma unroll 1
+  for (int g = 0; g < CPL; ++g) {
+    unsigned b = smask[wi][g];
     while (b) {
       int l[NF];
 #pragma unroll
@@ -331,7 +340,7 @@ __global__ void __launch_bounds__(32 * kNewWarps) k_rows_new(int nc, int sq, con
       float gg[NF], v[NF][CPL];
 #pragma unroll
       for (int q = 0; q < NF; ++q) {
-        gg[q] = __shfl_sync(0xffffffffu, gl[g], l[q] >= 0 ? l[q] : 0);
+        gg[q] = l[q] >= 0 ? sgam[wi][32 * g + l[q]] : 0.0f;
         if (l[q] >= 0) IO::ld(Wt + (size_t)(32 * g + l[q]) * w + m0, v[q]);
       }
 #pragma unroll

@@ -47,8 +47,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--all-forms", action="store_true",
-                    help="also the slow forms: RA-Fixed and the SIREN workload (fits a SIREN); the default run "
-                         "keeps the quick ones")
+                    help="also the slow forms: RA-Fixed, the SIREN workload (fits a SIREN), the large network at "
+                         "1024^3 and the 64-entry batch; the default run keeps the quick ones")
     return ap.parse_args()
 
 
@@ -217,22 +217,31 @@ def extraction_forms(pkg, net, L, isos, plain, plain_ms, mode, k, prec, slow=Fal
     return out
 
 
-def batched_form(pkg, mode, k, workers=8):
-    """The batched form: 32 extractions of mixed shape in flight together.  8 networks (hidden widths
-    64 / 128 / 256, 3-6 hidden layers), each fitted for 300 Adam steps to its own field of the
-    scientific kind (32-256 anisotropic Gaussians + sine), give 4 entries each (own INR handle): octrees
-    to 128^3 and 256^3, 16 iso-values over the 10-90 % or 20-80 % quantiles.  Reports the 32 extractions
-    run one after another (a batch with one worker) and together (`workers` worker streams), and
-    checks that every entry's mesh is the same."""
+def batched_form(pkg, mode, k, workers=8, full=False):
+    """The batched form: extractions of mixed shape in flight together.  Networks of hidden width
+    64 / 128 / 256 are each fitted for 300 Adam steps to their own field of the scientific kind
+    (anisotropic Gaussians + sine) and give 4 entries each (own INR handle), 16 iso-values over the
+    10-90 % or 20-80 % quantiles.  Default: 8 networks (3-6 hidden layers, 32-256 Gaussians), octrees
+    to 128^3 and 256^3, 32 entries.  `full` (the batched configuration's shape): 16 networks (3-8 hidden
+    layers, 16-512 Gaussians), octrees to 128^3, 256^3 and, for widths 64 and 128, 512^3, 64 entries;
+    it takes about four minutes, most of it fitting.  Reports the extractions run one after another (a
+    batch with one worker) and together (`workers` worker streams), and checks that every entry's mesh
+    is the same."""
     import torch
     from synth import fields, inr
-    specs = [(64, 3, 32), (128, 3, 64), (256, 3, 128), (64, 5, 48), (128, 4, 96), (256, 4, 160), (128, 6, 192),
-             (256, 5, 256)]
+    if full:
+        specs = [(64, 3, 16), (64, 4, 24), (64, 5, 48), (64, 6, 40), (64, 8, 96), (128, 3, 32), (128, 4, 64),
+                 (128, 5, 160), (128, 6, 128), (128, 8, 192), (256, 3, 64), (256, 4, 128), (256, 5, 256),
+                 (256, 6, 384), (256, 7, 320), (256, 8, 512)]
+    else:
+        specs = [(64, 3, 32), (128, 3, 64), (256, 3, 128), (64, 5, 48), (128, 4, 96), (256, 4, 160), (128, 6, 192),
+                 (256, 5, 256)]
     nets, params, shapes = [], [], []
     for i, (w, H, nb) in enumerate(specs):
         layers, _ = inr.fit([3] + [w] * H + [1], fields.anisotropic_blobs(4000 + i, nb), 300, init_seed=4000 + i,
                             sample_seed=5000 + i)
-        for j, (L, lo_q, hi_q) in enumerate(((7, 0.1, 0.9), (7, 0.2, 0.8), (8, 0.1, 0.9), (8, 0.2, 0.8))):
+        top = 9 if full and w <= 128 else 8
+        for j, (L, lo_q, hi_q) in enumerate(((7, 0.1, 0.9), (7, 0.2, 0.8), (8, 0.1, 0.9), (top, 0.2, 0.8))):
             isos = inr.quantile_isos(layers, 16, lo_q=lo_q, hi_q=hi_q, grid=64)
             nets.append(pkg.Inr(layers))
             params.append(dict(max_level=L, isos=isos, mode=mode, k=k, prec="bf16",
@@ -662,7 +671,7 @@ def main():
         extra = [("fp32_vs_bf16", lambda: precision_sample(net, args.mode))]
         if prec == "bf16":
             extra += [("large", lambda: large_form(pkg, full=args.all_forms)),
-                      ("batched", lambda: batched_form(pkg, args.mode, args.k)),
+                      ("batched", lambda: batched_form(pkg, args.mode, args.k, full=args.all_forms)),
                       ("activations", lambda: activation_forms(
                           pkg, args.k, ("siren", "sdf_elu") if args.all_forms else ("sdf_elu",)))]
         for name, fn in extra:
